@@ -1,0 +1,210 @@
+/*
+ * tmloops — stochastic disconnected fermion loops for twisted-mass Wilson
+ * fermions on one GB300 GPU (method of arXiv:1401.6749).
+ *
+ * C ABI.  Every pointer to a field, a loop array or a gauge field is a DEVICE
+ * pointer owned by the caller; the library never frees caller memory.  The
+ * library allocates device memory only inside an opaque tm_op_t (link copies,
+ * solver work vectors) and, for the two-stage reductions of the contraction
+ * kernels, stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on the
+ * caller's stream).  All calls are asynchronous with respect to the host and
+ * ordered on the given stream, except tm_op_create (waits for the link packing)
+ * and tm_cg_solve (returns when every right-hand side has converged or hit
+ * its iteration limit).  Functions return a tm_status_t; on failure
+ * tm_last_error() (thread-local) describes the cause.  Nothing here traps the
+ * GPU: argument errors are reported before any launch, and solver failures
+ * (no convergence, non-finite residuals) come back as status codes.
+ *
+ * Lattice and fields
+ * ------------------
+ * Extents L = {X, Y, Z, T}, every one even and >= 2; V = X*Y*Z*T.  Site
+ * x = (x, y, z, t) has lexicographic index  lex = x + X*(y + Y*(z + Z*t))  and
+ * parity (x + y + z + t) mod 2.  Direction mu = 0, 1, 2, 3 is x, y, z, t.
+ *
+ * Canonical (host-facing) layouts, complex numbers as (re, im) pairs of double:
+ *   spinor  [nrhs][V (lex)][4 Dirac][3 colour][2]
+ *   gauge   [4 mu][V (lex)][3][3][2]         U[mu](x) = link from x to x + mu_hat
+ *   loops   local: [nrhs][16 Gamma][T][2]    one-derivative: [nrhs][4 mu][16][T][2]
+ *
+ * Internal (device compute) spinor layout, produced by tm_spinor_pack or
+ * z4_noise and consumed by every kernel: for precision P with element size s,
+ * a field is [nrhs][2 parity][24*s/16 chunks][V/2 sites][16 bytes], site index
+ * within a parity cb = lex/2, each 16-byte chunk holding consecutive reals of the
+ * canonical per-site order.  Bytes per field: tm_spinor_bytes().
+ *
+ * Dirac basis: DeGrand-Rossi chiral, Euclidean, gamma_5 = g1 g2 g3 g4 =
+ * diag(1, 1, -1, -1).  The 16 insertions are Gamma_n = g1^n0 g2^n1 g3^n2 g4^n3
+ * with n = n0 + 2 n1 + 4 n2 + 8 n3 (Gamma_0 = 1, Gamma_15 = gamma_5).
+ */
+#ifndef TMLOOPS_H
+#define TMLOOPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *tm_stream_t;
+
+typedef enum {
+  TM_OK = 0,
+  TM_ERR_ARG = 1,        /* invalid argument (null pointer, bad extent, size) */
+  TM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  TM_ERR_NOCONV = 3,     /* CG reached max_iter before the tolerance */
+  TM_ERR_NAN = 4,        /* a residual norm became non-finite */
+  TM_ERR_TIMEOUT = 5,    /* a bounded wait gave up */
+  TM_ERR_UNSUPPORTED = 6 /* valid but unsupported combination (e.g. 18-real half links) */
+} tm_status_t;
+
+typedef enum {
+  TM_PREC_F64 = 0,
+  TM_PREC_F32 = 1,
+  TM_PREC_F16 = 2,  /* IEEE binary16 storage, FP32 arithmetic */
+  TM_PREC_BF16 = 3  /* bfloat16 storage, FP32 arithmetic */
+} tm_prec_t;
+
+typedef struct { int L[4]; } tm_geom_t;
+
+/* Twisted-mass Wilson operator (Sec. 2.2 and 2.4; kappa normalisation):
+ *   M psi(x) = psi(x) + i nu g5 psi(x)
+ *            - kappa sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ * nu = 2 kappa mu, psi antiperiodic in time when antiperiodic_t != 0.
+ * M^dag = g5 M(-mu) g5;  D_W = M at mu = 0 (Eq. 6).                      */
+typedef struct {
+  int L[4];
+  double kappa;
+  double mu;
+  int antiperiodic_t;
+  int recon;  /* 12 or 18: real numbers stored per link in the F32/F16/BF16
+                 copies (12 = two rows, third = conj(row0 x row1)); the F64
+                 copy always stores 18 */
+} tm_params_t;
+
+typedef struct tm_op tm_op_t;
+
+/* Create an operator: validates p, copies the FP64 canonical gauge field
+ * U_lex (device, [4][V][3][3][2] doubles, not retained) into internal
+ * even/odd link arrays for every precision.  Blocks until done.            */
+tm_status_t tm_op_create(tm_op_t **op, const tm_params_t *p, const double *U_lex, tm_stream_t s);
+tm_status_t tm_op_destroy(tm_op_t *op);
+
+/* Bytes of nrhs internal spinor fields of precision prec on geometry g. */
+size_t tm_spinor_bytes(const tm_geom_t *g, tm_prec_t prec, int nrhs);
+
+/* Canonical FP64 <-> internal layout (round to nearest even on narrowing). */
+tm_status_t tm_spinor_pack(const tm_geom_t *g, void *out, tm_prec_t prec,
+                           const double *in_lex, int nrhs, tm_stream_t s);
+tm_status_t tm_spinor_unpack(const tm_geom_t *g, double *out_lex, const void *in,
+                             tm_prec_t prec, int nrhs, tm_stream_t s);
+/* Internal layout precision conversion, out and in must not overlap. */
+tm_status_t tm_spinor_convert(const tm_geom_t *g, void *out, tm_prec_t out_prec,
+                              const void *in, tm_prec_t in_prec, int nrhs, tm_stream_t s);
+/* out = gamma_5 in (internal layout; out may equal in). */
+tm_status_t tm_gamma5(const tm_geom_t *g, void *out, const void *in, tm_prec_t prec,
+                      int nrhs, tm_stream_t s);
+
+/* out = M in, M^dag in (dagger != 0) or D_W in (mu_zero != 0) for nrhs
+ * internal-layout fields of precision prec; FP32 arithmetic for F16/BF16.
+ * out and in must not overlap.                                             */
+tm_status_t tm_dslash(tm_op_t *op, void *out, const void *in, int nrhs, int dagger,
+                      int mu_zero, tm_prec_t prec, tm_stream_t s);
+
+/* Z4 noise (Sec. 2, Eqs. 1-2): eta_r(x)_{alpha c} = i^k with k = bits
+ * [2(3 alpha + c), 2(3 alpha + c) + 1] of word 0 of Philox4x32-10 applied to
+ * counter (lex, r, 0, 0) with key (seed mod 2^32, seed >> 32), for
+ * r = first_src .. first_src + nsrc - 1.  Values are exact in every precision.
+ * Output: nsrc internal-layout fields of precision prec.                   */
+tm_status_t z4_noise(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t seed,
+                     uint32_t first_src, int nsrc, tm_stream_t s);
+
+/* Conjugate gradient on the normal equations (Sec. 2.1: "a CG solver"):
+ *   M^dag M x = M^dag eta,  x_0 = 0,  so that x = M^{-1} eta = s (Eq. 3);
+ * stop when the iterated residual satisfies |r| <= tol |M^dag eta|.
+ * TM_CG_PLAIN: every vector in `prec` (the low-precision TSM solves run this
+ *   way in F16/BF16 with tol ~ 1e-2, Sec. 2.1; the FP64 baseline in F64).
+ * TM_CG_MIXED: x, eta and the true residual in F64; the iteration in
+ *   inner_prec; reliable updates (x += y, r = b - M^dag M x in F64) whenever
+ *   |r| < delta * max|r| since the last update, and before accepting
+ *   convergence.  eta and x are then F64 internal fields.
+ * nrhs independent systems are solved together; each has its own scalars and
+ * stops on its own.  stats (host array of nrhs, may be NULL) receives per-system
+ * results.  Blocks the calling thread until all systems have stopped.
+ * Returns TM_ERR_NOCONV if any system hit max_iter, TM_ERR_NAN on non-finite
+ * norms.  x and eta must not overlap.                                       */
+typedef enum { TM_CG_PLAIN = 0, TM_CG_MIXED = 1 } tm_cg_mode_t;
+
+typedef struct {
+  double tol;
+  int max_iter;
+  tm_cg_mode_t mode;
+  tm_prec_t prec;        /* PLAIN: precision of eta, x and work vectors     */
+  tm_prec_t inner_prec;  /* MIXED: precision of the inner iteration         */
+  double delta;          /* MIXED: reliable-update threshold (e.g. 0.1)     */
+  int check_every;       /* host polls the convergence flags every N iterations (>= 1) */
+  int true_residual;     /* PLAIN: compute |b - M^dag M x| / |b| at the end */
+} tm_cg_params_t;
+
+typedef struct {
+  int iters;
+  int reliable_updates;
+  int status;            /* tm_status_t of this system */
+  double rel_res;        /* iterated |r| / |b| at exit  */
+  double true_res;       /* |b - M^dag M x| / |b| (MIXED, or PLAIN with true_residual), else -1 */
+} tm_cg_stats_t;
+
+tm_status_t tm_cg_solve(tm_op_t *op, void *x, const void *eta, int nrhs,
+                        const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
+
+/* Loop contractions (Sec. 2.2; Sec. 1 and Table 2 for the operator classes).
+ * For each right-hand side r and time slice t,
+ *   local:  out[r][g][t] = sum_{x_t = t} L_r(x)^dag (P Gamma_g) R_r(x)
+ *   oneD:   out[r][mu][g][t] = sum_{x_t = t} 1/4 [ Lb(x) G U_mu(x) R(x+mu) - Lb(x) G U_mu(x-mu)^dag R(x-mu)
+ *                                - Lb(x+mu) G U_mu(x)^dag R(x) + Lb(x-mu) G U_mu(x-mu) R(x) ]
+ *           (symmetric covariant derivative, Lb = L^dag, G = P Gamma_g, antiperiodic hops in t)
+ * with P = 1 for TM_LOOP_STD (L = eta, R = s: Tr[X M^-1], Eq. 3) and
+ * P = gamma_5 for TM_LOOP_VV (L = R = s, Eq. 5, prefactor -2 i nu) and
+ * TM_LOOP_GEN (L = s, R = gamma_5 D_W s, Eq. 6, prefactor 2).  The caller
+ * forms L and R; the prefactor is applied by tsm_combine.  left/right are
+ * internal-layout fields of precision prec; out is a device array of doubles
+ * (layout above).  Uses stream-ordered scratch of
+ * 32 * nrhs * T * 2 * ceil(X*Y*Z/2/256) doubles (local) and 8x that (oneD).  */
+typedef enum { TM_LOOP_STD = 0, TM_LOOP_VV = 1, TM_LOOP_GEN = 2 } tm_loop_mode_t;
+
+tm_status_t loop_contract_local(const tm_geom_t *g, const void *left, const void *right,
+                                tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                double *out, tm_stream_t s);
+tm_status_t loop_contract_oneD(tm_op_t *op, const void *left, const void *right,
+                               tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                               double *out, tm_stream_t s);
+
+/* Truncated Solver Method combination (Sec. 2.1, Eq. 4), per component j:
+ *   mean_j = (1/N_HP) sum_{i<N_HP} c (l_hp - l_lp_on_hp)_ij + (1/N_LP) sum_i c (l_lp)_ij
+ *   err_j^2 = Var_i(c (l_hp - l_lp_on_hp))/N_HP + Var_i(c l_lp)/N_LP,
+ * c = scale_re + i scale_im, unbiased variances, separately for re and im;
+ * a variance over fewer than two sources is NaN; n_hp = 0 drops the
+ * correction.  l_hp, l_lp_on_hp: [n_hp][len][2]; l_lp: [n_lp][len][2];
+ * mean, err: [len][2] (err = {err_re, err_im}).  Device pointers; n_lp >= 1. */
+tm_status_t tsm_combine(const double *l_hp, const double *l_lp_on_hp, int n_hp,
+                        const double *l_lp, int n_lp, size_t len, double scale_re,
+                        double scale_im, double *mean, double *err, tm_stream_t s);
+
+/* Diagnostics.  tm_last_error: thread-local text of the last failure.
+ * tm_launch_count: kernels this library launched so far (all threads).
+ * tm_trace_enable(1): bracket every Dslash launch with CUDA events on its
+ * stream; tm_trace_read returns the launches and summed device milliseconds
+ * since the last reset for a kernel class "dslash.<f64|f32|f16|bf16>.<out|
+ * cgupd|resid>" (exact name, or a prefix ending in '*', e.g. "dslash.f16.*"),
+ * after synchronising the recorded events.                                */
+const char *tm_last_error(void);
+uint64_t tm_launch_count(void);
+void tm_trace_enable(int on);
+void tm_trace_reset(void);
+tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMLOOPS_H */

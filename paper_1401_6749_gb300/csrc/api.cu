@@ -1,0 +1,197 @@
+// Operator object, status/error reporting, launch counting, Dslash tracing and
+// the tm_dslash entry point.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tm_host.h"
+
+namespace tml {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+tm_status_t check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+tm_status_t check_geom(const int L[4]) {
+  long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (L[i] < 2 || (L[i] & 1)) {
+      set_error("lattice extent L[%d] = %d must be even and >= 2", i, L[i]);
+      return TM_ERR_ARG;
+    }
+    V *= L[i];
+  }
+  if (V > (1L << 30)) {
+    set_error("lattice volume %ld exceeds 2^30 sites", V);
+    return TM_ERR_ARG;
+  }
+  return TM_OK;
+}
+
+// ------------------------------------------------------------ tracing
+struct TraceRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+static std::mutex g_trace_mu;
+static std::atomic<int> g_trace_on{0};
+static std::vector<TraceRec> g_trace;
+
+void trace_begin(cudaStream_t s, const char* name, cudaEvent_t* ev0) {
+  *ev0 = nullptr;
+  if (!g_trace_on.load(std::memory_order_relaxed)) return;
+  (void)name;
+  if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return; }
+  cudaEventRecord(*ev0, s);
+}
+
+void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0) {
+  if (!ev0) return;
+  cudaEvent_t ev1;
+  if (cudaEventCreate(&ev1) != cudaSuccess) { cudaEventDestroy(ev0); return; }
+  cudaEventRecord(ev1, s);
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace.push_back({name, ev0, ev1});
+}
+
+// ------------------------------------------------------------ dispatch
+tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
+  const bool r12 = op->recon == 12;
+  switch (prec) {
+    case TM_PREC_F64: return dslash_launch<double, 18>(op, c, s);
+    case TM_PREC_F32: return r12 ? dslash_launch<float, 12>(op, c, s) : dslash_launch<float, 18>(op, c, s);
+    case TM_PREC_F16: return r12 ? dslash_launch<__half, 12>(op, c, s) : dslash_launch<__half, 18>(op, c, s);
+    case TM_PREC_BF16:
+      return r12 ? dslash_launch<__nv_bfloat16, 12>(op, c, s) : dslash_launch<__nv_bfloat16, 18>(op, c, s);
+    default: set_error("unknown precision %d", (int)prec); return TM_ERR_ARG;
+  }
+}
+
+size_t link_bytes(const Geom& g, tm_prec_t p, int recon);
+tm_status_t pack_links(const Geom& g, tm_prec_t p, int recon, void* out, const double* U,
+                       cudaStream_t s);
+
+}  // namespace tml
+
+using namespace tml;
+
+extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
+extern "C" uint64_t tm_launch_count(void) { return g_launches.load(); }
+
+extern "C" void tm_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
+
+extern "C" void tm_trace_reset(void) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (auto& r : g_trace) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_trace.clear();
+}
+
+extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* total_ms) {
+  if (!name || !launches || !total_ms) { set_error("tm_trace_read: null argument"); return TM_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  int n = 0;
+  double ms = 0.0;
+  // exact class name, or a prefix followed by '*'
+  const std::string want(name);
+  const bool prefix = !want.empty() && want.back() == '*';
+  const std::string stem = prefix ? want.substr(0, want.size() - 1) : want;
+  for (auto& r : g_trace) {
+    if (prefix ? r.name.compare(0, stem.size(), stem) != 0 : r.name != want) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) { set_error("tm_trace_read: event sync failed"); return TM_ERR_CUDA; }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { set_error("tm_trace_read: elapsed time failed"); return TM_ERR_CUDA; }
+    ms += t;
+    ++n;
+  }
+  *launches = n;
+  *total_ms = ms;
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const double* U_lex,
+                                    tm_stream_t s) {
+  if (!out || !p || !U_lex) { set_error("tm_op_create: null argument"); return TM_ERR_ARG; }
+  *out = nullptr;
+  if (check_geom(p->L) != TM_OK) return TM_ERR_ARG;
+  if (p->recon != 12 && p->recon != 18) { set_error("recon must be 12 or 18, got %d", p->recon); return TM_ERR_ARG; }
+  tm_op* op = new tm_op();
+  op->g = make_geom(p->L, p->antiperiodic_t ? 1 : 0);
+  op->kappa = p->kappa;
+  op->mu = p->mu;
+  op->recon = p->recon;
+  op->work = nullptr;
+  op->work_bytes = 0;
+  op->host_flags = nullptr;
+  op->host_flags_n = 0;
+  for (int i = 0; i < 4; ++i) op->links[i] = nullptr;
+  const cudaStream_t st = (cudaStream_t)s;
+  for (int i = 0; i < 4; ++i) {
+    const tm_prec_t pr = (tm_prec_t)i;
+    const size_t nb = link_bytes(op->g, pr, p->recon);
+    if (cudaMalloc(&op->links[i], nb) != cudaSuccess) {
+      set_error("tm_op_create: cudaMalloc of %zu bytes failed", nb);
+      tm_op_destroy(op);
+      return TM_ERR_CUDA;
+    }
+    const tm_status_t st2 = pack_links(op->g, pr, p->recon, op->links[i], U_lex, st);
+    if (st2 != TM_OK) { tm_op_destroy(op); return st2; }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("tm_op_create: %s", cudaGetErrorString(cudaGetLastError()));
+    tm_op_destroy(op);
+    return TM_ERR_CUDA;
+  }
+  *out = op;
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
+  if (!op) return TM_OK;
+  for (int i = 0; i < 4; ++i)
+    if (op->links[i]) cudaFree(op->links[i]);
+  if (op->work) cudaFree(op->work);
+  if (op->host_flags) cudaFreeHost(op->host_flags);
+  delete op;
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_dslash(tm_op_t* op, void* out, const void* in, int nrhs, int dagger,
+                                 int mu_zero, tm_prec_t prec, tm_stream_t s) {
+  if (!op || !out || !in || nrhs < 0) { set_error("tm_dslash: null argument"); return TM_ERR_ARG; }
+  if (out == in) { set_error("tm_dslash: out and in must not overlap"); return TM_ERR_ARG; }
+  if (nrhs == 0) return TM_OK;
+  DslashCall c;
+  c.in = in;
+  c.out = out;
+  c.nrhs = nrhs;
+  c.dagger = dagger != 0;
+  c.mu_zero = mu_zero != 0;
+  c.epi = EPI_OUT;
+  return dslash_dispatch(op, prec, c, (cudaStream_t)s);
+}

@@ -1,0 +1,415 @@
+// Conjugate gradient on the normal equations M^dag M x = M^dag eta (Sec. 2.1:
+// the paper inverts with CG, truncating the low-precision solves at a
+// residual |r| ~ 1e-2).  Many independent systems run together: every kernel
+// covers all right-hand sides, each system keeps its own scalars on the
+// device and a mask retires it once it has converged, so the host only polls
+// a flag array every `check_every` iterations.
+//
+// Per iteration (PLAIN, every vector in one precision):
+//   t = M p                       Dslash, fused |t|^2 per-warp partials
+//   alpha = |r|^2 / |t|^2         fixed-order reduction + scalar kernel
+//   r -= alpha M^dag t, x += alpha p   Dslash with fused update, |r|^2 partials
+//   beta = |r_new|^2 / |r|^2      fixed-order reduction + scalar kernel
+//   p = r + beta p
+// MIXED adds FP64 reliable updates (Sleijpen & van der Vorst): the iteration
+// runs in inner precision on a correction y; when |r| drops below delta times
+// its value at the last update (or the tolerance is reached), x += y in FP64,
+// r = b - M^dag M x is recomputed in FP64 and the iteration continues from it.
+// Convergence is only accepted on such a true residual.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tm_host.h"
+
+namespace tml {
+
+tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
+                 const int* active, int nrhs, cudaStream_t s);
+tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
+                 const int* mask, int nrhs, cudaStream_t s);
+tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
+                    void* p, const double* ratio, const int* mask, int nrhs, cudaStream_t s);
+
+// per-system device state (structure of arrays)
+struct CgState {
+  double* bb;     // |b|^2
+  double* rr;     // |r|^2 of the current residual
+  double* red;    // output of the last reduction
+  double* alpha;
+  double* beta;
+  double* maxr2;  // |r|^2 at the last reliable update (absolute)
+  double* sigma;  // MIXED: inner vectors hold (true vector) / sigma
+  double* ratio;  // MIXED: sigma_old / sigma_new of the last reliable update
+  int* active;
+  int* ru;        // reliable update pending
+  int* iters;
+  int* nru;
+  int* status;
+};
+
+struct CgScalars {
+  double tol2;
+  double delta2;
+  double n12;     // 12 V complex components per field
+  int max_iter;
+  int nrhs;
+  int mixed;
+};
+
+__global__ void cg_init_kernel(CgState st, CgScalars sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.nrhs) return;
+  const double bb = st.red[i];
+  // MIXED: the inner iteration runs on b / sigma with entries of order one,
+  // so that narrow formats (FP16) neither overflow nor underflow
+  const double sg = (sc.mixed && bb > 0.0 && isfinite(bb)) ? sqrt(bb / sc.n12) : 1.0;
+  st.bb[i] = bb;
+  st.sigma[i] = sg;
+  st.ratio[i] = 1.0;
+  st.rr[i] = bb / (sg * sg);
+  st.maxr2[i] = bb;
+  st.iters[i] = 0;
+  st.nru[i] = 0;
+  st.ru[i] = 0;
+  st.alpha[i] = 0.0;
+  st.beta[i] = 0.0;
+  if (!isfinite(bb)) {
+    st.status[i] = TM_ERR_NAN;
+    st.active[i] = 0;
+  } else {
+    st.status[i] = TM_OK;
+    st.active[i] = (bb > 0.0 && sc.max_iter > 0) ? 1 : 0;
+    if (bb > 0.0 && sc.max_iter == 0 && sc.tol2 < 1.0) st.status[i] = TM_ERR_NOCONV;
+  }
+}
+
+__global__ void cg_alpha_kernel(CgState st, CgScalars sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.nrhs) return;
+  st.ru[i] = 0;  // the reliable update of the previous iteration is complete
+  if (!st.active[i]) return;
+  const double pap = st.red[i];
+  if (!isfinite(pap) || !(pap > 0.0)) {
+    st.status[i] = TM_ERR_NAN;
+    st.active[i] = 0;
+    st.alpha[i] = 0.0;
+    return;
+  }
+  st.alpha[i] = st.rr[i] / pap;
+}
+
+__global__ void cg_beta_plain_kernel(CgState st, CgScalars sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.nrhs || !st.active[i]) return;
+  const double rn = st.red[i];
+  const int it = ++st.iters[i];
+  if (!isfinite(rn)) {
+    st.status[i] = TM_ERR_NAN;
+    st.active[i] = 0;
+    return;
+  }
+  st.beta[i] = rn / st.rr[i];
+  st.rr[i] = rn;
+  if (rn <= sc.tol2 * st.bb[i]) {
+    st.active[i] = 0;
+    st.status[i] = TM_OK;
+  } else if (it >= sc.max_iter) {
+    st.active[i] = 0;
+    st.status[i] = TM_ERR_NOCONV;
+  }
+}
+
+__global__ void cg_beta_mixed_kernel(CgState st, CgScalars sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.nrhs || !st.active[i]) return;
+  const double rn = st.red[i];
+  const int it = ++st.iters[i];
+  if (!isfinite(rn)) {
+    st.status[i] = TM_ERR_NAN;
+    st.active[i] = 0;
+    return;
+  }
+  const double s2 = st.sigma[i] * st.sigma[i];
+  const double rabs = rn * s2;
+  if (rabs <= sc.tol2 * st.bb[i] || rabs < sc.delta2 * st.maxr2[i] || it >= sc.max_iter) {
+    st.ru[i] = 1;  // beta follows from the true residual
+    return;
+  }
+  st.beta[i] = rn / st.rr[i];
+  st.rr[i] = rn;
+}
+
+__global__ void cg_ru_kernel(CgState st, CgScalars sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.nrhs || !st.ru[i]) return;
+  const double rt = st.red[i];  // |b - M^dag M x|^2, absolute
+  st.nru[i] += 1;
+  if (!isfinite(rt)) {
+    st.status[i] = TM_ERR_NAN;
+    st.active[i] = 0;
+    st.ratio[i] = 1.0;
+    return;
+  }
+  const double s_old = st.sigma[i];
+  const double s_new = rt > 0.0 ? sqrt(rt / sc.n12) : s_old;
+  st.beta[i] = rt / (st.rr[i] * s_old * s_old);
+  st.rr[i] = rt / (s_new * s_new);
+  st.sigma[i] = s_new;
+  st.ratio[i] = s_old / s_new;
+  st.maxr2[i] = rt;
+  if (rt <= sc.tol2 * st.bb[i]) {
+    st.active[i] = 0;
+    st.status[i] = TM_OK;
+  } else if (st.iters[i] >= sc.max_iter) {
+    st.active[i] = 0;
+    st.status[i] = TM_ERR_NOCONV;
+  }
+}
+
+static size_t align_up(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Carve the operator's work space into the buffers a solve needs.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  void* take(size_t n) {
+    void* p = base ? base + off : nullptr;
+    off += align_up(n);
+    return p;
+  }
+};
+
+static tm_status_t ensure_work(tm_op* op, size_t bytes, int nflags) {
+  if (op->work_bytes < bytes) {
+    if (op->work) {
+      cudaDeviceSynchronize();
+      cudaFree(op->work);
+      op->work = nullptr;
+      op->work_bytes = 0;
+    }
+    if (cudaMalloc(&op->work, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("tm_cg_solve: cudaMalloc of %zu bytes of work space failed", bytes);
+      return TM_ERR_CUDA;
+    }
+    op->work_bytes = bytes;
+  }
+  if (op->host_flags_n < nflags) {
+    if (op->host_flags) cudaFreeHost(op->host_flags);
+    op->host_flags = nullptr;
+    if (cudaMallocHost(&op->host_flags, sizeof(int) * (size_t)nflags) != cudaSuccess) {
+      cudaGetLastError();
+      op->host_flags_n = 0;
+      set_error("tm_cg_solve: pinned host allocation failed");
+      return TM_ERR_CUDA;
+    }
+    op->host_flags_n = nflags;
+  }
+  return TM_OK;
+}
+
+#define TM_TRY(x)                          \
+  do {                                     \
+    const tm_status_t _s = (x);            \
+    if (_s != TM_OK) return _s;            \
+  } while (0)
+
+static tm_status_t scalar_launch(void (*k)(CgState, CgScalars), const CgState& st,
+                                 const CgScalars& sc, cudaStream_t s) {
+  const int nb = (sc.nrhs + 127) / 128;
+  k<<<nb, 128, 0, s>>>(st, sc);
+  count_launch();
+  return check_launch("cg scalar kernel");
+}
+
+static tm_status_t memcpy_d2d(void* dst, const void* src, size_t n, cudaStream_t s) {
+  if (cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    set_error("tm_cg_solve: device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+static tm_status_t memset_d(void* dst, size_t n, cudaStream_t s) {
+  if (cudaMemsetAsync(dst, 0, n, s) != cudaSuccess) {
+    set_error("tm_cg_solve: memset failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+}  // namespace tml
+
+using namespace tml;
+
+extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nrhs,
+                                   const tm_cg_params_t* prm, tm_cg_stats_t* stats, tm_stream_t strm) {
+  if (!op || !x || !eta || !prm || nrhs < 0) { set_error("tm_cg_solve: null argument"); return TM_ERR_ARG; }
+  if (x == eta) { set_error("tm_cg_solve: x and eta must not overlap"); return TM_ERR_ARG; }
+  if (!(prm->tol >= 0.0) || prm->max_iter < 0) { set_error("tm_cg_solve: tol must be >= 0 and max_iter >= 0"); return TM_ERR_ARG; }
+  const bool mixed = prm->mode == TM_CG_MIXED;
+  if (prm->mode != TM_CG_PLAIN && !mixed) { set_error("tm_cg_solve: unknown mode %d", (int)prm->mode); return TM_ERR_ARG; }
+  if (mixed && !(prm->delta > 0.0 && prm->delta < 1.0)) { set_error("tm_cg_solve: delta must be in (0, 1)"); return TM_ERR_ARG; }
+  const tm_prec_t lo = mixed ? prm->inner_prec : prm->prec;
+  if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: unknown precision"); return TM_ERR_ARG; }
+  if (nrhs == 0) return TM_OK;
+  const cudaStream_t s = (cudaStream_t)strm;
+  const Geom& g = op->g;
+  const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
+  const size_t F = tm_spinor_bytes(&gg, lo, nrhs);
+  const size_t F64 = tm_spinor_bytes(&gg, TM_PREC_F64, nrhs);
+  const int nwarp = nwarp_of(g);
+  const size_t P = sizeof(double) * (size_t)nrhs * 2 * (size_t)nwarp;
+
+  // lay out the work space (first pass sizes, second pass assigns)
+  void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
+  void *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr;
+  double* partial = nullptr;
+  CgState st{};
+  for (int pass = 0; pass < 2; ++pass) {
+    Carver c{pass ? (char*)op->work : nullptr};
+    if (mixed) {
+      b64 = c.take(F64); r64 = c.take(F64); tmp64 = c.take(F64);
+      y = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
+    } else {
+      b = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
+    }
+    partial = (double*)c.take(P);
+    st.bb = (double*)c.take(sizeof(double) * nrhs);
+    st.rr = (double*)c.take(sizeof(double) * nrhs);
+    st.red = (double*)c.take(sizeof(double) * nrhs);
+    st.alpha = (double*)c.take(sizeof(double) * nrhs);
+    st.beta = (double*)c.take(sizeof(double) * nrhs);
+    st.maxr2 = (double*)c.take(sizeof(double) * nrhs);
+    st.sigma = (double*)c.take(sizeof(double) * nrhs);
+    st.ratio = (double*)c.take(sizeof(double) * nrhs);
+    st.active = (int*)c.take(sizeof(int) * nrhs);
+    st.ru = (int*)c.take(sizeof(int) * nrhs);
+    st.iters = (int*)c.take(sizeof(int) * nrhs);
+    st.nru = (int*)c.take(sizeof(int) * nrhs);
+    st.status = (int*)c.take(sizeof(int) * nrhs);
+    if (pass == 0) TM_TRY(ensure_work(op, c.off, 5 * nrhs));
+  }
+  CgScalars sc;
+  sc.tol2 = prm->tol * prm->tol;
+  sc.delta2 = mixed ? prm->delta * prm->delta : 0.0;
+  sc.n12 = 24.0 * (double)g.Vh;
+  sc.max_iter = prm->max_iter;
+  sc.nrhs = nrhs;
+  sc.mixed = mixed ? 1 : 0;
+  const int nper = 2 * nwarp;
+  const tm_prec_t hi = mixed ? TM_PREC_F64 : lo;
+  void* xs = mixed ? y : x;          // iterate of the inner CG
+  void* bb_field = mixed ? b64 : b;  // right-hand side M^dag eta
+
+  // b = M^dag eta, |b|^2
+  {
+    DslashCall c;
+    c.in = eta; c.out = bb_field; c.nrhs = nrhs; c.dagger = true; c.partial = partial;
+    TM_TRY(dslash_dispatch(op, hi, c, s));
+    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    TM_TRY(scalar_launch(cg_init_kernel, st, sc, s));
+  }
+  if (mixed) {
+    TM_TRY(rescale(g, lo, r, b64, st.sigma, nullptr, nullptr, nullptr, nrhs, s));
+    TM_TRY(memset_d(x, F64, s));
+    TM_TRY(memset_d(y, F, s));
+  } else {
+    TM_TRY(memcpy_d2d(r, b, F, s));
+    TM_TRY(memset_d(x, F, s));
+  }
+  TM_TRY(memcpy_d2d(p, r, F, s));
+
+  const int check_every = prm->check_every > 0 ? prm->check_every : 1;
+  int* hflags = op->host_flags;
+  for (int it = 0; it < prm->max_iter; ++it) {
+    DslashCall c1;
+    c1.in = p; c1.out = t; c1.nrhs = nrhs; c1.partial = partial; c1.active = st.active;
+    TM_TRY(dslash_dispatch(op, lo, c1, s));
+    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    TM_TRY(scalar_launch(cg_alpha_kernel, st, sc, s));
+    DslashCall c2;
+    c2.in = t; c2.nrhs = nrhs; c2.dagger = true; c2.epi = EPI_CGUPD; c2.partial = partial;
+    c2.active = st.active; c2.alpha = st.alpha; c2.p = p; c2.x = xs; c2.r = r;
+    TM_TRY(dslash_dispatch(op, lo, c2, s));
+    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    if (!mixed) {
+      TM_TRY(scalar_launch(cg_beta_plain_kernel, st, sc, s));
+    } else {
+      TM_TRY(scalar_launch(cg_beta_mixed_kernel, st, sc, s));
+      // reliable update for the systems that asked for one
+      TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, s));
+      DslashCall c3;
+      c3.in = x; c3.out = tmp64; c3.nrhs = nrhs; c3.active = st.ru;
+      TM_TRY(dslash_dispatch(op, TM_PREC_F64, c3, s));
+      DslashCall c4;
+      c4.in = tmp64; c4.out = r64; c4.b = b64; c4.nrhs = nrhs; c4.dagger = true;
+      c4.epi = EPI_RESID; c4.partial = partial; c4.active = st.ru;
+      TM_TRY(dslash_dispatch(op, TM_PREC_F64, c4, s));
+      TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+      TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
+      TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, s));
+    }
+    TM_TRY(xpay(g, lo, p, r, st.beta, st.active, nrhs, s));
+    if ((it + 1) % check_every == 0 || it + 1 == prm->max_iter) {
+      if (cudaMemcpyAsync(hflags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+        return TM_ERR_CUDA;
+      }
+      bool any = false;
+      for (int i = 0; i < nrhs; ++i) any = any || hflags[i] != 0;
+      if (!any) break;
+    }
+  }
+  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, s));
+
+  // true residual |b - M^dag M x| / |b|
+  const bool want_true = mixed || prm->true_residual;
+  std::vector<double> h_true(nrhs, -1.0);
+  if (want_true) {
+    void* tmp = mixed ? tmp64 : t;
+    void* res = mixed ? r64 : r;
+    DslashCall c3;
+    c3.in = x; c3.out = tmp; c3.nrhs = nrhs;
+    TM_TRY(dslash_dispatch(op, hi, c3, s));
+    DslashCall c4;
+    c4.in = tmp; c4.out = res; c4.b = bb_field; c4.nrhs = nrhs; c4.dagger = true;
+    c4.epi = EPI_RESID; c4.partial = partial;
+    TM_TRY(dslash_dispatch(op, hi, c4, s));
+    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    if (cudaMemcpyAsync(h_true.data(), st.red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+      return TM_ERR_CUDA;
+    }
+  }
+  std::vector<double> h_bb(nrhs), h_rr(nrhs);
+  std::vector<int> h_it(nrhs), h_nru(nrhs), h_status(nrhs);
+  bool ok = cudaMemcpyAsync(h_bb.data(), st.bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h_rr.data(), st.rr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h_it.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h_nru.data(), st.nru, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h_status.data(), st.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  tm_status_t worst = TM_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    const double bbi = h_bb[i];
+    if (stats) {
+      stats[i].iters = h_it[i];
+      stats[i].reliable_updates = h_nru[i];
+      stats[i].status = h_status[i];
+      stats[i].rel_res = bbi > 0 ? std::sqrt(h_rr[i] / bbi) : 0.0;
+      stats[i].true_res = want_true ? (bbi > 0 ? std::sqrt(h_true[i] / bbi) : 0.0) : -1.0;
+    }
+    if (h_status[i] == TM_ERR_NAN) worst = TM_ERR_NAN;
+    else if (h_status[i] == TM_ERR_NOCONV && worst == TM_OK) worst = TM_ERR_NOCONV;
+  }
+  if (worst == TM_ERR_NAN) set_error("tm_cg_solve: non-finite residual norm");
+  else if (worst == TM_ERR_NOCONV) set_error("tm_cg_solve: max_iter reached before tolerance");
+  return worst;
+}

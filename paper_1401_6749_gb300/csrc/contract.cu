@@ -1,0 +1,495 @@
+// Loop contractions (Sec. 2.2; Table 2 "local" and "one-derivative"
+// operators) and the Truncated Solver Method combination (Sec. 2.1, Eq. 4).
+//
+// Both contractions first build, per time slice, the 4x4 Dirac matrices
+//   S_{ab}(t) = sum_{x_t = t} sum_c conj(L_{ac}(x)) W_{bc}(x)
+// (W = R for local insertions; W = U_mu(x) R(x+mu) or U_mu(x-mu)^dag R(x-mu) for
+// the one-derivative ones) and only then project them on the 16 Gamma
+// matrices: every Gamma_g of the DeGrand-Rossi basis is a phased permutation,
+// so Tr[(P Gamma_g)^T S] = sum_a i^{k_ga} S_{a, pi_g(a)} costs four terms.
+//
+// Reductions are deterministic and independent of the batch: each block sums
+// a fixed chunk of one (slice, parity) of one right-hand side; a warp
+// butterfly (transpose-reduce) leaves lane j with component j, the eight warp
+// results are added in order, and a final kernel adds the chunk partials in
+// order.
+#include <cstring>
+
+#include "tm_host.h"
+
+namespace tml {
+
+// ------------------------------------------------------- Gamma tables
+// gamma_mu rows as (column, i^k): upper rows from A_mu, lower rows from B_mu.
+struct GammaTab {
+  unsigned char perm[16][4];
+  unsigned char k[16][4];
+};
+
+static GammaTab make_gamma_tab() {
+  // DeGrand-Rossi gamma_1..4 as phased permutations (row -> column, phase i^k)
+  const int gp[4][4] = {{3, 2, 1, 0}, {3, 2, 1, 0}, {2, 3, 0, 1}, {2, 3, 0, 1}};
+  const int gk[4][4] = {{1, 1, 3, 3}, {2, 0, 0, 2}, {1, 3, 3, 1}, {0, 0, 0, 0}};
+  GammaTab t;
+  for (int n = 0; n < 16; ++n) {
+    int perm[4] = {0, 1, 2, 3}, ph[4] = {0, 0, 0, 0};
+    for (int m = 0; m < 4; ++m) {
+      if (!((n >> m) & 1)) continue;
+      // (X gamma_m): row a -> column gp[m][perm[a]], phase ph[a] + gk[m][perm[a]]
+      for (int a = 0; a < 4; ++a) {
+        const int c = perm[a];
+        ph[a] = (ph[a] + gk[m][c]) & 3;
+        perm[a] = gp[m][c];
+      }
+    }
+    for (int a = 0; a < 4; ++a) {
+      t.perm[n][a] = (unsigned char)perm[a];
+      t.k[n][a] = (unsigned char)ph[a];
+    }
+  }
+  return t;
+}
+
+static const GammaTab& gamma_tab() {
+  static const GammaTab t = make_gamma_tab();
+  return t;
+}
+
+// ------------------------------------------------------- warp butterfly
+// v[0..31] per lane in, lane l returns the warp sum of component l.
+template <class T>
+__device__ __forceinline__ T warp_transpose_reduce(T (&v)[32]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const T send = up ? v[i] : v[i + w];
+      const T keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(full, send, w);
+    }
+  }
+  return v[0];
+}
+
+// --------------------------------------------------------- local loops
+constexpr int kLocalK = 4;          // sites per thread
+constexpr int kLocalChunk = 256 * kLocalK;
+
+template <class S>
+__global__ void __launch_bounds__(256) local_partial_kernel(Geom g, const void* Lf, const void* Rf,
+                                                            int nchunk, double* partial) {
+  using R = typename Prec<S>::R;
+  const int chunk = blockIdx.x;
+  const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
+  const int rhs = blockIdx.z;
+  R acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0;
+#pragma unroll 1
+  for (int k = 0; k < kLocalK; ++k) {
+    const int i = chunk * kLocalChunk + k * 256 + (int)threadIdx.x;
+    if (i < g.V3h) {
+      const size_t b0 = SpinorRef<S>::base(g, rhs, par, t * g.V3h + i);
+      Cx<R> l[12], r[12];
+      load_spinor<S>(l, Lf, b0, (size_t)g.Vh);
+      load_spinor<S>(r, Rf, b0, (size_t)g.Vh);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const Cx<R> m = cmulc(l[3 * a + c], r[3 * b + c]);
+            acc[2 * (4 * a + b)] += m.re;
+            acc[2 * (4 * a + b) + 1] += m.im;
+          }
+    }
+  }
+  const R v = warp_transpose_reduce(acc);
+  __shared__ double sh[8][32];
+  sh[threadIdx.x >> 5][threadIdx.x & 31] = (double)v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += sh[w][threadIdx.x];
+    const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
+    partial[slot * 32 + threadIdx.x] = s;
+  }
+}
+
+// Gamma projection of a 4x4 complex matrix stored as 32 doubles (row-major, re/im).
+__device__ __forceinline__ Cx<double> gamma_project(const double* S, const GammaTab& tab, int gidx,
+                                                    int p_g5) {
+  Cx<double> acc = {0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int b = tab.perm[gidx][a];
+    const int k = tab.k[gidx][a] + ((p_g5 && a >= 2) ? 2 : 0);
+    const Cx<double> s = {S[2 * (4 * a + b)], S[2 * (4 * a + b) + 1]};
+    acc = acc + iphase_rt(k, s);
+  }
+  return acc;
+}
+
+__global__ void local_final_kernel(const double* partial, int nchunk, int T, GammaTab tab,
+                                   int p_g5, double* out) {
+  const int t = blockIdx.x, rhs = blockIdx.y;
+  __shared__ double S[32];
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int par = 0; par < 2; ++par) {
+      const size_t slot0 = (((size_t)rhs * T + t) * 2 + par) * nchunk;
+      for (int c = 0; c < nchunk; ++c) s += partial[(slot0 + c) * 32 + threadIdx.x];
+    }
+    S[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    const Cx<double> v = gamma_project(S, tab, threadIdx.x, p_g5);
+    const size_t o = (((size_t)rhs * 16 + threadIdx.x) * T + t) * 2;
+    out[o] = v.re;
+    out[o + 1] = v.im;
+  }
+}
+
+// ----------------------------------------------------- one-derivative loops
+constexpr int kOneDK = 4;           // sites per thread
+constexpr int kOneDLanes = 64;      // sites side by side in a block (x 4 directions)
+constexpr int kOneDChunk = kOneDLanes * kOneDK;
+
+__device__ __forceinline__ int sel4(const int (&a)[4], int mu) {
+  return mu == 0 ? a[0] : mu == 1 ? a[1] : mu == 2 ? a[2] : a[3];
+}
+
+template <class S, int RECON>
+__global__ void __launch_bounds__(256) oneD_partial_kernel(Geom g, const void* links, const void* Lf,
+                                                           const void* Rf, int nchunk,
+                                                           double* partial) {
+  using R = typename Prec<S>::R;
+  const int chunk = blockIdx.x;
+  const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
+  const int rhs = blockIdx.z;
+  const int mu = threadIdx.y;
+  const int opar = par ^ 1;
+  const size_t cs = (size_t)g.Vh;
+  R accA[32], accB[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) accA[j] = accB[j] = 0;
+  const int Lmu = sel4(g.L, mu), smu = sel4(g.stride, mu);
+#pragma unroll 1
+  for (int k = 0; k < kOneDK; ++k) {
+    const int i = chunk * kOneDChunk + k * kOneDLanes + (int)threadIdx.x;
+    if (i >= g.V3h) continue;
+    const int cb = t * g.V3h + i;
+    const Site s = site_of(g, par, cb);
+    const int cmu = sel4(s.c, mu);
+    const int lf = cmu + 1 < Lmu ? s.lex + smu : s.lex - (Lmu - 1) * smu;
+    const int lb = cmu > 0 ? s.lex - smu : s.lex + (Lmu - 1) * smu;
+    R sf = 1, sb = 1;
+    if (mu == 3 && g.antiperiodic) {
+      if (cmu == Lmu - 1) sf = -1;
+      if (cmu == 0) sb = -1;
+    }
+    Cx<R> l[12], r[12], w[12];
+    load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
+    // A: W = U_mu(x) R(x + mu)
+    load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
+    {
+      const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Cx<R> z = {0, 0};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) z = z + U.m[c][d] * r[3 * a + d];
+          w[3 * a + c] = sf * z;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const Cx<R> m = cmulc(l[3 * a + c], w[3 * b + c]);
+          accA[2 * (4 * a + b)] += m.re;
+          accA[2 * (4 * a + b) + 1] += m.im;
+        }
+    // B: W = U_mu(x - mu)^dag R(x - mu)
+    load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lb >> 1), cs);
+    {
+      const Mat3<R> U = load_link<S, RECON>(links, g, mu, opar, lb >> 1);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Cx<R> z = {0, 0};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) z = z + cmulc(U.m[d][c], r[3 * a + d]);
+          w[3 * a + c] = sb * z;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const Cx<R> m = cmulc(l[3 * a + c], w[3 * b + c]);
+          accB[2 * (4 * a + b)] += m.re;
+          accB[2 * (4 * a + b) + 1] += m.im;
+        }
+  }
+  const R va = warp_transpose_reduce(accA);
+  const R vb = warp_transpose_reduce(accB);
+  // 8 warps: warps 2*mu and 2*mu + 1 hold direction mu
+  __shared__ double sh[8][64];
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  sh[warp][lane] = (double)va;
+  sh[warp][32 + lane] = (double)vb;
+  __syncthreads();
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;  // 0..255 -> (mu, 64 values)
+  const int m2 = tid >> 6, j = tid & 63;
+  const double s = sh[2 * m2][j] + sh[2 * m2 + 1][j];
+  const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
+  partial[slot * 256 + tid] = s;  // [mu][A(32) | B(32)]
+}
+
+// block per (t, rhs); 320 threads: 256 sums of slice t, 32 of A_t(t - 1), 32 of B_t(t + 1)
+__global__ void oneD_final_kernel(const double* partial, int nchunk, int T, GammaTab tab, int p_g5,
+                                  double* out) {
+  const int t = blockIdx.x, rhs = blockIdx.y;
+  __shared__ double Q[4][64];   // per mu: A(t) (32), B(t) (32)
+  __shared__ double Ax[32], Bx[32];
+  const int tid = threadIdx.x;
+  int slice, comp;
+  if (tid < 256) { slice = t; comp = tid; }
+  else if (tid < 288) { slice = (t + T - 1) % T; comp = 3 * 64 + (tid - 256); }
+  else { slice = (t + 1) % T; comp = 3 * 64 + 32 + (tid - 288); }
+  double s = 0.0;
+  for (int par = 0; par < 2; ++par) {
+    const size_t slot0 = (((size_t)rhs * T + slice) * 2 + par) * nchunk;
+    for (int c = 0; c < nchunk; ++c) s += partial[(slot0 + c) * 256 + comp];
+  }
+  if (tid < 256) Q[tid >> 6][tid & 63] = s;
+  else if (tid < 288) Ax[tid - 256] = s;
+  else Bx[tid - 288] = s;
+  __syncthreads();
+  // symmetric derivative: spatial mu -> (A - B)/2 of slice t; time -> [A(t) + A(t-1) - B(t) - B(t+1)]/4
+  __shared__ double D[4][32];
+  if (tid < 128) {
+    const int mu = tid >> 5, e = tid & 31;
+    double v;
+    if (mu < 3) v = 0.5 * (Q[mu][e] - Q[mu][32 + e]);
+    else v = 0.25 * (Q[3][e] + Ax[e] - Q[3][32 + e] - Bx[e]);
+    D[mu][e] = v;
+  }
+  __syncthreads();
+  if (tid < 64) {
+    const int mu = tid >> 4, gi = tid & 15;
+    const Cx<double> v = gamma_project(D[mu], tab, gi, p_g5);
+    const size_t o = ((((size_t)rhs * 4 + mu) * 16 + gi) * T + t) * 2;
+    out[o] = v.re;
+    out[o + 1] = v.im;
+  }
+}
+
+// --------------------------------------------------------- TSM combine
+__device__ __forceinline__ Cx<double> scaled(const double* a, size_t idx, Cx<double> c) {
+  return c * Cx<double>{a[2 * idx], a[2 * idx + 1]};
+}
+
+__global__ void tsm_kernel(const double* hp, const double* lphp, int n_hp, const double* lp, int n_lp,
+                           size_t len, Cx<double> c, double* mean, double* err) {
+  const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  // biased estimate over the low-precision-only sources
+  double mr = 0, mi = 0;
+  for (int i = 0; i < n_lp; ++i) {
+    const Cx<double> v = scaled(lp, (size_t)i * len + j, c);
+    mr += v.re;
+    mi += v.im;
+  }
+  mr /= n_lp;
+  mi /= n_lp;
+  double e2r, e2i;
+  if (n_lp > 1) {
+    double vr = 0, vi = 0;
+    for (int i = 0; i < n_lp; ++i) {
+      const Cx<double> v = scaled(lp, (size_t)i * len + j, c);
+      vr += (v.re - mr) * (v.re - mr);
+      vi += (v.im - mi) * (v.im - mi);
+    }
+    e2r = vr / (n_lp - 1) / n_lp;
+    e2i = vi / (n_lp - 1) / n_lp;
+  } else {
+    e2r = e2i = nan;
+  }
+  if (n_hp > 0) {
+    double dr = 0, di = 0;
+    for (int i = 0; i < n_hp; ++i) {
+      const size_t q = (size_t)i * len + j;
+      const Cx<double> v = scaled(hp, q, c) - scaled(lphp, q, c);
+      dr += v.re;
+      di += v.im;
+    }
+    dr /= n_hp;
+    di /= n_hp;
+    if (n_hp > 1) {
+      double vr = 0, vi = 0;
+      for (int i = 0; i < n_hp; ++i) {
+        const size_t q = (size_t)i * len + j;
+        const Cx<double> v = scaled(hp, q, c) - scaled(lphp, q, c);
+        vr += (v.re - dr) * (v.re - dr);
+        vi += (v.im - di) * (v.im - di);
+      }
+      e2r += vr / (n_hp - 1) / n_hp;
+      e2i += vi / (n_hp - 1) / n_hp;
+    } else {
+      e2r = e2i = nan;
+    }
+    mr += dr;
+    mi += di;
+  }
+  mean[2 * j] = mr;
+  mean[2 * j + 1] = mi;
+  err[2 * j] = sqrt(e2r);
+  err[2 * j + 1] = sqrt(e2i);
+}
+
+template <class F>
+static tm_status_t by_prec_c(tm_prec_t p, F&& f) {
+  switch (p) {
+    case TM_PREC_F64: return f(double{});
+    case TM_PREC_F32: return f(float{});
+    case TM_PREC_F16: return f(__half{});
+    case TM_PREC_BF16: return f(__nv_bfloat16{});
+    default: set_error("unknown precision %d", (int)p); return TM_ERR_ARG;
+  }
+}
+
+static tm_status_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+  if (cudaMallocAsync(p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("contraction scratch: cudaMallocAsync of %zu bytes failed", bytes);
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+// local contraction with caller-chosen scratch (>= local_scratch_bytes)
+size_t local_scratch_bytes(const Geom& g, int nrhs) {
+  const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
+  return sizeof(double) * 32 * (size_t)nrhs * g.L[3] * 2 * nchunk;
+}
+
+tm_status_t local_contract_into(const Geom& g, const void* left, const void* right, tm_prec_t prec,
+                                int nrhs, int p_g5, double* out, double* scratch, cudaStream_t s) {
+  const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
+  const dim3 grid(nchunk, 2 * g.L[3], nrhs);
+  tm_status_t st = by_prec_c(prec, [&](auto tag) {
+    using S = decltype(tag);
+    local_partial_kernel<S><<<grid, 256, 0, s>>>(g, left, right, nchunk, scratch);
+    count_launch();
+    return check_launch("loop_contract_local");
+  });
+  if (st != TM_OK) return st;
+  local_final_kernel<<<dim3(g.L[3], nrhs), 32, 0, s>>>(scratch, nchunk, g.L[3], gamma_tab(), p_g5, out);
+  count_launch();
+  return check_launch("loop_contract_local final");
+}
+
+}  // namespace tml
+
+using namespace tml;
+
+static bool valid_mode(tm_loop_mode_t m) { return m == TM_LOOP_STD || m == TM_LOOP_VV || m == TM_LOOP_GEN; }
+
+extern "C" tm_status_t loop_contract_local(const tm_geom_t* gg, const void* left, const void* right,
+                                           tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                           double* out, tm_stream_t strm) {
+  if (!gg || !left || !right || !out || nrhs < 0) { set_error("loop_contract_local: null argument"); return TM_ERR_ARG; }
+  if (!valid_mode(mode)) { set_error("loop_contract_local: unknown mode %d", (int)mode); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  if (nrhs > 65535) { set_error("loop_contract_local: nrhs must be <= 65535"); return TM_ERR_ARG; }
+  const cudaStream_t s = (cudaStream_t)strm;
+  const Geom g = make_geom(gg->L, 1);
+  double* scratch = nullptr;
+  tm_status_t st = scratch_alloc((void**)&scratch, local_scratch_bytes(g, nrhs), s);
+  if (st != TM_OK) return st;
+  st = local_contract_into(g, left, right, prec, nrhs, mode != TM_LOOP_STD, out, scratch, s);
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const void* right,
+                                          tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                          double* out, tm_stream_t strm) {
+  if (!op || !left || !right || !out || nrhs < 0) { set_error("loop_contract_oneD: null argument"); return TM_ERR_ARG; }
+  if (!valid_mode(mode)) { set_error("loop_contract_oneD: unknown mode %d", (int)mode); return TM_ERR_ARG; }
+  if (nrhs == 0) return TM_OK;
+  if (nrhs > 65535) { set_error("loop_contract_oneD: nrhs must be <= 65535"); return TM_ERR_ARG; }
+  const cudaStream_t s = (cudaStream_t)strm;
+  const Geom& g = op->g;
+  const int nchunk = (g.V3h + kOneDChunk - 1) / kOneDChunk;
+  double* scratch = nullptr;
+  tm_status_t st = scratch_alloc((void**)&scratch, sizeof(double) * 256 * (size_t)nrhs * g.L[3] * 2 * nchunk, s);
+  if (st != TM_OK) return st;
+  const dim3 grid(nchunk, 2 * g.L[3], nrhs);
+  const dim3 block(kOneDLanes, 4);
+  const bool r12 = op->recon == 12;
+  const void* links = op->links[prec];
+  switch (prec) {
+    case TM_PREC_F64:
+      oneD_partial_kernel<double, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch); break;
+    case TM_PREC_F32:
+      if (r12) oneD_partial_kernel<float, 12><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      else oneD_partial_kernel<float, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      break;
+    case TM_PREC_F16:
+      if (r12) oneD_partial_kernel<__half, 12><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      else oneD_partial_kernel<__half, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      break;
+    case TM_PREC_BF16:
+      if (r12) oneD_partial_kernel<__nv_bfloat16, 12><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      else oneD_partial_kernel<__nv_bfloat16, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
+      break;
+    default:
+      cudaFreeAsync(scratch, s);
+      set_error("loop_contract_oneD: unknown precision %d", (int)prec);
+      return TM_ERR_ARG;
+  }
+  count_launch();
+  st = check_launch("loop_contract_oneD");
+  if (st == TM_OK) {
+    oneD_final_kernel<<<dim3(g.L[3], nrhs), 320, 0, s>>>(scratch, nchunk, g.L[3], gamma_tab(),
+                                                          mode != TM_LOOP_STD, out);
+    count_launch();
+    st = check_launch("loop_contract_oneD final");
+  }
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+extern "C" tm_status_t tsm_combine(const double* l_hp, const double* l_lp_on_hp, int n_hp,
+                                   const double* l_lp, int n_lp, size_t len, double scale_re,
+                                   double scale_im, double* mean, double* err, tm_stream_t strm) {
+  if (!l_lp || !mean || !err || n_hp < 0) { set_error("tsm_combine: null argument"); return TM_ERR_ARG; }
+  if (n_lp < 1) { set_error("tsm_combine: the estimator needs n_lp >= 1"); return TM_ERR_ARG; }
+  if (n_hp > 0 && (!l_hp || !l_lp_on_hp)) { set_error("tsm_combine: null high-precision arrays"); return TM_ERR_ARG; }
+  if (len == 0) return TM_OK;
+  const cudaStream_t s = (cudaStream_t)strm;
+  const unsigned nb = (unsigned)((len + 127) / 128);
+  tsm_kernel<<<nb, 128, 0, s>>>(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, len, Cx<double>{scale_re, scale_im},
+                                mean, err);
+  count_launch();
+  return check_launch("tsm_combine");
+}

@@ -1,0 +1,477 @@
+// Field utilities: layout packing, precision conversion, gamma_5, Z4 noise,
+// gauge-link packing, the BLAS-1 updates of the solver and the fixed-order
+// reduction of per-warp partial sums.
+#include <cstdio>
+
+#include "tm_host.h"
+
+namespace tml {
+
+// ------------------------------------------------ exact double <-> storage
+// Stores from double values round once (round to nearest even) directly to
+// the storage format.
+template <class S>
+__device__ __forceinline__ void store_spinor_f64(void* field, size_t b0, size_t cs,
+                                                 const Cx<double> (&v)[12]) {
+  if constexpr (std::is_same<S, double>::value) {
+    store_spinor<double>(field, b0, cs, v);
+  } else if constexpr (std::is_same<S, float>::value) {
+    Cx<float> w[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) w[j] = {(float)v[j].re, (float)v[j].im};
+    store_spinor<float>(field, b0, cs, w);
+  } else {
+    uint4* f = reinterpret_cast<uint4*>(field);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint4 d;
+      S* h = reinterpret_cast<S*>(&d);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (std::is_same<S, __half>::value) {
+          h[2 * k] = __double2half(v[4 * j + k].re);
+          h[2 * k + 1] = __double2half(v[4 * j + k].im);
+        } else {
+          h[2 * k] = __double2bfloat16(v[4 * j + k].re);
+          h[2 * k + 1] = __double2bfloat16(v[4 * j + k].im);
+        }
+      }
+      f[b0 + j * cs] = d;
+    }
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void load_spinor_f64(Cx<double> (&v)[12], const void* field, size_t b0,
+                                                size_t cs) {
+  Cx<typename Prec<S>::R> w[12];
+  load_spinor<S>(w, field, b0, cs);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) v[j] = {(double)w[j].re, (double)w[j].im};
+}
+
+template <class F>
+tm_status_t by_prec(tm_prec_t p, F&& f) {
+  switch (p) {
+    case TM_PREC_F64: return f(double{});
+    case TM_PREC_F32: return f(float{});
+    case TM_PREC_F16: return f(__half{});
+    case TM_PREC_BF16: return f(__nv_bfloat16{});
+    default: set_error("unknown precision %d", (int)p); return TM_ERR_ARG;
+  }
+}
+
+static unsigned blocks_for(long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------- pack/unpack
+template <class S>
+__global__ void pack_kernel(Geom g, void* out, const double* in, int nrhs) {
+  const long V = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * nrhs) return;
+  const int rhs = (int)(i / V);
+  const int lex = (int)(i % V);
+  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
+  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+  const int par = (x + y + z + t) & 1;
+  Cx<double> v[12];
+  const double2* src = reinterpret_cast<const double2*>(in) + ((size_t)rhs * V + lex) * 12;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const double2 d = src[j];
+    v[j] = {d.x, d.y};
+  }
+  store_spinor_f64<S>(out, SpinorRef<S>::base(g, rhs, par, lex >> 1), (size_t)g.Vh, v);
+}
+
+template <class S>
+__global__ void unpack_kernel(Geom g, double* out, const void* in, int nrhs) {
+  const long V = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * nrhs) return;
+  const int rhs = (int)(i / V);
+  const int lex = (int)(i % V);
+  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
+  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+  const int par = (x + y + z + t) & 1;
+  Cx<double> v[12];
+  load_spinor_f64<S>(v, in, SpinorRef<S>::base(g, rhs, par, lex >> 1), (size_t)g.Vh);
+  double2* dst = reinterpret_cast<double2*>(out) + ((size_t)rhs * V + lex) * 12;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) dst[j] = make_double2(v[j].re, v[j].im);
+}
+
+template <class SO, class SI>
+__global__ void convert_kernel(Geom g, void* out, const void* in, int nrhs, const int* active) {
+  const long n = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  if (active && !active[rhs]) return;
+  const int rem = (int)(i % n);
+  const int par = rem / g.Vh, cb = rem % g.Vh;
+  Cx<double> v[12];
+  load_spinor_f64<SI>(v, in, SpinorRef<SI>::base(g, rhs, par, cb), (size_t)g.Vh);
+  store_spinor_f64<SO>(out, SpinorRef<SO>::base(g, rhs, par, cb), (size_t)g.Vh, v);
+}
+
+template <class S>
+__global__ void gamma5_kernel(Geom g, void* out, const void* in, int nrhs) {
+  const long n = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  const int rem = (int)(i % n);
+  const int par = rem / g.Vh, cb = rem % g.Vh;
+  Cx<typename Prec<S>::R> v[12];
+  const size_t b0 = SpinorRef<S>::base(g, rhs, par, cb);
+  load_spinor<S>(v, in, b0, (size_t)g.Vh);
+#pragma unroll
+  for (int j = 6; j < 12; ++j) v[j] = {-v[j].re, -v[j].im};
+  store_spinor<S>(out, b0, (size_t)g.Vh, v);
+}
+
+// ------------------------------------------------------------ Z4 noise
+// Philox4x32 with 10 rounds (Salmon et al., SC'11): per round
+//   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// keys advanced by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += W0;
+      k.y += W1;
+    }
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+template <class S>
+__global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc) {
+  const long V = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * nsrc) return;
+  const int j = (int)(i / V);
+  const int lex = (int)(i % V);
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)lex, first + (uint32_t)j, 0u, 0u), key);
+  Cx<double> v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int q = (int)((w.x >> (2 * k)) & 3u);  // component k = 3*alpha + colour
+    v[k] = q == 0 ? Cx<double>{1, 0} : q == 1 ? Cx<double>{0, 1} : q == 2 ? Cx<double>{-1, 0}
+                                                                          : Cx<double>{0, -1};
+  }
+  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
+  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+  const int par = (x + y + z + t) & 1;
+  store_spinor_f64<S>(eta, SpinorRef<S>::base(g, j, par, lex >> 1), (size_t)g.Vh, v);
+}
+
+// ------------------------------------------------------------ gauge packing
+template <class S, int RECON>
+__global__ void pack_links_kernel(Geom g, void* out, const double* U) {
+  const long V = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * V) return;
+  const int mu = (int)(i / V);
+  const int lex = (int)(i % V);
+  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
+  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+  const int par = (x + y + z + t) & 1;
+  const int cb = lex >> 1;
+  const double2* src = reinterpret_cast<const double2*>(U) + ((size_t)mu * V + lex) * 9;
+  using F = LinkFmt<S, RECON>;
+  const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
+  const size_t cs = (size_t)g.Vh;
+  constexpr int NC = RECON == 18 ? 9 : 6;
+  if constexpr (std::is_same<S, double>::value) {
+    double2* p = reinterpret_cast<double2*>(out);
+    for (int u = 0; u < NC; ++u) p[b0 + u * cs] = src[u];
+  } else if constexpr (std::is_same<S, float>::value) {
+    if constexpr (RECON == 18) {
+      float2* p = reinterpret_cast<float2*>(out);
+      for (int u = 0; u < 9; ++u) p[b0 + u * cs] = make_float2((float)src[u].x, (float)src[u].y);
+    } else {
+      float4* p = reinterpret_cast<float4*>(out);
+      for (int u = 0; u < 3; ++u)
+        p[b0 + u * cs] = make_float4((float)src[2 * u].x, (float)src[2 * u].y,
+                                     (float)src[2 * u + 1].x, (float)src[2 * u + 1].y);
+    }
+  } else {
+    auto cvt = [](double v) -> S {
+      if constexpr (std::is_same<S, __half>::value) return __double2half(v);
+      else return __double2bfloat16(v);
+    };
+    if constexpr (RECON == 18) {
+      S* p = reinterpret_cast<S*>(out);
+      for (int u = 0; u < 9; ++u) {
+        p[2 * (b0 + u * cs)] = cvt(src[u].x);
+        p[2 * (b0 + u * cs) + 1] = cvt(src[u].y);
+      }
+    } else {
+      S* p = reinterpret_cast<S*>(out);
+      for (int u = 0; u < 3; ++u) {
+        S* q = p + 4 * (b0 + u * cs);
+        q[0] = cvt(src[2 * u].x);
+        q[1] = cvt(src[2 * u].y);
+        q[2] = cvt(src[2 * u + 1].x);
+        q[3] = cvt(src[2 * u + 1].y);
+      }
+    }
+  }
+}
+
+size_t link_bytes(const Geom& g, tm_prec_t p, int recon) {
+  const size_t reals = (p == TM_PREC_F64 || recon == 18) ? 18 : 12;
+  return 4 * 2 * (size_t)g.Vh * reals * prec_size(p);
+}
+
+tm_status_t pack_links(const Geom& g, tm_prec_t p, int recon, void* out, const double* U,
+                       cudaStream_t s) {
+  const long n = 4L * 2 * g.Vh;
+  const unsigned nb = blocks_for(n, 256);
+  if (p == TM_PREC_F64) pack_links_kernel<double, 18><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F32 && recon == 12) pack_links_kernel<float, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F32) pack_links_kernel<float, 18><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F16 && recon == 12) pack_links_kernel<__half, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F16) pack_links_kernel<__half, 18><<<nb, 256, 0, s>>>(g, out, U);
+  else if (recon == 12) pack_links_kernel<__nv_bfloat16, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else pack_links_kernel<__nv_bfloat16, 18><<<nb, 256, 0, s>>>(g, out, U);
+  count_launch();
+  return check_launch("pack_links");
+}
+
+// ------------------------------------------------------------ solver BLAS
+// p = r + beta[rhs] p for active systems
+template <class S>
+__global__ void xpay_kernel(Geom g, void* p, const void* r, const double* beta, const int* active,
+                            int nrhs) {
+  const long n = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  if (!active[rhs]) return;
+  const int rem = (int)(i % n);
+  const size_t b0 = SpinorRef<S>::base(g, rhs, rem / g.Vh, rem % g.Vh);
+  using R = typename Prec<S>::R;
+  const R be = (R)beta[rhs];
+  Cx<R> a[12], b[12];
+  load_spinor<S>(a, r, b0, (size_t)g.Vh);
+  load_spinor<S>(b, p, b0, (size_t)g.Vh);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) a[j] = a[j] + be * b[j];
+  store_spinor<S>(p, b0, (size_t)g.Vh, a);
+}
+
+// x64 += sigma[rhs] * y (exact widening), y = 0, for systems with mask[rhs] != 0;
+// sigma may be null (scale 1)
+template <class S>
+__global__ void fold_kernel(Geom g, void* x64, void* y, const double* sigma, const int* mask,
+                            int nrhs) {
+  const long n = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  if (mask && !mask[rhs]) return;
+  const int rem = (int)(i % n);
+  const int par = rem / g.Vh, cb = rem % g.Vh;
+  const double sc = sigma ? sigma[rhs] : 1.0;
+  Cx<double> a[12], b[12];
+  const size_t bx = SpinorRef<double>::base(g, rhs, par, cb);
+  const size_t by = SpinorRef<S>::base(g, rhs, par, cb);
+  load_spinor<double>(a, x64, bx, (size_t)g.Vh);
+  load_spinor_f64<S>(b, y, by, (size_t)g.Vh);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    a[j] = a[j] + sc * b[j];
+    b[j] = {0.0, 0.0};
+  }
+  store_spinor<double>(x64, bx, (size_t)g.Vh, a);
+  store_spinor_f64<S>(y, by, (size_t)g.Vh, b);
+}
+
+// Reliable-update rescaling of the inner iteration (masked systems):
+//   r = r64 / sigma[rhs]   and, if p != null,   p *= ratio[rhs]
+template <class S>
+__global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* sigma, void* p,
+                               const double* ratio, const int* mask, int nrhs) {
+  const long n = 2L * g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  if (mask && !mask[rhs]) return;
+  const int rem = (int)(i % n);
+  const int par = rem / g.Vh, cb = rem % g.Vh;
+  const size_t b64 = SpinorRef<double>::base(g, rhs, par, cb);
+  const size_t bs = SpinorRef<S>::base(g, rhs, par, cb);
+  const double inv = 1.0 / sigma[rhs];
+  Cx<double> v[12];
+  load_spinor<double>(v, r64, b64, (size_t)g.Vh);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) v[j] = inv * v[j];
+  store_spinor_f64<S>(r, bs, (size_t)g.Vh, v);
+  if (p) {
+    const double q = ratio[rhs];
+    load_spinor_f64<S>(v, p, bs, (size_t)g.Vh);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) v[j] = q * v[j];
+    store_spinor_f64<S>(p, bs, (size_t)g.Vh, v);
+  }
+}
+
+tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
+                 const int* active, int nrhs, cudaStream_t s) {
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    xpay_kernel<S><<<nb, 256, 0, s>>>(g, p, r, beta, active, nrhs);
+    count_launch();
+    return check_launch("xpay");
+  });
+}
+
+tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
+                 const int* mask, int nrhs, cudaStream_t s) {
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    fold_kernel<S><<<nb, 256, 0, s>>>(g, x64, y, sigma, mask, nrhs);
+    count_launch();
+    return check_launch("fold");
+  });
+}
+
+tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
+                    void* p, const double* ratio, const int* mask, int nrhs, cudaStream_t s) {
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    rescale_kernel<S><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs);
+    count_launch();
+    return check_launch("rescale");
+  });
+}
+
+tm_status_t convert_masked(const Geom& g, void* out, tm_prec_t po, const void* in, tm_prec_t pi,
+                           int nrhs, const int* active, cudaStream_t s) {
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(po, [&](auto to) {
+    using SO = decltype(to);
+    return by_prec(pi, [&](auto ti) {
+      using SI = decltype(ti);
+      convert_kernel<SO, SI><<<nb, 256, 0, s>>>(g, out, in, nrhs, active);
+      count_launch();
+      return check_launch("convert");
+    });
+  });
+}
+
+// ------------------------------------------------ fixed-order reductions
+// One block per system; thread i sums entries i, i + 256, ... in order, then
+// a fixed shared-memory tree.  The result depends only on the partial array.
+__global__ void reduce_partials_kernel(const double* partial, int nper, double* result) {
+  __shared__ double sh[256];
+  const double* p = partial + (size_t)blockIdx.x * nper;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nper; i += 256) acc += p[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) result[blockIdx.x] = sh[0];
+}
+
+tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* result,
+                            cudaStream_t s) {
+  reduce_partials_kernel<<<nrhs, 256, 0, s>>>(partial, nper, result);
+  count_launch();
+  return check_launch("reduce_partials");
+}
+
+}  // namespace tml
+
+using namespace tml;
+
+// ------------------------------------------------------------ C ABI
+extern "C" size_t tm_spinor_bytes(const tm_geom_t* g, tm_prec_t prec, int nrhs) {
+  if (!g || nrhs < 0) return 0;
+  const size_t V = (size_t)g->L[0] * g->L[1] * g->L[2] * g->L[3];
+  return V * 24 * prec_size(prec) * (size_t)nrhs;
+}
+
+extern "C" tm_status_t tm_spinor_pack(const tm_geom_t* gg, void* out, tm_prec_t prec,
+                                      const double* in_lex, int nrhs, tm_stream_t s) {
+  if (!gg || !out || !in_lex || nrhs < 0) { set_error("tm_spinor_pack: null argument"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  const Geom g = make_geom(gg->L, 1);
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    pack_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, out, in_lex, nrhs);
+    count_launch();
+    return check_launch("pack");
+  });
+}
+
+extern "C" tm_status_t tm_spinor_unpack(const tm_geom_t* gg, double* out_lex, const void* in,
+                                        tm_prec_t prec, int nrhs, tm_stream_t s) {
+  if (!gg || !out_lex || !in || nrhs < 0) { set_error("tm_spinor_unpack: null argument"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  const Geom g = make_geom(gg->L, 1);
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    unpack_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, out_lex, in, nrhs);
+    count_launch();
+    return check_launch("unpack");
+  });
+}
+
+extern "C" tm_status_t tm_spinor_convert(const tm_geom_t* gg, void* out, tm_prec_t out_prec,
+                                         const void* in, tm_prec_t in_prec, int nrhs, tm_stream_t s) {
+  if (!gg || !out || !in || nrhs < 0) { set_error("tm_spinor_convert: null argument"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  return convert_masked(make_geom(gg->L, 1), out, out_prec, in, in_prec, nrhs, nullptr,
+                        (cudaStream_t)s);
+}
+
+extern "C" tm_status_t tm_gamma5(const tm_geom_t* gg, void* out, const void* in, tm_prec_t prec,
+                                 int nrhs, tm_stream_t s) {
+  if (!gg || !out || !in || nrhs < 0) { set_error("tm_gamma5: null argument"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  const Geom g = make_geom(gg->L, 1);
+  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    gamma5_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, out, in, nrhs);
+    count_launch();
+    return check_launch("gamma5");
+  });
+}
+
+extern "C" tm_status_t z4_noise(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,
+                                uint32_t first_src, int nsrc, tm_stream_t s) {
+  if (!gg || !eta || nsrc < 0) { set_error("z4_noise: null argument"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nsrc == 0) return TM_OK;
+  const Geom g = make_geom(gg->L, 1);
+  const unsigned nb = blocks_for(2L * g.Vh * nsrc, 256);
+  const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    z4_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, eta, key, first_src, nsrc);
+    count_launch();
+    return check_launch("z4_noise");
+  });
+}

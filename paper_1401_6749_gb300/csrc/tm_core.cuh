@@ -1,0 +1,313 @@
+// Shared device-side building blocks of the tmloops library: complex
+// arithmetic, storage-precision traits, the even/odd site geometry, spinor
+// and link accessors for the internal layouts, and launch bookkeeping.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <type_traits>
+
+#include "tmloops.h"
+
+namespace tml {
+
+// ---------------------------------------------------------------- complex
+template <class R>
+struct Cx {
+  R re, im;
+};
+
+template <class R>
+__device__ __forceinline__ Cx<R> cx(R re, R im) { return Cx<R>{re, im}; }
+template <class R>
+__device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
+// conj(a) * b
+template <class R>
+__device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> conjx(Cx<R> a) { return {a.re, -a.im}; }
+// i^k * a for a compile-time k in 0..3
+template <int K, class R>
+__device__ __forceinline__ Cx<R> iphase(Cx<R> a) {
+  constexpr int k = ((K % 4) + 4) % 4;
+  if constexpr (k == 0) return a;
+  else if constexpr (k == 1) return {-a.im, a.re};
+  else if constexpr (k == 2) return {-a.re, -a.im};
+  else return {a.im, -a.re};
+}
+// runtime version (k in 0..3)
+template <class R>
+__device__ __forceinline__ Cx<R> iphase_rt(int k, Cx<R> a) {
+  switch (k & 3) {
+    case 0: return a;
+    case 1: return {-a.im, a.re};
+    case 2: return {-a.re, -a.im};
+    default: return {a.im, -a.re};
+  }
+}
+
+// ------------------------------------------------------- storage precisions
+// Storage type S -> arithmetic type R and how many reals one 16-byte chunk holds.
+template <class S> struct Prec;
+template <> struct Prec<double> { using R = double; static constexpr int kChunkReals = 2; static constexpr tm_prec_t id = TM_PREC_F64; };
+template <> struct Prec<float> { using R = float; static constexpr int kChunkReals = 4; static constexpr tm_prec_t id = TM_PREC_F32; };
+template <> struct Prec<__half> { using R = float; static constexpr int kChunkReals = 8; static constexpr tm_prec_t id = TM_PREC_F16; };
+template <> struct Prec<__nv_bfloat16> { using R = float; static constexpr int kChunkReals = 8; static constexpr tm_prec_t id = TM_PREC_BF16; };
+
+template <class S>
+__host__ __device__ constexpr int spinor_chunks() { return 24 / Prec<S>::kChunkReals; }
+
+inline size_t prec_size(tm_prec_t p) {
+  switch (p) {
+    case TM_PREC_F64: return 8;
+    case TM_PREC_F32: return 4;
+    default: return 2;
+  }
+}
+
+// two reals <-> storage pair
+__device__ __forceinline__ float2 h2f(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 h2f(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <class S> __device__ __forceinline__ S f2h(float2 v);
+template <> __device__ __forceinline__ __half2 f2h<__half2>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 f2h<__nv_bfloat162>(float2 v) { return __float22bfloat162_rn(v); }
+template <class S> struct Pair;
+template <> struct Pair<__half> { using T = __half2; };
+template <> struct Pair<__nv_bfloat16> { using T = __nv_bfloat162; };
+
+// ----------------------------------------------------------------- geometry
+struct Geom {
+  int L[4];   // X, Y, Z, T
+  int Xh;     // X / 2
+  int Vh;     // V / 2 (sites per parity)
+  int V3h;    // X*Y*Z / 2 (sites per parity and time slice)
+  int stride[4];  // lexicographic strides 1, X, XY, XYZ
+  int antiperiodic;
+};
+
+inline Geom make_geom(const int L[4], int antiperiodic) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = L[i];
+  g.Xh = L[0] / 2;
+  g.stride[0] = 1;
+  g.stride[1] = L[0];
+  g.stride[2] = L[0] * L[1];
+  g.stride[3] = L[0] * L[1] * L[2];
+  g.V3h = g.stride[3] / 2;
+  g.Vh = g.V3h * L[3];
+  g.antiperiodic = antiperiodic;
+  return g;
+}
+
+// Site of parity `par` with checkerboard index cb: coordinates and lex index.
+struct Site {
+  int c[4];
+  int lex;
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int par, int cb) {
+  Site s;
+  const int xh = cb % g.Xh;
+  int rest = cb / g.Xh;
+  s.c[1] = rest % g.L[1];
+  rest /= g.L[1];
+  s.c[2] = rest % g.L[2];
+  s.c[3] = rest / g.L[2];
+  s.c[0] = 2 * xh + ((par + s.c[1] + s.c[2] + s.c[3]) & 1);
+  s.lex = s.c[0] + g.stride[1] * s.c[1] + g.stride[2] * s.c[2] + g.stride[3] * s.c[3];
+  return s;
+}
+
+// lex index of x +/- mu_hat (periodic wrap), and whether the hop crossed the
+// time boundary.
+__device__ __forceinline__ int lex_fwd(const Geom& g, const Site& s, int mu) {
+  return (s.c[mu] + 1 < g.L[mu]) ? s.lex + g.stride[mu] : s.lex - (g.L[mu] - 1) * g.stride[mu];
+}
+__device__ __forceinline__ int lex_bwd(const Geom& g, const Site& s, int mu) {
+  return (s.c[mu] > 0) ? s.lex - g.stride[mu] : s.lex + (g.L[mu] - 1) * g.stride[mu];
+}
+
+// --------------------------------------------------------- spinor accessors
+// A field of nrhs spinors in the internal layout:
+//   chunk index ((rhs * 2 + par) * NCH + j) * Vh + cb, each chunk 16 bytes.
+template <class S>
+struct SpinorRef {
+  using R = typename Prec<S>::R;
+  static constexpr int NCH = spinor_chunks<S>();
+  __device__ __forceinline__ static size_t base(const Geom& g, int rhs, int par, int cb) {
+    return ((size_t)(rhs * 2 + par) * NCH) * (size_t)g.Vh + (size_t)cb;
+  }
+};
+
+// Load the 12 complex components (index 3*spin + colour) of one site.
+template <class S>
+__device__ __forceinline__ void load_spinor(Cx<typename Prec<S>::R> (&v)[12], const void* field,
+                                            size_t b0, size_t cs) {
+  const uint4* f = reinterpret_cast<const uint4*>(field);
+  if constexpr (std::is_same<S, double>::value) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const double2 d = reinterpret_cast<const double2*>(f)[b0 + j * cs];
+      v[j] = {d.x, d.y};
+    }
+  } else if constexpr (std::is_same<S, float>::value) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float4 d = reinterpret_cast<const float4*>(f)[b0 + j * cs];
+      v[2 * j] = {d.x, d.y};
+      v[2 * j + 1] = {d.z, d.w};
+    }
+  } else {
+    using P2 = typename Pair<S>::T;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint4 d = f[b0 + j * cs];
+      const P2* h = reinterpret_cast<const P2*>(&d);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 q = h2f(h[k]);
+        v[4 * j + k] = {q.x, q.y};
+      }
+    }
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void store_spinor(void* field, size_t b0, size_t cs,
+                                             const Cx<typename Prec<S>::R> (&v)[12]) {
+  uint4* f = reinterpret_cast<uint4*>(field);
+  if constexpr (std::is_same<S, double>::value) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j)
+      reinterpret_cast<double2*>(f)[b0 + j * cs] = make_double2(v[j].re, v[j].im);
+  } else if constexpr (std::is_same<S, float>::value) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      reinterpret_cast<float4*>(f)[b0 + j * cs] =
+          make_float4(v[2 * j].re, v[2 * j].im, v[2 * j + 1].re, v[2 * j + 1].im);
+  } else {
+    using P2 = typename Pair<S>::T;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint4 d;
+      P2* h = reinterpret_cast<P2*>(&d);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) h[k] = f2h<P2>(make_float2(v[4 * j + k].re, v[4 * j + k].im));
+      f[b0 + j * cs] = d;
+    }
+  }
+}
+
+// ----------------------------------------------------------- link accessors
+// Links of direction mu at site (par, cb): unit index ((mu * 2 + par) * NU + u) * Vh + cb.
+// RECON 18: 9 units of one complex each; RECON 12: two rows (6 complex).
+//   F64: unit = double2 (one complex).
+//   F32: RECON 18 -> float2 units (9), RECON 12 -> float4 units of two complex (3).
+//   F16/BF16: RECON 18 -> one half pair (9), RECON 12 -> 8-byte units of two complex (3).
+template <class S, int RECON>
+struct LinkFmt {
+  static constexpr bool kF64 = std::is_same<S, double>::value;
+  static constexpr int kCplxPerUnit = (kF64 || RECON == 18) ? 1 : 2;
+  static constexpr int NU = (RECON == 18 ? 9 : 6) / kCplxPerUnit;
+  static constexpr int kUnitBytes = kCplxPerUnit * 2 * (int)sizeof(S);
+};
+
+template <class R>
+struct Mat3 {
+  Cx<R> m[3][3];
+};
+
+template <class S, int RECON>
+__device__ __forceinline__ Mat3<typename Prec<S>::R> load_link(const void* links, const Geom& g,
+                                                                int mu, int par, int cb) {
+  using R = typename Prec<S>::R;
+  using F = LinkFmt<S, RECON>;
+  Mat3<R> U;
+  Cx<R> e[9];
+  const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
+  const size_t cs = (size_t)g.Vh;
+  constexpr int NC = RECON == 18 ? 9 : 6;
+  if constexpr (std::is_same<S, double>::value) {
+    const double2* p = reinterpret_cast<const double2*>(links);
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const double2 d = p[b0 + u * cs];
+      e[u] = {d.x, d.y};
+    }
+  } else if constexpr (std::is_same<S, float>::value) {
+    if constexpr (RECON == 18) {
+      const float2* p = reinterpret_cast<const float2*>(links);
+#pragma unroll
+      for (int u = 0; u < 9; ++u) {
+        const float2 d = p[b0 + u * cs];
+        e[u] = {d.x, d.y};
+      }
+    } else {
+      const float4* p = reinterpret_cast<const float4*>(links);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const float4 d = p[b0 + u * cs];
+        e[2 * u] = {d.x, d.y};
+        e[2 * u + 1] = {d.z, d.w};
+      }
+    }
+  } else {
+    using P2 = typename Pair<S>::T;
+    if constexpr (RECON == 18) {
+      const P2* p = reinterpret_cast<const P2*>(links);
+#pragma unroll
+      for (int u = 0; u < 9; ++u) {
+        const float2 q = h2f(p[b0 + u * cs]);
+        e[u] = {q.x, q.y};
+      }
+    } else {
+      const uint2* p = reinterpret_cast<const uint2*>(links);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const uint2 d = p[b0 + u * cs];
+        const P2* h = reinterpret_cast<const P2*>(&d);
+        const float2 q0 = h2f(h[0]), q1 = h2f(h[1]);
+        e[2 * u] = {q0.x, q0.y};
+        e[2 * u + 1] = {q1.x, q1.y};
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) U.m[i][j] = e[3 * i + j];
+  if constexpr (RECON == 18) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) U.m[2][j] = e[6 + j];
+  } else {
+    // third row of an SU(3) matrix: complex conjugate of row0 x row1
+    U.m[2][0] = conjx(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
+    U.m[2][1] = conjx(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
+    U.m[2][2] = conjx(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+  }
+  return U;
+}
+
+// ------------------------------------------------------------ bookkeeping
+void count_launch(int n = 1);
+void set_error(const char* fmt, ...);
+tm_status_t check_launch(const char* what);
+void trace_begin(cudaStream_t s, const char* name, cudaEvent_t* ev0);
+void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0);
+
+
+}  // namespace tml

@@ -1,0 +1,64 @@
+// Host-side internals of the tmloops library: the operator object, the
+// Dslash call descriptor shared by the operator and the solver, and the
+// per-precision launch entry points.
+#pragma once
+
+#include <cstddef>
+
+#include "tm_core.cuh"
+
+struct tm_op {
+  tml::Geom g;
+  double kappa;
+  double mu;
+  int recon;          // link format of the F32/F16/BF16 copies (12 or 18)
+  void* links[4];     // indexed by tm_prec_t; F64 always 18-real
+  // solver work space, grown on demand, owned by the operator
+  void* work;
+  size_t work_bytes;
+  // pinned host mirror of the solver's per-system flags
+  int* host_flags;
+  int host_flags_n;
+};
+
+namespace tml {
+
+enum Epi { EPI_OUT = 0, EPI_CGUPD = 1, EPI_RESID = 2 };
+
+// One Dslash application over nrhs fields, with an optional fused epilogue.
+//   EPI_OUT   : out = D in;                 partial |out|^2 if partial != null
+//   EPI_CGUPD : q = D in (not stored); r -= alpha q; x += alpha p;  partial |r|^2
+//   EPI_RESID : out = b - D in;             partial |out|^2
+// D = M, M^dag (dagger) or D_W (mu_zero).  Systems with active[rhs] == 0
+// are skipped entirely (no stores, zero partial).  Partial sums are written
+// per warp of 32 consecutive checkerboard sites: partial[(rhs*2 + par)*nwarp + cb/32].
+struct DslashCall {
+  const void* in = nullptr;
+  void* out = nullptr;
+  int nrhs = 1;
+  bool dagger = false;
+  bool mu_zero = false;
+  int epi = EPI_OUT;
+  double* partial = nullptr;
+  const int* active = nullptr;
+  const double* alpha = nullptr;
+  const void* p = nullptr;
+  void* x = nullptr;
+  void* r = nullptr;
+  const void* b = nullptr;
+};
+
+inline int nwarp_of(const Geom& g) { return (g.Vh + 31) / 32; }
+
+template <class S, int RECON>
+tm_status_t dslash_launch(const tm_op* op, const DslashCall& c, cudaStream_t s);
+
+tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s);
+
+// per-warp partial sums [nrhs][2][nwarp] -> result[rhs] (fixed summation order)
+tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* result,
+                            cudaStream_t s);
+
+tm_status_t check_geom(const int L[4]);
+
+}  // namespace tml

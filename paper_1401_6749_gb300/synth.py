@@ -25,30 +25,34 @@ _GELL_MANN[6][1, 2], _GELL_MANN[6][2, 1] = -1j, 1j
 _GELL_MANN[7] = np.diag([1, 1, -2]) / np.sqrt(3)
 
 
-def _expi(H, chunk=1 << 20):
-    """exp(i H) for a batch of Hermitian 3x3 matrices (torch's matrix_exp, CPU)."""
+def _expi(H, chunk=1 << 20, device="cpu"):
+    """exp(i H) for a batch of Hermitian 3x3 matrices (torch's matrix_exp)."""
     import torch
     out = np.empty_like(H)
     flat = H.reshape(-1, 3, 3)
     res = out.reshape(-1, 3, 3)
     for s in range(0, flat.shape[0], chunk):
-        res[s:s + chunk] = torch.linalg.matrix_exp(
-            torch.from_numpy(1j * flat[s:s + chunk])).numpy()
+        m = torch.from_numpy(1j * flat[s:s + chunk]).to(device)
+        res[s:s + chunk] = torch.linalg.matrix_exp(m).cpu().numpy()
     return out
 
 
-def random_su3(shape, seed, eps):
+def random_su3(shape, seed, eps, device="cpu"):
     """Array shape + (3, 3) of exp(i eps H) with H random traceless Hermitian."""
     rng = np.random.default_rng(seed)
     w = rng.standard_normal(tuple(shape) + (8,))
     H = (w.reshape(-1, 8) @ (_GELL_MANN / 2).reshape(8, 9)).reshape(tuple(shape) + (3, 3))
-    return _expi(eps * H)
+    return _expi(eps * H, device=device)
 
 
-def gauge_field(L, seed, eps=0.3):
-    """Smooth random SU(3) gauge field for lattice L = (X, Y, Z, T)."""
+def gauge_field(L, seed, eps=0.3, device="cpu"):
+    """Smooth random SU(3) gauge field for lattice L = (X, Y, Z, T).
+
+    ``device`` only selects where torch evaluates the matrix exponentials (a
+    GPU makes the 32^3 x 64 field quick); the result is a host array either way.
+    """
     X, Y, Z, T = (int(v) for v in L)
-    return random_su3((4, T, Z, Y, X), seed, eps)
+    return random_su3((4, T, Z, Y, X), seed, eps, device=device)
 
 
 def unit_gauge(L):

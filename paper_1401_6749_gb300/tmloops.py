@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the tmloops C ABI (include/tmloops.h).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in libtmloops.so; tensors are passed by device pointer, the stream
+defaults to torch's current stream.  Importing this module loads the library
+and raises if it is missing — there is no fallback path.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtmloops.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libtmloops.so is not built; run paper_1401_6749_gb300.build.build() "
+                      "(or __graft_entry__.build()) first")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# precisions, modes, status codes (tmloops.h)
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+CG_PLAIN, CG_MIXED = 0, 1
+LOOP_STD, LOOP_VV, LOOP_GEN = 0, 1, 2
+LOOP_MODE = {"std": LOOP_STD, "vv": LOOP_VV, "gen": LOOP_GEN}
+STATUS = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_CUDA", 3: "TM_ERR_NOCONV", 4: "TM_ERR_NAN",
+          5: "TM_ERR_TIMEOUT", 6: "TM_ERR_UNSUPPORTED"}
+ELEM_SIZE = {F64: 8, F32: 4, F16: 2, BF16: 2}
+
+
+class TmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class tm_geom_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4)]
+
+
+class tm_params_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
+                ("antiperiodic_t", ctypes.c_int), ("recon", ctypes.c_int)]
+
+
+class tm_cg_params_t(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("prec", ctypes.c_int), ("inner_prec", ctypes.c_int), ("delta", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int)]
+
+
+class tm_cg_stats_t(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("true_res", ctypes.c_double)]
+
+
+_vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint32,
+                                ctypes.c_uint64, ctypes.c_size_t)
+_P = ctypes.POINTER
+_SIGS = {
+    "tm_op_create": [_P(_vp), _P(tm_params_t), _vp, _vp],
+    "tm_op_destroy": [_vp],
+    "tm_spinor_bytes": [_P(tm_geom_t), _i, _i],
+    "tm_spinor_pack": [_P(tm_geom_t), _vp, _i, _vp, _i, _vp],
+    "tm_spinor_unpack": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
+    "tm_spinor_convert": [_P(tm_geom_t), _vp, _i, _vp, _i, _i, _vp],
+    "tm_gamma5": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
+    "tm_dslash": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
+    "z4_noise": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _vp],
+    "tm_cg_solve": [_vp, _vp, _vp, _i, _P(tm_cg_params_t), _P(tm_cg_stats_t), _vp],
+    "loop_contract_local": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
+    "loop_contract_oneD": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp],
+    "tsm_combine": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp, _vp],
+    "tm_last_error": [],
+    "tm_launch_count": [],
+    "tm_trace_enable": [_i],
+    "tm_trace_reset": [],
+    "tm_trace_read": [ctypes.c_char_p, _P(_i), _P(_d)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _i
+_lib.tm_spinor_bytes.restype = _sz
+_lib.tm_last_error.restype = ctypes.c_char_p
+_lib.tm_launch_count.restype = _u64
+_lib.tm_trace_enable.restype = None
+_lib.tm_trace_reset.restype = None
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(status):
+    if status != 0:
+        raise TmError(status, _lib.tm_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def geom(L):
+    g = tm_geom_t()
+    for i in range(4):
+        g.L[i] = int(L[i])
+    return g
+
+
+def tm_spinor_bytes(L, prec, nrhs):
+    return int(_lib.tm_spinor_bytes(ctypes.byref(geom(L)), int(prec), int(nrhs)))
+
+
+def empty_field(L, prec, nrhs, device="cuda"):
+    """Uninitialised internal-layout field storage (uint8 tensor, 256-byte aligned)."""
+    return torch.empty(tm_spinor_bytes(L, prec, nrhs), dtype=torch.uint8, device=device)
+
+
+class Operator:
+    """Owner of a tm_op_t handle (gauge links in every precision)."""
+
+    def __init__(self, L, kappa, mu, U, antiperiodic=True, recon=12, stream=None):
+        self.L = tuple(int(v) for v in L)
+        self.kappa, self.mu = float(kappa), float(mu)
+        p = tm_params_t()
+        for i in range(4):
+            p.L[i] = self.L[i]
+        p.kappa, p.mu, p.antiperiodic_t, p.recon = self.kappa, self.mu, int(bool(antiperiodic)), int(recon)
+        h = ctypes.c_void_p()
+        _check(_lib.tm_op_create(ctypes.byref(h), ctypes.byref(p), _ptr(U), _stream(stream)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.tm_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_spinor_pack(L, out, prec, in_lex, nrhs, stream=None):
+    _check(_lib.tm_spinor_pack(ctypes.byref(geom(L)), _ptr(out), int(prec), _ptr(in_lex), int(nrhs),
+                               _stream(stream)))
+
+
+def tm_spinor_unpack(L, out_lex, inp, prec, nrhs, stream=None):
+    _check(_lib.tm_spinor_unpack(ctypes.byref(geom(L)), _ptr(out_lex), _ptr(inp), int(prec), int(nrhs),
+                                 _stream(stream)))
+
+
+def tm_spinor_convert(L, out, out_prec, inp, in_prec, nrhs, stream=None):
+    _check(_lib.tm_spinor_convert(ctypes.byref(geom(L)), _ptr(out), int(out_prec), _ptr(inp),
+                                  int(in_prec), int(nrhs), _stream(stream)))
+
+
+def tm_gamma5(L, out, inp, prec, nrhs, stream=None):
+    _check(_lib.tm_gamma5(ctypes.byref(geom(L)), _ptr(out), _ptr(inp), int(prec), int(nrhs),
+                          _stream(stream)))
+
+
+def tm_dslash(op, out, inp, nrhs, dagger=False, mu_zero=False, prec=F32, stream=None):
+    _check(_lib.tm_dslash(op.handle, _ptr(out), _ptr(inp), int(nrhs), int(bool(dagger)),
+                          int(bool(mu_zero)), int(prec), _stream(stream)))
+
+
+def z4_noise(L, eta, prec, seed, first_src, nsrc, stream=None):
+    _check(_lib.z4_noise(ctypes.byref(geom(L)), _ptr(eta), int(prec), int(seed), int(first_src),
+                         int(nsrc), _stream(stream)))
+
+
+def cg_params(tol, max_iter=10000, mode=CG_PLAIN, prec=F64, inner_prec=F32, delta=0.1,
+              check_every=8, true_residual=False):
+    p = tm_cg_params_t()
+    p.tol, p.max_iter, p.mode, p.prec, p.inner_prec = float(tol), int(max_iter), int(mode), int(prec), int(inner_prec)
+    p.delta, p.check_every, p.true_residual = float(delta), int(check_every), int(bool(true_residual))
+    return p
+
+
+def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
+    """Returns (status, list of per-system dicts)."""
+    stats = (tm_cg_stats_t * max(int(nrhs), 1))()
+    st = _lib.tm_cg_solve(op.handle, _ptr(x), _ptr(eta), int(nrhs), ctypes.byref(params), stats,
+                          _stream(stream))
+    out = [dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status,
+                rel_res=s.rel_res, true_res=s.true_res) for s in list(stats)[:int(nrhs)]]
+    if st != 0 and (st != 3 or raise_on_noconv):
+        _check(st)
+    return st, out
+
+
+def loop_contract_local(L, left, right, prec, nrhs, mode, out, stream=None):
+    _check(_lib.loop_contract_local(ctypes.byref(geom(L)), _ptr(left), _ptr(right), int(prec),
+                                    int(nrhs), int(mode), _ptr(out), _stream(stream)))
+
+
+def loop_contract_oneD(op, left, right, prec, nrhs, mode, out, stream=None):
+    _check(_lib.loop_contract_oneD(op.handle, _ptr(left), _ptr(right), int(prec), int(nrhs), int(mode),
+                                   _ptr(out), _stream(stream)))
+
+
+def tsm_combine(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, length, scale, mean, err, stream=None):
+    scale = complex(scale)
+    _check(_lib.tsm_combine(_ptr(l_hp), _ptr(l_lp_on_hp), int(n_hp), _ptr(l_lp), int(n_lp),
+                            int(length), scale.real, scale.imag, _ptr(mean), _ptr(err), _stream(stream)))
+
+
+def tm_launch_count():
+    return int(_lib.tm_launch_count())
+
+
+def tm_trace_enable(on):
+    _lib.tm_trace_enable(int(bool(on)))
+
+
+def tm_trace_reset():
+    _lib.tm_trace_reset()
+
+
+def tm_trace_read(name="dslash"):
+    n = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(_lib.tm_trace_read(name.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value

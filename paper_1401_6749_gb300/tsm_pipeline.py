@@ -1,0 +1,107 @@
+"""The Truncated Solver Method loop pipeline (Sec. 2.1, Eq. 4) over the C ABI.
+
+Orchestration only: every arithmetic step is a libtmloops kernel.
+
+For sources r = first .. first + N_HP + N_LP - 1 (Z4, Sec. 2):
+  * low-precision (LP) solves of all N_HP + N_LP sources, PLAIN CG in F16/BF16
+    truncated at |r|/|b| = tol_lp, in batches of `batch` right-hand sides;
+  * high-precision (HP) solves of the first N_HP sources, MIXED CG (FP64
+    reliable updates) to tol_hp;
+  * for every solution s: local and one-derivative loops with the one-end
+    trick (L = R = s, P = g5, Eq. 5) and its generalisation (L = s,
+    R = g5 D_W s, P = g5, Eq. 6);
+  * TSM combination with prefactor -2 i nu (one-end) and 2 (generalised).
+The LP solve of a source is the same function of the source in every batch
+(per-system arithmetic, fixed-order reductions), so the correction term of
+Eq. 4 is unbiased.
+"""
+import torch
+
+from . import tmloops as tl
+
+KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
+
+
+class TsmPipeline:
+    def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
+                 tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=8,
+                 delta=0.1, kinds=KINDS):
+        self.op = op
+        self.L = op.L
+        self.T = op.L[3]
+        self.n_hp, self.n_lp = int(n_hp), int(n_lp)
+        self.batch = int(batch)
+        self.lp_prec, self.hp_inner = lp_prec, hp_inner
+        self.tol_lp, self.tol_hp = tol_lp, tol_hp
+        self.seed, self.first = int(seed), int(first_src)
+        self.max_iter, self.check_every, self.delta = max_iter, check_every, delta
+        self.kinds = tuple(kinds)
+        self.nu = 2.0 * op.kappa * op.mu
+        n_all = self.n_hp + self.n_lp
+        self.len = {"local": 16 * self.T, "oneD": 64 * self.T}
+        dev = "cuda"
+        # per-source loop arrays (complex as re/im doubles)
+        self.lp_loops = {k: torch.empty((n_all, self.len[k.split("_")[0]] * 2), dtype=torch.float64,
+                                        device=dev) for k in self.kinds}
+        self.hp_loops = {k: torch.empty((max(self.n_hp, 1), self.len[k.split("_")[0]] * 2),
+                                        dtype=torch.float64, device=dev) for k in self.kinds}
+        b = min(self.batch, n_all)
+        self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(4)]  # eta, x, D_W x, g5 D_W x
+        nh = max(min(self.batch, self.n_hp), 1)
+        self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(4)] if self.n_hp else None
+        self.stats_lp, self.stats_hp = [], []
+
+    def _contract(self, x, w, g5w, prec, n, dst, row0):
+        for k in self.kinds:
+            kind, mode = k.split("_")
+            left, right = (x, x) if mode == "vv" else (x, g5w)
+            out = dst[k][row0:row0 + n]
+            if kind == "local":
+                tl.loop_contract_local(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out)
+            else:
+                tl.loop_contract_oneD(self.op, left, right, prec, n, tl.LOOP_MODE[mode], out)
+
+    def _solve_and_contract(self, fields, prec, first, n, params, dst, row0):
+        eta, x, w, g5w = fields
+        tl.z4_noise(self.L, eta, prec, self.seed, first, n)
+        st, stats = tl.tm_cg_solve(self.op, x, eta, n, params, raise_on_noconv=False)
+        if any("gen" in k for k in self.kinds):
+            tl.tm_dslash(self.op, w, x, n, mu_zero=True, prec=prec)
+            tl.tm_gamma5(self.L, g5w, w, prec, n)
+        self._contract(x, w, g5w, prec, n, dst, row0)
+        return stats
+
+    def run(self):
+        """One full TSM estimate; returns per-kind (mean, err) device tensors."""
+        n_all = self.n_hp + self.n_lp
+        self.stats_lp, self.stats_hp = [], []
+        lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
+                                 check_every=self.check_every)
+        for b0 in range(0, n_all, self.batch):
+            n = min(self.batch, n_all - b0)
+            self.stats_lp += self._solve_and_contract(self._lp, self.lp_prec, self.first + b0, n,
+                                                      lp_params, self.lp_loops, b0)
+        if self.n_hp:
+            hp_params = tl.cg_params(self.tol_hp, self.max_iter, tl.CG_MIXED, inner_prec=self.hp_inner,
+                                     delta=self.delta, check_every=self.check_every)
+            for b0 in range(0, self.n_hp, self.batch):
+                n = min(self.batch, self.n_hp - b0)
+                self.stats_hp += self._solve_and_contract(self._hp, tl.F64, self.first + b0, n,
+                                                          hp_params, self.hp_loops, b0)
+        return self.combine()
+
+    def combine(self):
+        res = {}
+        for k in self.kinds:
+            length = self.len[k.split("_")[0]]
+            scale = -2j * self.nu if k.endswith("vv") else 2.0
+            mean = torch.empty(2 * length, dtype=torch.float64, device="cuda")
+            err = torch.empty(2 * length, dtype=torch.float64, device="cuda")
+            lp = self.lp_loops[k]
+            if self.n_hp:
+                tl.tsm_combine(self.hp_loops[k][:self.n_hp], lp[:self.n_hp], self.n_hp,
+                               lp[self.n_hp:], self.n_lp, length, scale, mean, err)
+            else:
+                tl.tsm_combine(None, None, 0, lp, self.n_lp, length, scale, mean, err)
+            res[k] = (mean, err)
+        return res
