@@ -180,6 +180,26 @@ tm_status_t loop_contract_oneD(tm_op_t *op, const void *left, const void *right,
                                tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
                                double *out, tm_stream_t s);
 
+/* Same computation and result as loop_contract_local, for callers that cannot
+ * allocate device memory: e.g. an application whose own memory manager has
+ * reserved the GPU's memory up front, or a tight loop that must not pay for an
+ * allocation on every call.  This call allocates nothing (no cudaMalloc,
+ * cudaMallocAsync, cudaFree or allocating library routine).  Its reduction
+ * scratch is a fixed array of 2^20 doubles (8 MiB) inside the library, which
+ * every GPU that loads the library holds until the process exits; sizes that
+ * need more, i.e. 64 * nrhs * T * ceil(X*Y*Z/2048) > 2^20 doubles (e.g. more
+ * than 16 right-hand sides at 32^3 x 64), are rejected with TM_ERR_ARG before
+ * any launch.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels may overlap on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  The paper has no
+ * counterpart to this entry point; it exists for the allocation constraint
+ * only.  Arguments, layouts and errors as for loop_contract_local.         */
+tm_status_t loop_contract_local_noalloc(const tm_geom_t *g, const void *left, const void *right,
+                                        tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                        double *out, tm_stream_t s);
+
 /* Truncated Solver Method combination (Sec. 2.1, Eq. 4), per component j:
  *   mean_j = (1/N_HP) sum_{i<N_HP} c (l_hp - l_lp_on_hp)_ij + (1/N_LP) sum_i c (l_lp)_ij
  *   err_j^2 = Var_i(c (l_hp - l_lp_on_hp))/N_HP + Var_i(c l_lp)/N_LP,

@@ -71,6 +71,7 @@ _SIGS = {
     "tm_cg_solve": [_vp, _vp, _vp, _i, _P(tm_cg_params_t), _P(tm_cg_stats_t), _vp],
     "loop_contract_local": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
     "loop_contract_oneD": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp],
+    "loop_contract_local_noalloc": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
     "tsm_combine": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp, _vp],
     "tm_last_error": [],
     "tm_launch_count": [],
@@ -201,6 +202,13 @@ def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
 def loop_contract_local(L, left, right, prec, nrhs, mode, out, stream=None):
     _check(_lib.loop_contract_local(ctypes.byref(geom(L)), _ptr(left), _ptr(right), int(prec),
                                     int(nrhs), int(mode), _ptr(out), _stream(stream)))
+
+
+def loop_contract_local_noalloc(L, left, right, prec, nrhs, mode, out, stream=None):
+    """loop_contract_local without device allocation (fixed 8 MiB scratch in the
+    library; calls that overlap on the GPU race)."""
+    _check(_lib.loop_contract_local_noalloc(ctypes.byref(geom(L)), _ptr(left), _ptr(right), int(prec),
+                                            int(nrhs), int(mode), _ptr(out), _stream(stream)))
 
 
 def loop_contract_oneD(op, left, right, prec, nrhs, mode, out, stream=None):
