@@ -387,6 +387,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- standalone Dslash
+def run_dslash(args):
+    """Time tm_dslash alone: M applied to nrhs Z4 fields (seed 7), the
+    per-launch time averaged over --steps launches after --warmup launches.
+    Algorithmic bytes per launch: nrhs x (in + out spinor) + the links once."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_6749_gb300 import synth
+    from paper_1401_6749_gb300 import tmloops as tl
+    L = tuple(int(v) for v in args.lattice.split(","))
+    prec = tl.PREC[args.prec]
+    n = args.nrhs
+    V = int(np.prod(L))
+    U = synth.gauge_field(L, 1234, device="cuda")
+    op = tl.Operator(L, 0.161, 0.003, torch.from_numpy(U.view(np.float64)).cuda(), recon=args.recon)
+    del U
+    fin = tl.empty_field(L, prec, n)
+    fout = tl.empty_field(L, prec, n)
+    tl.z4_noise(L, fin, prec, 7, 0, n)
+    for _ in range(args.warmup):
+        tl.tm_dslash(op, fout, fin, n, prec=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        tl.tm_dslash(op, fout, fin, n, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    esz = tl.ELEM_SIZE[prec]
+    link_reals = 18 if (prec == tl.F64 or args.recon == 18) else 12
+    nbytes = n * 2 * 24 * esz * V + 4 * link_reals * esz * V
+    peak, src = _peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    print(json.dumps({"mode": "dslash", "lattice": list(L), "nrhs": n, "prec": args.prec,
+                      "recon": link_reals, "ms_per_launch": round(ms, 4), "bytes_per_launch": nbytes,
+                      "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "peak_source": src,
+                      "l2": "in+out fields %.0f MB" % (2 * n * 24 * esz * V / 1e6)}), flush=True)
+    op.close()
+
+
 # ----------------------------------------------------------------- oracle
 def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
     """Time the FP64 oracle, as it stands, on a bounded sample: one M^dag M
@@ -461,8 +504,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-lp-iters", type=float, default=7)
     ap.add_argument("--ref-hp-iters", type=float, default=60)
+    ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
+    ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--recon", type=int, default=12)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.dslash:
+        run_dslash(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
