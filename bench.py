@@ -30,11 +30,11 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126),
+                  seed=20140126, schur=True, delta=0.001, recon=18),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126),
+                 seed=20140126, schur=True, delta=0.001, recon=18),
 }
 
 PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -44,9 +44,10 @@ METRIC = "Dslash HBM GB/s and % roofline; TSM loop sec/source at fixed error vs 
 def workload_name(c):
     X, Y, Z, T = c["L"]
     return ("TSM loops %dx%dx%dx%d kappa=%g mu=%g: %d LP (%s, |r|<=%g) + %d HP (mixed %s/FP64, "
-            "|r|<=%g), batches of %d, local+oneD x (one-end, generalised one-end)" % (
+            "|r|<=%g, delta=%g), batches of %d, %s CG, local+oneD x (one-end, generalised one-end)" % (
                 X, Y, Z, T, c["kappa"], c["mu"], c["n_lp"] + c["n_hp"], c["lp_prec"], c["tol_lp"],
-                c["n_hp"], c["hp_inner"], c["tol_hp"], c["batch"]))
+                c["n_hp"], c["hp_inner"], c["tol_hp"], c["delta"], c["batch"],
+                "even/odd-preconditioned" if c["schur"] else "unpreconditioned"))
 
 
 def _peaks():
@@ -138,37 +139,6 @@ def _barrier(dist):
         dist.barrier()
 
 
-def _lp_bytes(c, stats_lp, launches, V):
-    """Algorithmic bytes of the LP-precision Dslash classes of one step.
-
-    Every array is counted once per launch: a spinor stream is 24 reals per
-    site and right-hand side, the links 4 x 12 reals per site per launch.
-    out class:   b = M^dag eta and D_W s (2 streams, all systems) + t = M p
-                 (2 streams per active system and iteration);
-    cgupd class: t in, r in/out, x in/out, p in (6 streams per active system
-                 and iteration)."""
-    e = PREC_BYTES[c["lp_prec"]]
-    spin = 24 * e * V
-    link = 48 * e * V
-    iters = sum(s["iters"] for s in stats_lp)
-    n = len(stats_lp)
-    out_b = (2 * n + iters) * 2 * spin + launches["out"] * link
-    cg_b = iters * 6 * spin + launches["cgupd"] * link
-    return out_b, cg_b
-
-
-def _effective_launches(c, stats_lp):
-    """Launches that had at least one active system (masked-out tail launches of
-    a batch do no work and are not credited with link traffic)."""
-    nb = c["batch"]
-    out = cg = 0
-    for b0 in range(0, len(stats_lp), nb):
-        m = max(s["iters"] for s in stats_lp[b0:b0 + nb])
-        out += 2 + m
-        cg += m
-    return {"out": out, "cgupd": cg}
-
-
 def _observables(pipe, c):
     """Per-source values of three volume-summed loops (sigma-term, g_A and
     Fig. 1 operator analogues) for the HP and LP sets, on the host."""
@@ -224,11 +194,12 @@ def run_ours(args):
     U_host = torch.from_numpy(U.view(np.float64)).pin_memory()
     U_dev = U_host.cuda()
     del U
-    op = tl.Operator(L, c["kappa"], c["mu"], U_dev, recon=12)
+    op = tl.Operator(L, c["kappa"], c["mu"], U_dev, recon=c["recon"])
     n_src = c["n_hp"] + c["n_lp"]
     mk = lambda o: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
                                hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
-                               seed=c["seed"], first_src=rank * n_src)
+                               seed=c["seed"], first_src=rank * n_src, schur=c["schur"],
+                               delta=c["delta"])
     pipe = mk(op)
     _log("inputs ready")
     for _ in range(args.warmup):
@@ -259,29 +230,25 @@ def run_ours(args):
     classes = {}
     for prec in ("f64", "f32", "f16", "bf16"):
         for epi in ("out", "cgupd", "resid"):
-            n, tms = tl.tm_trace_read("dslash.%s.%s" % (prec, epi))
+            n, tms, nbytes = tl.tm_trace_read("dslash.%s.%s" % (prec, epi))
             if n:
-                classes["dslash.%s.%s" % (prec, epi)] = (n // args.steps, tms / args.steps)
+                classes["dslash.%s.%s" % (prec, epi)] = (n / args.steps, tms / args.steps,
+                                                          nbytes / args.steps)
     tl.tm_trace_reset()
     ms = _max_over_ranks(dist, ms)
     _log("timed: %.3f ms/step, %d launches/step, classes %s" % (ms, launches, classes))
 
-    # ---- roofline of the dominant Dslash class (by device time)
+    # ---- roofline of the dominant Dslash class (by device time): algorithmic
+    # bytes recorded per launch by the library (active systems only), device
+    # time from CUDA events on the launch stream
     peak, peak_src = _peaks()
-    eff = _effective_launches(c, pipe.stats_lp)
-    out_b, cg_b = _lp_bytes(c, pipe.stats_lp, eff, V)
-    lp = c["lp_prec"]
     kernels = {}
-    for name, (n, tms) in classes.items():
-        entry = {"launches": n, "ms": round(tms, 3), "share_of_step": round(tms / ms, 4)}
-        if name == "dslash.%s.out" % lp:
-            entry["GBps"] = round(out_b / (tms * 1e-3) / 1e9, 1)
-        if name == "dslash.%s.cgupd" % lp:
-            entry["GBps"] = round(cg_b / (tms * 1e-3) / 1e9, 1)
-        kernels[name] = entry
-    dom = max((k for k in kernels if "GBps" in kernels[k]), key=lambda k: kernels[k]["ms"])
+    for name, (n, tms, nbytes) in classes.items():
+        kernels[name] = {"launches": round(n, 1), "ms": round(tms, 3), "share_of_step": round(tms / ms, 4),
+                         "GBps": round(nbytes / (tms * 1e-3) / 1e9, 1) if tms > 0 else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    n_dom, t_dom, b_dom = classes[dom]
     ach = kernels[dom]["GBps"]
-    n_dom, _ = classes[dom]
     traffic_path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
     traffic = None
     if os.path.exists(traffic_path):
@@ -291,8 +258,7 @@ def run_ours(args):
             traffic = tj.get("bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic, "kernel": dom,
-                "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": round((cg_b if dom.endswith("cgupd") else out_b) / n_dom)}
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": round(b_dom / n_dom)}
 
     # ---- correctness/quality summary of the last step
     it_lp = [s["iters"] for s in pipe.stats_lp]
@@ -311,7 +277,8 @@ def run_ours(args):
         T = L[3]
         loc = torch.empty(32 * T, dtype=torch.float64, device="cuda")
         oned = torch.empty(128 * T, dtype=torch.float64, device="cuda")
-        prm = tl.cg_params(c["tol_hp"], 20000, tl.CG_PLAIN, prec=tl.F64, check_every=8)
+        prm = tl.cg_params(c["tol_hp"], 20000, tl.CG_PLAIN, prec=tl.F64, check_every=8,
+                           schur=c["schur"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for j in range(n_plain):
@@ -339,7 +306,7 @@ def run_ours(args):
         e0.record()
         for _ in range(args.steps):
             Ud = U_host.to("cuda", non_blocking=True)
-            op2 = tl.Operator(L, c["kappa"], c["mu"], Ud, recon=12)
+            op2 = tl.Operator(L, c["kappa"], c["mu"], Ud, recon=c["recon"])
             p2 = mk(op2)
             r2 = p2.run()
             for h, (m, e) in zip(host_out, r2.values()):
@@ -504,12 +471,29 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-lp-iters", type=float, default=7)
     ap.add_argument("--ref-hp-iters", type=float, default=60)
+    ap.add_argument("--schur", type=int, default=None, help="override even/odd preconditioning")
+    ap.add_argument("--delta", type=float, default=None, help="override the reliable-update delta")
+    ap.add_argument("--recon", type=int, default=None, choices=[12, 18])
+    ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
+    ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16"])
-    ap.add_argument("--recon", type=int, default=12)
     args = ap.parse_args()
+    c = CONFIGS[args.config]
+    if args.schur is not None:
+        c["schur"] = bool(args.schur)
+    if args.delta is not None:
+        c["delta"] = args.delta
+    if args.recon is not None:
+        c["recon"] = args.recon
+    else:
+        args.recon = 12 if args.dslash else c["recon"]
+    if args.lp_prec is not None:
+        c["lp_prec"] = args.lp_prec
+    if args.hp_inner is not None:
+        c["hp_inner"] = args.hp_inner
     if args.dslash:
         run_dslash(args)
     elif args.impl == "reference":

@@ -129,6 +129,12 @@ tm_status_t z4_noise(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t see
  *   inner_prec; reliable updates (x += y, r = b - M^dag M x in F64) whenever
  *   |r| < delta * max|r| since the last update, and before accepting
  *   convergence.  eta and x are then F64 internal fields.
+ * schur = 1: even/odd preconditioning (the paper does not say whether it was
+ *   used).  With A = 1 + i nu g5 (the even-even and odd-odd blocks of M),
+ *   CG runs on M_hat^dag M_hat x_o = M_hat^dag eta_hat on the odd sites,
+ *   M_hat = A - kappa^2 H_oe A^-1 H_eo, eta_hat = eta_o + kappa H_oe A^-1 eta_e,
+ *   and s_e = A^-1 (eta_e + kappa H_eo s_o) completes x = M^-1 eta; tol,
+ *   rel_res and true_res then refer to this odd-site system.
  * nrhs independent systems are solved together; each has its own scalars and
  * stops on its own.  stats (host array of nrhs, may be NULL) receives per-system
  * results.  Blocks the calling thread until all systems have stopped.
@@ -145,6 +151,7 @@ typedef struct {
   double delta;          /* MIXED: reliable-update threshold (e.g. 0.1)     */
   int check_every;       /* host polls the convergence flags every N iterations (>= 1) */
   int true_residual;     /* PLAIN: compute |b - M^dag M x| / |b| at the end */
+  int schur;             /* 1: even/odd preconditioned solve (see below), 0: plain M */
 } tm_cg_params_t;
 
 typedef struct {
@@ -214,15 +221,18 @@ tm_status_t tsm_combine(const double *l_hp, const double *l_lp_on_hp, int n_hp,
 /* Diagnostics.  tm_last_error: thread-local text of the last failure.
  * tm_launch_count: kernels this library launched so far (all threads).
  * tm_trace_enable(1): bracket every Dslash launch with CUDA events on its
- * stream; tm_trace_read returns the launches and summed device milliseconds
- * since the last reset for a kernel class "dslash.<f64|f32|f16|bf16>.<out|
- * cgupd|resid>" (exact name, or a prefix ending in '*', e.g. "dslash.f16.*"),
- * after synchronising the recorded events.                                */
+ * stream and record its algorithmic bytes (every array once: per active
+ * system the neighbour, centre and epilogue fields of the output sites, per
+ * launch the links of all sites); the kernel itself records how many systems
+ * were active.  tm_trace_read returns, since the last reset, the launches,
+ * summed device milliseconds and summed algorithmic bytes of a kernel class
+ * "dslash.<f64|f32|f16|bf16>.<out|cgupd|resid>" (exact name, or a prefix
+ * ending in '*', e.g. "dslash.f16.*"); it synchronises the device.        */
 const char *tm_last_error(void);
 uint64_t tm_launch_count(void);
 void tm_trace_enable(int on);
 void tm_trace_reset(void);
-tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms);
+tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms, double *total_bytes);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -55,26 +56,46 @@ tm_status_t check_geom(const int L[4]) {
 struct TraceRec {
   std::string name;
   cudaEvent_t a, b;
+  int slot;
+  double bytes_per_rhs, fixed_bytes;
 };
 static std::mutex g_trace_mu;
 static std::atomic<int> g_trace_on{0};
 static std::vector<TraceRec> g_trace;
+static int* g_trace_counts = nullptr;  // device: active systems per traced launch
+static int g_trace_next = 0;
+constexpr int kTraceSlots = 1 << 20;
 
-void trace_begin(cudaStream_t s, const char* name, cudaEvent_t* ev0) {
+int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
   *ev0 = nullptr;
-  if (!g_trace_on.load(std::memory_order_relaxed)) return;
-  (void)name;
-  if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return; }
+  if (!g_trace_on.load(std::memory_order_relaxed)) return nullptr;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (!g_trace_counts || g_trace_next >= kTraceSlots) return nullptr;
+  if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return nullptr; }
   cudaEventRecord(*ev0, s);
+  return g_trace_counts + g_trace_next;
 }
 
-void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0) {
+void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
+               double fixed_bytes) {
   if (!ev0) return;
   cudaEvent_t ev1;
   if (cudaEventCreate(&ev1) != cudaSuccess) { cudaEventDestroy(ev0); return; }
   cudaEventRecord(ev1, s);
   std::lock_guard<std::mutex> lk(g_trace_mu);
-  g_trace.push_back({name, ev0, ev1});
+  g_trace.push_back({name, ev0, ev1, (int)(slot - g_trace_counts), bytes_per_rhs, fixed_bytes});
+  ++g_trace_next;
+}
+
+// Systems per thread of the FP32/FP16/BF16 Dslash: TM_DSLASH_NR = 1, 2 or 4
+// overrides the built-in choice (a tuning knob; results do not depend on it).
+int dslash_nr_override() {
+  static const int v = [] {
+    const char* e = getenv("TM_DSLASH_NR");
+    const int n = e ? atoi(e) : 0;
+    return (n == 1 || n == 2 || n == 4) ? n : 0;
+  }();
+  return v;
 }
 
 // ------------------------------------------------------------ dispatch
@@ -101,7 +122,18 @@ using namespace tml;
 extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
 extern "C" uint64_t tm_launch_count(void) { return g_launches.load(); }
 
-extern "C" void tm_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
+extern "C" void tm_trace_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (on && !g_trace_counts) {
+    if (cudaMalloc(&g_trace_counts, sizeof(int) * kTraceSlots) != cudaSuccess) {
+      cudaGetLastError();
+      g_trace_counts = nullptr;
+      set_error("tm_trace_enable: could not allocate the trace counters");
+      return;
+    }
+  }
+  g_trace_on.store(on ? 1 : 0);
+}
 
 extern "C" void tm_trace_reset(void) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
@@ -110,13 +142,23 @@ extern "C" void tm_trace_reset(void) {
     cudaEventDestroy(r.b);
   }
   g_trace.clear();
+  g_trace_next = 0;
 }
 
-extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* total_ms) {
-  if (!name || !launches || !total_ms) { set_error("tm_trace_read: null argument"); return TM_ERR_ARG; }
+extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* total_ms,
+                                     double* total_bytes) {
+  if (!name || !launches || !total_ms || !total_bytes) { set_error("tm_trace_read: null argument"); return TM_ERR_ARG; }
   std::lock_guard<std::mutex> lk(g_trace_mu);
+  std::vector<int> counts((size_t)g_trace_next);
+  if (g_trace_next > 0) {
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(counts.data(), g_trace_counts, sizeof(int) * counts.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_error("tm_trace_read: reading the trace counters failed");
+      return TM_ERR_CUDA;
+    }
+  }
   int n = 0;
-  double ms = 0.0;
+  double ms = 0.0, bytes = 0.0;
   // exact class name, or a prefix followed by '*'
   const std::string want(name);
   const bool prefix = !want.empty() && want.back() == '*';
@@ -127,10 +169,13 @@ extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* to
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { set_error("tm_trace_read: elapsed time failed"); return TM_ERR_CUDA; }
     ms += t;
+    const int act = (r.slot >= 0 && r.slot < (int)counts.size()) ? counts[r.slot] : 0;
+    bytes += act > 0 ? act * r.bytes_per_rhs + r.fixed_bytes : 0.0;
     ++n;
   }
   *launches = n;
   *total_ms = ms;
+  *total_bytes = bytes;
   return TM_OK;
 }
 

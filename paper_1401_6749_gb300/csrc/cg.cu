@@ -16,6 +16,15 @@
 // its value at the last update (or the tolerance is reached), x += y in FP64,
 // r = b - M^dag M x is recomputed in FP64 and the iteration continues from it.
 // Convergence is only accepted on such a true residual.
+//
+// With schur = 1 the solve is even/odd preconditioned: with A = 1 + i nu g5 the
+// diagonal blocks of M are M_ee = M_oo = A, and M s = eta is solved through
+//   eta_hat_o = eta_o + kappa H_oe A^-1 eta_e,
+//   M_hat s_o = eta_hat_o,   M_hat = A - kappa^2 H_oe A^-1 H_eo   (CG on M_hat^dag M_hat),
+//   s_e = A^-1 (eta_e + kappa H_eo s_o),
+// with M_hat^dag = A(-nu) - kappa^2 (H^dag)_oe A(-nu)^-1 (H^dag)_eo.  The CG vectors
+// live on the odd sites; the even half of the vector an operator is applied to
+// holds the intermediate A^-1 H_eo v.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -25,11 +34,79 @@
 namespace tml {
 
 tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
-                 const int* active, int nrhs, cudaStream_t s);
+                 const int* active, int nrhs, int par0, int npar, cudaStream_t s);
 tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
-                 const int* mask, int nrhs, cudaStream_t s);
+                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s);
 tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
-                    void* p, const double* ratio, const int* mask, int nrhs, cudaStream_t s);
+                    void* p, const double* ratio, const int* mask, int nrhs, int par0, int npar,
+                    cudaStream_t s);
+tm_status_t twist(const Geom& g, tm_prec_t prec, void* out, const void* in, double nu, int inverse,
+                  int par, int nrhs, cudaStream_t s);
+
+// The operator of the solve: M (both parities) or the odd-site Schur complement.
+struct SolveOp {
+  tm_op* op;
+  bool schur;
+  int nrhs;
+  cudaStream_t s;
+  double nu() const { return 2.0 * op->kappa * op->mu; }
+
+  // t = Op v (+ |t|^2 partials); for the Schur operator v's even half is scratch
+  tm_status_t apply(tm_prec_t prec, void* v, void* t, double* partial, const int* active) const {
+    if (!schur) {
+      DslashCall c;
+      c.in = v; c.out = t; c.nrhs = nrhs; c.partial = partial; c.active = active;
+      return dslash_dispatch(op, prec, c, s);
+    }
+    DslashCall c1;  // v_e = A^-1 H_eo v_o
+    c1.custom = true; c1.in = v; c1.out = v; c1.nrhs = nrhs; c1.active = active;
+    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = nu();
+    const tm_status_t st = dslash_dispatch(op, prec, c1, s);
+    if (st != TM_OK) return st;
+    DslashCall c2;  // t_o = A v_o - kappa^2 H_oe v_e
+    c2.custom = true; c2.in = v; c2.cfield = v; c2.out = t; c2.nrhs = nrhs; c2.active = active;
+    c2.parity = 1; c2.centre = 2; c2.hop_scale = -op->kappa * op->kappa; c2.nu = nu();
+    c2.partial = partial;
+    return dslash_dispatch(op, prec, c2, s);
+  }
+
+  // Op^dag t with the epilogue of `e` (EPI_OUT into e.out, EPI_CGUPD, EPI_RESID);
+  // for the Schur operator t's even half is scratch
+  tm_status_t apply_dag(tm_prec_t prec, void* t, DslashCall e) const {
+    e.nrhs = nrhs;
+    e.dagger = true;
+    if (!schur) {
+      e.in = t;
+      return dslash_dispatch(op, prec, e, s);
+    }
+    DslashCall c1;  // t_e = A(-nu)^-1 (H^dag)_eo t_o
+    c1.custom = true; c1.dagger = true; c1.in = t; c1.out = t; c1.nrhs = nrhs; c1.active = e.active;
+    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = -nu();
+    const tm_status_t st = dslash_dispatch(op, prec, c1, s);
+    if (st != TM_OK) return st;
+    e.custom = true; e.in = t; e.cfield = t; e.parity = 1; e.centre = 2;
+    e.hop_scale = -op->kappa * op->kappa; e.nu = -nu();
+    return dslash_dispatch(op, prec, e, s);
+  }
+
+  // eta_hat_o = eta_o + kappa H_oe A^-1 eta_e into dst (odd half; even half scratch)
+  tm_status_t prepare(tm_prec_t prec, const void* eta, void* dst) const {
+    tm_status_t st = twist(op->g, prec, dst, eta, nu(), 1, 0, nrhs, s);
+    if (st != TM_OK) return st;
+    DslashCall c;
+    c.custom = true; c.in = dst; c.cfield = eta; c.out = dst; c.nrhs = nrhs;
+    c.parity = 1; c.centre = 1; c.hop_scale = op->kappa; c.nu = nu();
+    return dslash_dispatch(op, prec, c, s);
+  }
+
+  // x_e = A^-1 (eta_e + kappa H_eo x_o)
+  tm_status_t reconstruct(tm_prec_t prec, const void* eta, void* x) const {
+    DslashCall c;
+    c.custom = true; c.in = x; c.cfield = eta; c.out = x; c.nrhs = nrhs;
+    c.parity = 0; c.centre = 1; c.hop_scale = op->kappa; c.out_inv = true; c.nu = nu();
+    return dslash_dispatch(op, prec, c, s);
+  }
+};
 
 // per-system device state (structure of arrays)
 struct CgState {
@@ -251,11 +328,16 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   const bool mixed = prm->mode == TM_CG_MIXED;
   if (prm->mode != TM_CG_PLAIN && !mixed) { set_error("tm_cg_solve: unknown mode %d", (int)prm->mode); return TM_ERR_ARG; }
   if (mixed && !(prm->delta > 0.0 && prm->delta < 1.0)) { set_error("tm_cg_solve: delta must be in (0, 1)"); return TM_ERR_ARG; }
+  if (prm->schur != 0 && prm->schur != 1) { set_error("tm_cg_solve: schur must be 0 or 1"); return TM_ERR_ARG; }
   const tm_prec_t lo = mixed ? prm->inner_prec : prm->prec;
   if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: unknown precision"); return TM_ERR_ARG; }
   if (nrhs == 0) return TM_OK;
   const cudaStream_t s = (cudaStream_t)strm;
   const Geom& g = op->g;
+  const bool schur = prm->schur == 1;
+  const SolveOp A{op, schur, nrhs, s};
+  // the CG vectors cover both parities, or only the odd one (Schur)
+  const int par0 = schur ? 1 : 0, npar = schur ? 1 : 2;
   const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
   const size_t F = tm_spinor_bytes(&gg, lo, nrhs);
   const size_t F64 = tm_spinor_bytes(&gg, TM_PREC_F64, nrhs);
@@ -294,25 +376,44 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   CgScalars sc;
   sc.tol2 = prm->tol * prm->tol;
   sc.delta2 = mixed ? prm->delta * prm->delta : 0.0;
-  sc.n12 = 24.0 * (double)g.Vh;
+  sc.n12 = 12.0 * (double)g.Vh * npar;
   sc.max_iter = prm->max_iter;
   sc.nrhs = nrhs;
   sc.mixed = mixed ? 1 : 0;
-  const int nper = 2 * nwarp;
+  // reductions over the parities the vectors live on
+  const double* part0 = partial + (schur ? nwarp : 0);
+  const int nper = npar * nwarp;
+  const size_t pstride = 2 * (size_t)nwarp;
+  auto reduce = [&]() { return reduce_partials(part0, nper, nrhs, st.red, s, pstride); };
   const tm_prec_t hi = mixed ? TM_PREC_F64 : lo;
   void* xs = mixed ? y : x;          // iterate of the inner CG
-  void* bb_field = mixed ? b64 : b;  // right-hand side M^dag eta
+  void* bb_field = mixed ? b64 : b;  // right-hand side Op^dag eta(_hat)
+  void* scratch_hi = mixed ? tmp64 : t;
 
-  // b = M^dag eta, |b|^2
+  // b = Op^dag eta (Schur: Op^dag eta_hat), |b|^2
   {
-    DslashCall c;
-    c.in = eta; c.out = bb_field; c.nrhs = nrhs; c.dagger = true; c.partial = partial;
-    TM_TRY(dslash_dispatch(op, hi, c, s));
-    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    const void* src = eta;
+    if (schur) {
+      TM_TRY(A.prepare(hi, eta, scratch_hi));
+      src = scratch_hi;
+    } else if (eta != scratch_hi) {
+      src = eta;
+    }
+    DslashCall e;
+    e.out = bb_field; e.partial = partial;
+    if (schur) {
+      TM_TRY(A.apply_dag(hi, scratch_hi, e));
+    } else {
+      e.in = src;
+      e.nrhs = nrhs;
+      e.dagger = true;
+      TM_TRY(dslash_dispatch(op, hi, e, s));
+    }
+    TM_TRY(reduce());
     TM_TRY(scalar_launch(cg_init_kernel, st, sc, s));
   }
   if (mixed) {
-    TM_TRY(rescale(g, lo, r, b64, st.sigma, nullptr, nullptr, nullptr, nrhs, s));
+    TM_TRY(rescale(g, lo, r, b64, st.sigma, nullptr, nullptr, nullptr, nrhs, par0, npar, s));
     TM_TRY(memset_d(x, F64, s));
     TM_TRY(memset_d(y, F, s));
   } else {
@@ -324,34 +425,30 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   const int check_every = prm->check_every > 0 ? prm->check_every : 1;
   int* hflags = op->host_flags;
   for (int it = 0; it < prm->max_iter; ++it) {
-    DslashCall c1;
-    c1.in = p; c1.out = t; c1.nrhs = nrhs; c1.partial = partial; c1.active = st.active;
-    TM_TRY(dslash_dispatch(op, lo, c1, s));
-    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    TM_TRY(A.apply(lo, p, t, partial, st.active));  // t = Op p, |t|^2
+    TM_TRY(reduce());
     TM_TRY(scalar_launch(cg_alpha_kernel, st, sc, s));
-    DslashCall c2;
-    c2.in = t; c2.nrhs = nrhs; c2.dagger = true; c2.epi = EPI_CGUPD; c2.partial = partial;
-    c2.active = st.active; c2.alpha = st.alpha; c2.p = p; c2.x = xs; c2.r = r;
-    TM_TRY(dslash_dispatch(op, lo, c2, s));
-    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+    DslashCall e;  // r -= alpha Op^dag t, x += alpha p, |r|^2
+    e.epi = EPI_CGUPD; e.partial = partial; e.active = st.active; e.alpha = st.alpha;
+    e.p = p; e.x = xs; e.r = r;
+    TM_TRY(A.apply_dag(lo, t, e));
+    TM_TRY(reduce());
     if (!mixed) {
       TM_TRY(scalar_launch(cg_beta_plain_kernel, st, sc, s));
     } else {
       TM_TRY(scalar_launch(cg_beta_mixed_kernel, st, sc, s));
-      // reliable update for the systems that asked for one
-      TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, s));
-      DslashCall c3;
-      c3.in = x; c3.out = tmp64; c3.nrhs = nrhs; c3.active = st.ru;
-      TM_TRY(dslash_dispatch(op, TM_PREC_F64, c3, s));
-      DslashCall c4;
-      c4.in = tmp64; c4.out = r64; c4.b = b64; c4.nrhs = nrhs; c4.dagger = true;
-      c4.epi = EPI_RESID; c4.partial = partial; c4.active = st.ru;
-      TM_TRY(dslash_dispatch(op, TM_PREC_F64, c4, s));
-      TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
+      // reliable update for the systems that asked for one: x += sigma y,
+      // r = b - Op^dag Op x in FP64
+      TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, par0, npar, s));
+      TM_TRY(A.apply(TM_PREC_F64, x, tmp64, nullptr, st.ru));
+      DslashCall e4;
+      e4.out = r64; e4.b = b64; e4.epi = EPI_RESID; e4.partial = partial; e4.active = st.ru;
+      TM_TRY(A.apply_dag(TM_PREC_F64, tmp64, e4));
+      TM_TRY(reduce());
       TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
-      TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, s));
+      TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s));
     }
-    TM_TRY(xpay(g, lo, p, r, st.beta, st.active, nrhs, s));
+    TM_TRY(xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s));
     if ((it + 1) % check_every == 0 || it + 1 == prm->max_iter) {
       if (cudaMemcpyAsync(hflags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess) {
@@ -363,39 +460,49 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
       if (!any) break;
     }
   }
-  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, s));
+  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, par0, npar, s));
 
-  // true residual |b - M^dag M x| / |b|
-  const bool want_true = mixed || prm->true_residual;
+  std::vector<double> h_bb(nrhs), h_rr(nrhs), h_sig(nrhs);
+  std::vector<int> h_it(nrhs), h_nru(nrhs), h_status(nrhs);
+  auto fetch = [&]() -> bool {
+    bool ok = cudaMemcpyAsync(h_bb.data(), st.bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h_rr.data(), st.rr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h_sig.data(), st.sigma, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h_it.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h_nru.data(), st.nru, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h_status.data(), st.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    return ok && cudaStreamSynchronize(s) == cudaSuccess;
+  };
+  if (!fetch()) {
+    set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  // true residual |b - Op^dag Op x| / |b|: a mixed solve that converged already
+  // accepted it on such a residual (the last reliable update); otherwise, and
+  // for plain solves that ask for it, it is recomputed here
+  bool all_ok = true;
+  for (int i = 0; i < nrhs; ++i) all_ok = all_ok && h_status[i] == TM_OK;
+  const bool recompute = (mixed && !all_ok) || (!mixed && prm->true_residual);
   std::vector<double> h_true(nrhs, -1.0);
-  if (want_true) {
+  if (mixed && all_ok) {
+    for (int i = 0; i < nrhs; ++i) h_true[i] = h_rr[i] * h_sig[i] * h_sig[i];
+  }
+  if (recompute) {
     void* tmp = mixed ? tmp64 : t;
     void* res = mixed ? r64 : r;
-    DslashCall c3;
-    c3.in = x; c3.out = tmp; c3.nrhs = nrhs;
-    TM_TRY(dslash_dispatch(op, hi, c3, s));
-    DslashCall c4;
-    c4.in = tmp; c4.out = res; c4.b = bb_field; c4.nrhs = nrhs; c4.dagger = true;
-    c4.epi = EPI_RESID; c4.partial = partial;
-    TM_TRY(dslash_dispatch(op, hi, c4, s));
-    TM_TRY(reduce_partials(partial, nper, nrhs, st.red, s));
-    if (cudaMemcpyAsync(h_true.data(), st.red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    TM_TRY(A.apply(hi, x, tmp, nullptr, nullptr));
+    DslashCall e4;
+    e4.out = res; e4.b = bb_field; e4.epi = EPI_RESID; e4.partial = partial;
+    TM_TRY(A.apply_dag(hi, tmp, e4));
+    TM_TRY(reduce());
+    if (cudaMemcpyAsync(h_true.data(), st.red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
       return TM_ERR_CUDA;
     }
   }
-  std::vector<double> h_bb(nrhs), h_rr(nrhs);
-  std::vector<int> h_it(nrhs), h_nru(nrhs), h_status(nrhs);
-  bool ok = cudaMemcpyAsync(h_bb.data(), st.bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(h_rr.data(), st.rr, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(h_it.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(h_nru.data(), st.nru, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(h_status.data(), st.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
-  if (!ok) {
-    set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
-    return TM_ERR_CUDA;
-  }
+  if (schur) TM_TRY(A.reconstruct(hi, eta, x));
+  const bool want_true = mixed || prm->true_residual;
   tm_status_t worst = TM_OK;
   for (int i = 0; i < nrhs; ++i) {
     const double bbi = h_bb[i];
@@ -403,7 +510,7 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
       stats[i].iters = h_it[i];
       stats[i].reliable_updates = h_nru[i];
       stats[i].status = h_status[i];
-      stats[i].rel_res = bbi > 0 ? std::sqrt(h_rr[i] / bbi) : 0.0;
+      stats[i].rel_res = bbi > 0 ? std::sqrt(h_rr[i] * h_sig[i] * h_sig[i] / bbi) : 0.0;
       stats[i].true_res = want_true ? (bbi > 0 ? std::sqrt(h_true[i] / bbi) : 0.0) : -1.0;
     }
     if (h_status[i] == TM_ERR_NAN) worst = TM_ERR_NAN;

@@ -157,12 +157,49 @@ __global__ void local_final_kernel(const double* partial, int nchunk, int T, Gam
 }
 
 // ----------------------------------------------------- one-derivative loops
+// With A_mu(x) = Lb(x) G U_mu(x) R(x+mu) and B_mu(x) = Lb(x) G U_mu(x-mu)^dag R(x-mu)
+// the symmetric-derivative loop of slice t is
+//   spatial mu:  1/4 sum_{x_t=t} [A(x) + A(x-mu) - B(x) - B(x+mu)] = 1/2 sum_{x_t=t} (A - B)(x),
+//   mu = t:      1/4 [C(t) + C(t-1)],  C(t) = sum_{x_t=t} C(x),  C(x) = A(x) - B(x+t),
+// since x -> x +/- mu permutes a time slice for spatial mu, and A(x), B(x+t)
+// both live on the link (x, x+t).  So one 4x4 accumulator per direction:
+//   spatial: L^dag(x) [U_mu(x) R(x+mu) - U_mu(x-mu)^dag R(x-mu)]
+//   time:    L^dag(x) U_t(x) R(x+t) - L^dag(x+t) U_t(x)^dag R(x)   (boundary sign on both)
 constexpr int kOneDK = 4;           // sites per thread
 constexpr int kOneDLanes = 64;      // sites side by side in a block (x 4 directions)
 constexpr int kOneDChunk = kOneDLanes * kOneDK;
 
 __device__ __forceinline__ int sel4(const int (&a)[4], int mu) {
   return mu == 0 ? a[0] : mu == 1 ? a[1] : mu == 2 ? a[2] : a[3];
+}
+
+// w = U r (ADJ: U^dag r) for the 4 spins of a spinor; SUB: w -= (...) instead
+template <bool ADJ, bool SUB = false, class R>
+__device__ __forceinline__ void link_times(Cx<R> (&w)[12], const Mat3<R>& U, const Cx<R> (&r)[12]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<R> z = {0, 0};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) z = z + (ADJ ? cmulc(U.m[d][c], r[3 * a + d]) : U.m[c][d] * r[3 * a + d]);
+      w[3 * a + c] = SUB ? w[3 * a + c] - z : z;
+    }
+}
+
+// acc_{ab} += sgn * sum_c conj(l_{ac}) w_{bc}
+template <class R>
+__device__ __forceinline__ void outer_acc(R (&acc)[32], const Cx<R> (&l)[12], const Cx<R> (&w)[12], R sgn) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      Cx<R> m = {0, 0};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m = m + cmulc(l[3 * a + c], w[3 * b + c]);
+      acc[2 * (4 * a + b)] += sgn * m.re;
+      acc[2 * (4 * a + b) + 1] += sgn * m.im;
+    }
 }
 
 template <class S, int RECON>
@@ -176,9 +213,9 @@ __global__ void __launch_bounds__(256) oneD_partial_kernel(Geom g, const void* l
   const int mu = threadIdx.y;
   const int opar = par ^ 1;
   const size_t cs = (size_t)g.Vh;
-  R accA[32], accB[32];
+  R acc[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) accA[j] = accB[j] = 0;
+  for (int j = 0; j < 32; ++j) acc[j] = 0;
   const int Lmu = sel4(g.L, mu), smu = sel4(g.stride, mu);
 #pragma unroll 1
   for (int k = 0; k < kOneDK; ++k) {
@@ -188,107 +225,65 @@ __global__ void __launch_bounds__(256) oneD_partial_kernel(Geom g, const void* l
     const Site s = site_of(g, par, cb);
     const int cmu = sel4(s.c, mu);
     const int lf = cmu + 1 < Lmu ? s.lex + smu : s.lex - (Lmu - 1) * smu;
-    const int lb = cmu > 0 ? s.lex - smu : s.lex + (Lmu - 1) * smu;
-    R sf = 1, sb = 1;
-    if (mu == 3 && g.antiperiodic) {
-      if (cmu == Lmu - 1) sf = -1;
-      if (cmu == 0) sb = -1;
-    }
     Cx<R> l[12], r[12], w[12];
-    load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
-    // A: W = U_mu(x) R(x + mu)
-    load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
-    {
-      const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          Cx<R> z = {0, 0};
-#pragma unroll
-          for (int d = 0; d < 3; ++d) z = z + U.m[c][d] * r[3 * a + d];
-          w[3 * a + c] = sf * z;
-        }
+    const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
+    if (mu < 3) {
+      const int lb = cmu > 0 ? s.lex - smu : s.lex + (Lmu - 1) * smu;
+      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
+      link_times<false>(w, U, r);
+      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lb >> 1), cs);
+      const Mat3<R> Ub = load_link<S, RECON>(links, g, mu, opar, lb >> 1);
+      link_times<true, true>(w, Ub, r);
+      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
+      outer_acc(acc, l, w, (R)1);
+    } else {
+      const R sf = (g.antiperiodic && cmu == Lmu - 1) ? (R)-1 : (R)1;
+      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
+      link_times<false>(w, U, r);
+      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
+      outer_acc(acc, l, w, sf);
+      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, par, cb), cs);
+      link_times<true>(w, U, r);
+      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
+      outer_acc(acc, l, w, -sf);
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const Cx<R> m = cmulc(l[3 * a + c], w[3 * b + c]);
-          accA[2 * (4 * a + b)] += m.re;
-          accA[2 * (4 * a + b) + 1] += m.im;
-        }
-    // B: W = U_mu(x - mu)^dag R(x - mu)
-    load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lb >> 1), cs);
-    {
-      const Mat3<R> U = load_link<S, RECON>(links, g, mu, opar, lb >> 1);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          Cx<R> z = {0, 0};
-#pragma unroll
-          for (int d = 0; d < 3; ++d) z = z + cmulc(U.m[d][c], r[3 * a + d]);
-          w[3 * a + c] = sb * z;
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const Cx<R> m = cmulc(l[3 * a + c], w[3 * b + c]);
-          accB[2 * (4 * a + b)] += m.re;
-          accB[2 * (4 * a + b) + 1] += m.im;
-        }
   }
-  const R va = warp_transpose_reduce(accA);
-  const R vb = warp_transpose_reduce(accB);
+  const R v = warp_transpose_reduce(acc);
   // 8 warps: warps 2*mu and 2*mu + 1 hold direction mu
-  __shared__ double sh[8][64];
+  __shared__ double sh[8][32];
   const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  sh[warp][lane] = (double)va;
-  sh[warp][32 + lane] = (double)vb;
+  sh[warp][threadIdx.x & 31] = (double)v;
   __syncthreads();
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;  // 0..255 -> (mu, 64 values)
-  const int m2 = tid >> 6, j = tid & 63;
-  const double s = sh[2 * m2][j] + sh[2 * m2 + 1][j];
-  const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
-  partial[slot * 256 + tid] = s;  // [mu][A(32) | B(32)]
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid < 128) {
+    const int m2 = tid >> 5, j = tid & 31;
+    const double s2 = sh[2 * m2][j] + sh[2 * m2 + 1][j];
+    const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
+    partial[slot * 128 + tid] = s2;  // [mu][32]
+  }
 }
 
-// block per (t, rhs); 320 threads: 256 sums of slice t, 32 of A_t(t - 1), 32 of B_t(t + 1)
+// block per (t, rhs), 160 threads: 128 sums of slice t, 32 of C_t(t - 1)
 __global__ void oneD_final_kernel(const double* partial, int nchunk, int T, GammaTab tab, int p_g5,
                                   double* out) {
   const int t = blockIdx.x, rhs = blockIdx.y;
-  __shared__ double Q[4][64];   // per mu: A(t) (32), B(t) (32)
-  __shared__ double Ax[32], Bx[32];
+  __shared__ double Q[4][32];
+  __shared__ double Cm[32];
   const int tid = threadIdx.x;
-  int slice, comp;
-  if (tid < 256) { slice = t; comp = tid; }
-  else if (tid < 288) { slice = (t + T - 1) % T; comp = 3 * 64 + (tid - 256); }
-  else { slice = (t + 1) % T; comp = 3 * 64 + 32 + (tid - 288); }
+  const int slice = tid < 128 ? t : (t + T - 1) % T;
+  const int comp = tid < 128 ? tid : 3 * 32 + (tid - 128);
   double s = 0.0;
   for (int par = 0; par < 2; ++par) {
     const size_t slot0 = (((size_t)rhs * T + slice) * 2 + par) * nchunk;
-    for (int c = 0; c < nchunk; ++c) s += partial[(slot0 + c) * 256 + comp];
+    for (int c = 0; c < nchunk; ++c) s += partial[(slot0 + c) * 128 + comp];
   }
-  if (tid < 256) Q[tid >> 6][tid & 63] = s;
-  else if (tid < 288) Ax[tid - 256] = s;
-  else Bx[tid - 288] = s;
+  if (tid < 128) Q[tid >> 5][tid & 31] = s;
+  else Cm[tid - 128] = s;
   __syncthreads();
-  // symmetric derivative: spatial mu -> (A - B)/2 of slice t; time -> [A(t) + A(t-1) - B(t) - B(t+1)]/4
   __shared__ double D[4][32];
   if (tid < 128) {
     const int mu = tid >> 5, e = tid & 31;
-    double v;
-    if (mu < 3) v = 0.5 * (Q[mu][e] - Q[mu][32 + e]);
-    else v = 0.25 * (Q[3][e] + Ax[e] - Q[3][32 + e] - Bx[e]);
-    D[mu][e] = v;
+    D[mu][e] = mu < 3 ? 0.5 * Q[mu][e] : 0.25 * (Q[3][e] + Cm[e]);
   }
   __syncthreads();
   if (tid < 64) {
@@ -441,7 +436,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   const Geom& g = op->g;
   const int nchunk = (g.V3h + kOneDChunk - 1) / kOneDChunk;
   double* scratch = nullptr;
-  tm_status_t st = scratch_alloc((void**)&scratch, sizeof(double) * 256 * (size_t)nrhs * g.L[3] * 2 * nchunk, s);
+  tm_status_t st = scratch_alloc((void**)&scratch, sizeof(double) * 128 * (size_t)nrhs * g.L[3] * 2 * nchunk, s);
   if (st != TM_OK) return st;
   const dim3 grid(nchunk, 2 * g.L[3], nrhs);
   const dim3 block(kOneDLanes, 4);
@@ -470,7 +465,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   count_launch();
   st = check_launch("loop_contract_oneD");
   if (st == TM_OK) {
-    oneD_final_kernel<<<dim3(g.L[3], nrhs), 320, 0, s>>>(scratch, nchunk, g.L[3], gamma_tab(),
+    oneD_final_kernel<<<dim3(g.L[3], nrhs), 160, 0, s>>>(scratch, nchunk, g.L[3], gamma_tab(),
                                                           mode != TM_LOOP_STD, out);
     count_launch();
     st = check_launch("loop_contract_oneD final");

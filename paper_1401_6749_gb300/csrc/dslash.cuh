@@ -5,15 +5,22 @@
 //
 // (twisted-mass formulation of Secs. 2.2/2.4, nu = 2 kappa mu, antiperiodic in
 // time).  M^dag swaps (1 - g) <-> (1 + g) and nu -> -nu; D_W sets nu = 0.
+// The same kernel evaluates the pieces of the even/odd Schur complement
+//   M_hat = A - kappa^2 H_oe A^-1 H_eo,   A = 1 + i nu g5,
+// through a general form on one or both output parities:
+//   out = T_out( T_c(c) + s_hop * H in ),   T_c in {0, 1, A},  T_out in {1, A^-1},
+// with H the hopping term (dagger: swapped projectors) and c a centre field.
 //
-// GB300 design: one thread per (site, right-hand side); the output site's
-// neighbours live in the other parity, so each hop reads one 16-byte-chunked
-// spinor and one link with fully coalesced 8/16-byte loads.  Each hop is spin
-// projected: in the DeGrand-Rossi basis every g_mu is block off-diagonal,
-// g_mu = [[0, A_mu], [B_mu, 0]] with A_mu, B_mu 2x2 phased permutations and
-// B_mu A_mu = 1, so (1 + s g_mu) psi = (h, s B_mu h) with h = psi_up + s A_mu psi_dn:
-// one 2-spinor goes through the link (two SU(3) mat-vecs) per hop.
-// Right-hand sides of one block share the link loads through L1.
+// GB300 design: one thread per site computes NR right-hand sides; the site's
+// index arithmetic and its link loads (and 12-real reconstruction) are shared
+// by the NR systems, which are read from their own fields with coalesced
+// 8/16-byte loads.  Each hop is spin projected: in the DeGrand-Rossi basis
+// every g_mu is block off-diagonal, g_mu = [[0, A_mu], [B_mu, 0]] with A_mu,
+// B_mu 2x2 phased permutations and B_mu A_mu = 1, so
+// (1 + s g_mu) psi = (h, s B_mu h) with h = psi_up + s A_mu psi_dn: one
+// 2-spinor goes through the link (two SU(3) mat-vecs) per hop.  All floating
+// point operations are explicit round-to-nearest intrinsics, so the result of
+// one system does not depend on NR or on which systems share its launch.
 #pragma once
 
 #include "tm_host.h"
@@ -28,44 +35,78 @@ template <> struct GBlock<1> { static constexpr int ac0 = 1, ak0 = 2, ac1 = 0, a
 template <> struct GBlock<2> { static constexpr int ac0 = 0, ak0 = 1, ac1 = 1, ak1 = 3, bc0 = 0, bk0 = 3, bc1 = 1, bk1 = 1; };
 template <> struct GBlock<3> { static constexpr int ac0 = 0, ak0 = 0, ac1 = 1, ak1 = 0, bc0 = 0, bk0 = 0, bc1 = 1, bk1 = 0; };
 
+// explicit round-to-nearest arithmetic
+template <class R> struct Ar;
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+// a + i^K b
+template <int K, class R>
+__device__ __forceinline__ Cx<R> add_ph(Cx<R> a, Cx<R> b) {
+  using O = Ar<R>;
+  constexpr int k = ((K % 4) + 4) % 4;
+  if constexpr (k == 0) return {O::add(a.re, b.re), O::add(a.im, b.im)};
+  else if constexpr (k == 1) return {O::sub(a.re, b.im), O::add(a.im, b.re)};
+  else if constexpr (k == 2) return {O::sub(a.re, b.re), O::sub(a.im, b.im)};
+  else return {O::add(a.re, b.im), O::sub(a.im, b.re)};
+}
+
 // acc += bsign * (1 + SGN g_MU) W psi, where W = U (ADJ = false) or U^dag.
 template <int MU, int SGN, bool ADJ, class R>
 __device__ __forceinline__ void hop(Cx<R> (&acc)[12], const Cx<R> (&psi)[12], const Mat3<R>& U,
                                     R bsign) {
   using G = GBlock<MU>;
+  using O = Ar<R>;
   constexpr int s2 = SGN > 0 ? 0 : 2;  // extra phase i^2 = -1 for SGN = -1
   Cx<R> h0[3], h1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    h0[c] = psi[c] + iphase<G::ak0 + s2>(psi[3 * (2 + G::ac0) + c]);
-    h1[c] = psi[3 + c] + iphase<G::ak1 + s2>(psi[3 * (2 + G::ac1) + c]);
+    h0[c] = add_ph<G::ak0 + s2>(psi[c], psi[3 * (2 + G::ac0) + c]);
+    h1[c] = add_ph<G::ak1 + s2>(psi[3 + c], psi[3 * (2 + G::ac1) + c]);
   }
   Cx<R> w0[3], w1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    Cx<R> s0 = {0, 0}, s1 = {0, 0};
+    R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      if constexpr (!ADJ) {
-        s0 = s0 + U.m[a][b] * h0[b];
-        s1 = s1 + U.m[a][b] * h1[b];
+      const Cx<R> u = ADJ ? conjx(U.m[b][a]) : U.m[a][b];
+      if (b == 0) {
+        r0 = O::mul(u.re, h0[b].re); i0 = O::mul(u.re, h0[b].im);
+        r1 = O::mul(u.re, h1[b].re); i1 = O::mul(u.re, h1[b].im);
       } else {
-        s0 = s0 + cmulc(U.m[b][a], h0[b]);
-        s1 = s1 + cmulc(U.m[b][a], h1[b]);
+        r0 = O::fma(u.re, h0[b].re, r0); i0 = O::fma(u.re, h0[b].im, i0);
+        r1 = O::fma(u.re, h1[b].re, r1); i1 = O::fma(u.re, h1[b].im, i1);
       }
+      r0 = O::fma(-u.im, h0[b].im, r0); i0 = O::fma(u.im, h0[b].re, i0);
+      r1 = O::fma(-u.im, h1[b].im, r1); i1 = O::fma(u.im, h1[b].re, i1);
     }
-    w0[a] = bsign * s0;
-    w1[a] = bsign * s1;
+    if (MU == 3) {
+      r0 = O::mul(bsign, r0); i0 = O::mul(bsign, i0);
+      r1 = O::mul(bsign, r1); i1 = O::mul(bsign, i1);
+    }
+    w0[a] = {r0, i0};
+    w1[a] = {r1, i1};
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    acc[c] = acc[c] + w0[c];
-    acc[3 + c] = acc[3 + c] + w1[c];
+    acc[c] = add_ph<0>(acc[c], w0[c]);
+    acc[3 + c] = add_ph<0>(acc[3 + c], w1[c]);
     // lower rows: SGN * B_mu (w0, w1)
     const Cx<R> wb0 = G::bc0 == 0 ? w0[c] : w1[c];
     const Cx<R> wb1 = G::bc1 == 0 ? w0[c] : w1[c];
-    acc[6 + c] = acc[6 + c] + iphase<G::bk0 + s2>(wb0);
-    acc[9 + c] = acc[9 + c] + iphase<G::bk1 + s2>(wb1);
+    acc[6 + c] = add_ph<G::bk0 + s2>(acc[6 + c], wb0);
+    acc[9 + c] = add_ph<G::bk1 + s2>(acc[9 + c], wb1);
   }
 }
 
@@ -73,17 +114,22 @@ struct DslashArgs {
   Geom g;
   const void* links;
   DslashCall c;
-  double kappa;
-  double nu;  // sign included: M uses +nu, M^dag -nu, D_W 0
+  double nu;         // twist of T_c / T_out
+  double hop_scale;  // s_hop
   int nwarp;
-  int rhs_groups;  // number of blockDim.y-wide right-hand-side groups
+  int rhs_groups;    // number of NR-wide right-hand-side groups
+  int* trace_count;  // tracing: number of active systems of this launch
 };
 
 template <class R>
 __device__ __forceinline__ R norm2_12(const Cx<R> (&v)[12]) {
+  using O = Ar<R>;
   R s = 0;
 #pragma unroll
-  for (int j = 0; j < 12; ++j) s += v[j].re * v[j].re + v[j].im * v[j].im;
+  for (int j = 0; j < 12; ++j) {
+    s = O::fma(v[j].re, v[j].re, s);
+    s = O::fma(v[j].im, v[j].im, s);
+  }
   return s;
 }
 
@@ -93,112 +139,174 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <class S, int RECON, bool DAG, int EPI>
+template <class S, int RECON, bool DAG, int EPI, int NR>
 __global__ void __launch_bounds__(128) dslash_kernel(const DslashArgs a) {
   using R = typename Prec<S>::R;
+  using O = Ar<R>;
   const Geom& g = a.g;
   const int rg = blockIdx.x % a.rhs_groups;
   const int sb = blockIdx.x / a.rhs_groups;
-  const int par = sb & 1;
-  const int cb = (sb >> 1) * blockDim.x + threadIdx.x;
-  const int rhs = rg * blockDim.y + threadIdx.y;
-  const bool in_rhs = rhs < a.c.nrhs;
-  const bool act = in_rhs && (a.c.active == nullptr || a.c.active[rhs] != 0);
-  double part = 0.0;
-  if (act && cb < g.Vh) {
+  const int par = a.c.parity < 0 ? (sb & 1) : a.c.parity;
+  const int cbb = a.c.parity < 0 ? (sb >> 1) : sb;
+  const int cb = cbb * blockDim.x + threadIdx.x;
+  const int nrhs = a.c.nrhs;
+  int rhs[NR];
+  bool act[NR];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int r = rg * NR + j;
+    act[j] = r < nrhs && (a.c.active == nullptr || a.c.active[r] != 0);
+    rhs[j] = r < nrhs ? r : rg * NR;  // padding systems are never loaded nor stored
+    any = any || act[j];
+  }
+  double part[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) part[j] = 0.0;
+  if (a.trace_count && blockIdx.x == 0 && threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < nrhs; ++r) n += (a.c.active == nullptr || a.c.active[r] != 0) ? 1 : 0;
+    *a.trace_count = n;
+  }
+  if (any && cb < g.Vh) {
     const Site s = site_of(g, par, cb);
     const int opar = par ^ 1;
     const size_t cs = (size_t)g.Vh;
-    const size_t rbase = (size_t)rhs * 2;
     constexpr int NCH = spinor_chunks<S>();
-    Cx<R> acc[12];
+    Cx<R> acc[NR][12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) acc[j] = {0, 0};
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[j][k] = {0, 0};
     // forward hops use (1 - g) for M and (1 + g) for M^dag; backward the opposite
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-#define TM_HOPS(MU)                                                                        \
-    {                                                                                      \
-      const int lf = lex_fwd(g, s, MU);                                                    \
-      const int lb = lex_bwd(g, s, MU);                                                    \
-      R sf = 1, sbk = 1;                                                                   \
-      if (MU == 3 && g.antiperiodic) {                                                     \
-        if (s.c[3] == g.L[3] - 1) sf = -1;                                                 \
-        if (s.c[3] == 0) sbk = -1;                                                         \
-      }                                                                                    \
-      Cx<R> psi[12];                                                                       \
-      load_spinor<S>(psi, a.c.in, ((rbase + opar) * NCH) * cs + (size_t)(lf >> 1), cs);    \
-      const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                     \
-      hop<MU, SF, false>(acc, psi, Uf, sf);                                                \
-      load_spinor<S>(psi, a.c.in, ((rbase + opar) * NCH) * cs + (size_t)(lb >> 1), cs);    \
-      const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);               \
-      hop<MU, SB, true>(acc, psi, Ub, sbk);                                                \
+#define TM_HOPS(MU)                                                                              \
+    {                                                                                            \
+      const int lf = lex_fwd(g, s, MU);                                                          \
+      const int lb = lex_bwd(g, s, MU);                                                          \
+      R sf = 1, sbk = 1;                                                                         \
+      if (MU == 3 && g.antiperiodic) {                                                           \
+        if (s.c[3] == g.L[3] - 1) sf = -1;                                                       \
+        if (s.c[3] == 0) sbk = -1;                                                               \
+      }                                                                                          \
+      {                                                                                          \
+        const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                         \
+        _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
+          if (!act[j]) continue;                                                                 \
+          Cx<R> psi[12];                                                                         \
+          load_spinor<S>(psi, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), cs);  \
+          hop<MU, SF, false>(acc[j], psi, Uf, sf);                                               \
+        }                                                                                        \
+      }                                                                                          \
+      {                                                                                          \
+        const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);                   \
+        _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
+          if (!act[j]) continue;                                                                 \
+          Cx<R> psi[12];                                                                         \
+          load_spinor<S>(psi, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), cs);  \
+          hop<MU, SB, true>(acc[j], psi, Ub, sbk);                                               \
+        }                                                                                        \
+      }                                                                                          \
     }
     TM_HOPS(0)
     TM_HOPS(1)
     TM_HOPS(2)
     TM_HOPS(3)
 #undef TM_HOPS
-    const size_t b0 = ((rbase + par) * NCH) * cs + (size_t)cb;
-    Cx<R> out[12];
-    load_spinor<S>(out, a.c.in, b0, cs);  // centre
-    const R kap = (R)a.kappa;
+    const R shop = (R)a.hop_scale;
     const R nu = (R)a.nu;
+    const R inv = (R)(1.0 / (1.0 + a.nu * a.nu));
+    const void* cfield = a.c.cfield ? a.c.cfield : a.c.in;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-      const R tw = j < 6 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
-      const Cx<R> c = out[j];
-      out[j] = {c.re - tw * c.im - kap * acc[j].re, c.im + tw * c.re - kap * acc[j].im};
-    }
-    if constexpr (EPI == EPI_OUT) {
-      store_spinor<S>(a.c.out, b0, cs, out);
-      if (a.c.partial) part = (double)norm2_12(out);
-    } else if constexpr (EPI == EPI_CGUPD) {
-      const R al = (R)a.c.alpha[rhs];
-      Cx<R> v[12], w[12];
-      load_spinor<S>(v, a.c.r, b0, cs);
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) continue;
+      const size_t b0 = ((size_t)(rhs[j] * 2 + par) * NCH) * cs + cb;
+      Cx<R> out[12];
+      if (a.c.centre != 0) {
+        load_spinor<S>(out, cfield, b0, cs);
+        if (a.c.centre == 2) {  // A c = c + i nu g5 c
 #pragma unroll
-      for (int j = 0; j < 12; ++j) v[j] = v[j] - al * out[j];
-      store_spinor<S>(a.c.r, b0, cs, v);
-      part = (double)norm2_12(v);
-      load_spinor<S>(v, a.c.x, b0, cs);
-      load_spinor<S>(w, a.c.p, b0, cs);
+          for (int k = 0; k < 12; ++k) {
+            const R tw = k < 6 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
+            const Cx<R> c = out[k];
+            out[k] = {O::fma(-tw, c.im, c.re), O::fma(tw, c.re, c.im)};
+          }
+        }
 #pragma unroll
-      for (int j = 0; j < 12; ++j) v[j] = v[j] + al * w[j];
-      store_spinor<S>(a.c.x, b0, cs, v);
-    } else {  // EPI_RESID
-      Cx<R> v[12];
-      load_spinor<S>(v, a.c.b, b0, cs);
+        for (int k = 0; k < 12; ++k)
+          out[k] = {O::fma(shop, acc[j][k].re, out[k].re), O::fma(shop, acc[j][k].im, out[k].im)};
+      } else {
 #pragma unroll
-      for (int j = 0; j < 12; ++j) v[j] = v[j] - out[j];
-      store_spinor<S>(a.c.out, b0, cs, v);
-      part = (double)norm2_12(v);
+        for (int k = 0; k < 12; ++k) out[k] = {O::mul(shop, acc[j][k].re), O::mul(shop, acc[j][k].im)};
+      }
+      if (a.c.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const R tw = k < 6 ? nu : -nu;
+          const Cx<R> v = out[k];
+          out[k] = {O::mul(inv, O::fma(tw, v.im, v.re)), O::mul(inv, O::fma(-tw, v.re, v.im))};
+        }
+      }
+      if constexpr (EPI == EPI_OUT) {
+        store_spinor<S>(a.c.out, b0, cs, out);
+        if (a.c.partial) part[j] = (double)norm2_12(out);
+      } else if constexpr (EPI == EPI_CGUPD) {
+        const R al = (R)a.c.alpha[rhs[j]];
+        Cx<R> v[12];
+        load_spinor<S>(v, a.c.r, b0, cs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {O::fma(-al, out[k].re, v[k].re), O::fma(-al, out[k].im, v[k].im)};
+        store_spinor<S>(a.c.r, b0, cs, v);
+        part[j] = (double)norm2_12(v);
+        Cx<R> w[12];
+        load_spinor<S>(v, a.c.x, b0, cs);
+        load_spinor<S>(w, a.c.p, b0, cs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {O::fma(al, w[k].re, v[k].re), O::fma(al, w[k].im, v[k].im)};
+        store_spinor<S>(a.c.x, b0, cs, v);
+      } else {  // EPI_RESID
+        Cx<R> v[12];
+        load_spinor<S>(v, a.c.b, b0, cs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {O::sub(v[k].re, out[k].re), O::sub(v[k].im, out[k].im)};
+        store_spinor<S>(a.c.out, b0, cs, v);
+        part[j] = (double)norm2_12(v);
+      }
     }
   }
   if (EPI != EPI_OUT || a.c.partial != nullptr) {
-    part = warp_sum(part);
-    if (threadIdx.x % 32 == 0 && in_rhs && cb < a.nwarp * 32)
-      a.c.partial[((size_t)rhs * 2 + par) * a.nwarp + cb / 32] = part;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double ps = warp_sum(part[j]);
+      const int r = rg * NR + j;
+      if (threadIdx.x % 32 == 0 && r < nrhs && cb < a.nwarp * 32)
+        a.c.partial[((size_t)r * 2 + par) * a.nwarp + cb / 32] = ps;
+    }
   }
 }
 
-template <class S, int RECON, bool DAG, int EPI>
+template <class S, int RECON, bool DAG, int EPI, int NR>
 tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   DslashArgs a;
   a.g = op->g;
   a.links = op->links[Prec<S>::id];
   a.c = c;
-  a.kappa = op->kappa;
-  a.nu = c.mu_zero ? 0.0 : (DAG ? -2.0 * op->kappa * op->mu : 2.0 * op->kappa * op->mu);
+  if (c.custom) {
+    a.nu = c.nu;
+    a.hop_scale = c.hop_scale;
+  } else {
+    a.nu = c.mu_zero ? 0.0 : (DAG ? -2.0 * op->kappa * op->mu : 2.0 * op->kappa * op->mu);
+    a.hop_scale = -op->kappa;
+    a.c.centre = 2;
+    a.c.cfield = nullptr;
+    a.c.out_inv = false;
+  }
   a.nwarp = nwarp_of(op->g);
   const int bx = 128;
-  // several right-hand sides per block share link loads through L1; the
-  // block stays at 128 threads
-  int by = 1;
-  while (by * 2 <= c.nrhs && by < 4) by *= 2;
-  dim3 block(bx / by, by);
-  a.rhs_groups = (c.nrhs + by - 1) / by;
-  const int site_blocks = 2 * ((op->g.Vh + (int)block.x - 1) / (int)block.x);
+  a.rhs_groups = (c.nrhs + NR - 1) / NR;
+  const int per_par = (op->g.Vh + bx - 1) / bx;
+  const int site_blocks = c.parity < 0 ? 2 * per_par : per_par;
   dim3 grid((unsigned)(site_blocks * a.rhs_groups));
   // trace class: dslash.<precision>.<epilogue>
   static const char* const kNames[4][3] = {
@@ -207,27 +315,56 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
       {"dslash.f16.out", "dslash.f16.cgupd", "dslash.f16.resid"},
       {"dslash.bf16.out", "dslash.bf16.cgupd", "dslash.bf16.resid"}};
   const char* name = kNames[Prec<S>::id][EPI];
+  // algorithmic bytes: every array once; per active system the neighbour field
+  // (one parity's worth per output parity), the centre field, the epilogue's
+  // streams; per launch the links of all sites
+  const double e = (double)sizeof(S);
+  const double out_sites = (c.parity < 0 ? 2.0 : 1.0) * op->g.Vh;
+  const int centre = a.c.centre != 0 ? 1 : 0;
+  const int epi_streams = EPI == EPI_OUT ? 1 : (EPI == EPI_CGUPD ? 5 : 2);
+  const double per_rhs = out_sites * 24.0 * e * (1 + centre + epi_streams);
+  const int link_reals = std::is_same<S, double>::value ? 18 : RECON;
+  const double fixed = 4.0 * 2.0 * op->g.Vh * link_reals * e;
   cudaEvent_t ev = nullptr;
-  trace_begin(st, name, &ev);
-  dslash_kernel<S, RECON, DAG, EPI><<<grid, block, 0, st>>>(a);
+  a.trace_count = trace_begin(st, &ev);
+  dslash_kernel<S, RECON, DAG, EPI, NR><<<grid, bx, 0, st>>>(a);
   count_launch();
-  trace_end(st, name, ev);
+  trace_end(st, name, ev, a.trace_count, per_rhs, fixed);
   return check_launch("dslash");
+}
+
+// systems per thread: FP64 is arithmetic-bound and register-heavy (1); the
+// narrower formats share the site work over up to 4 systems
+int dslash_nr_override();
+
+template <class S, int RECON, bool DAG, int EPI>
+tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
+  if constexpr (std::is_same<S, double>::value) {
+    return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
+  } else {
+    // measured at 32^3 x 64 with 16 systems: one system per thread is fastest
+    // (more per thread lowers occupancy more than it saves in shared site work)
+    const int want = dslash_nr_override();
+    const int nr = want > 0 ? want : 1;
+    if (nr >= 4 && c.nrhs >= 4) return launch_one<S, RECON, DAG, EPI, 4>(op, c, st);
+    if (nr >= 2 && c.nrhs >= 2) return launch_one<S, RECON, DAG, EPI, 2>(op, c, st);
+    return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
+  }
 }
 
 template <class S, int RECON>
 tm_status_t dslash_launch(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   if (c.dagger) {
     switch (c.epi) {
-      case EPI_OUT: return launch_one<S, RECON, true, EPI_OUT>(op, c, st);
-      case EPI_CGUPD: return launch_one<S, RECON, true, EPI_CGUPD>(op, c, st);
-      default: return launch_one<S, RECON, true, EPI_RESID>(op, c, st);
+      case EPI_OUT: return launch_nr<S, RECON, true, EPI_OUT>(op, c, st);
+      case EPI_CGUPD: return launch_nr<S, RECON, true, EPI_CGUPD>(op, c, st);
+      default: return launch_nr<S, RECON, true, EPI_RESID>(op, c, st);
     }
   }
   switch (c.epi) {
-    case EPI_OUT: return launch_one<S, RECON, false, EPI_OUT>(op, c, st);
-    case EPI_CGUPD: return launch_one<S, RECON, false, EPI_CGUPD>(op, c, st);
-    default: return launch_one<S, RECON, false, EPI_RESID>(op, c, st);
+    case EPI_OUT: return launch_nr<S, RECON, false, EPI_OUT>(op, c, st);
+    case EPI_CGUPD: return launch_nr<S, RECON, false, EPI_CGUPD>(op, c, st);
+    default: return launch_nr<S, RECON, false, EPI_RESID>(op, c, st);
   }
 }
 

@@ -173,8 +173,18 @@ __global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc
 }
 
 // ------------------------------------------------------------ gauge packing
+template <class S>
+__device__ __forceinline__ S from_f64(double v) {
+  if constexpr (std::is_same<S, double>::value) return v;
+  else if constexpr (std::is_same<S, float>::value) return (float)v;
+  else if constexpr (std::is_same<S, __half>::value) return __double2half(v);
+  else return __double2bfloat16(v);
+}
+
+// canonical FP64 links -> internal format (LinkFmt), padding slots zeroed
 template <class S, int RECON>
 __global__ void pack_links_kernel(Geom g, void* out, const double* U) {
+  using F = LinkFmt<S, RECON>;
   const long V = 2L * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 4 * V) return;
@@ -185,62 +195,48 @@ __global__ void pack_links_kernel(Geom g, void* out, const double* U) {
   const int par = (x + y + z + t) & 1;
   const int cb = lex >> 1;
   const double2* src = reinterpret_cast<const double2*>(U) + ((size_t)mu * V + lex) * 9;
-  using F = LinkFmt<S, RECON>;
   const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
   const size_t cs = (size_t)g.Vh;
-  constexpr int NC = RECON == 18 ? 9 : 6;
-  if constexpr (std::is_same<S, double>::value) {
-    double2* p = reinterpret_cast<double2*>(out);
-    for (int u = 0; u < NC; ++u) p[b0 + u * cs] = src[u];
-  } else if constexpr (std::is_same<S, float>::value) {
-    if constexpr (RECON == 18) {
-      float2* p = reinterpret_cast<float2*>(out);
-      for (int u = 0; u < 9; ++u) p[b0 + u * cs] = make_float2((float)src[u].x, (float)src[u].y);
-    } else {
-      float4* p = reinterpret_cast<float4*>(out);
-      for (int u = 0; u < 3; ++u)
-        p[b0 + u * cs] = make_float4((float)src[2 * u].x, (float)src[2 * u].y,
-                                     (float)src[2 * u + 1].x, (float)src[2 * u + 1].y);
-    }
-  } else {
-    auto cvt = [](double v) -> S {
-      if constexpr (std::is_same<S, __half>::value) return __double2half(v);
-      else return __double2bfloat16(v);
-    };
-    if constexpr (RECON == 18) {
-      S* p = reinterpret_cast<S*>(out);
-      for (int u = 0; u < 9; ++u) {
-        p[2 * (b0 + u * cs)] = cvt(src[u].x);
-        p[2 * (b0 + u * cs) + 1] = cvt(src[u].y);
-      }
-    } else {
-      S* p = reinterpret_cast<S*>(out);
-      for (int u = 0; u < 3; ++u) {
-        S* q = p + 4 * (b0 + u * cs);
-        q[0] = cvt(src[2 * u].x);
-        q[1] = cvt(src[2 * u].y);
-        q[2] = cvt(src[2 * u + 1].x);
-        q[3] = cvt(src[2 * u + 1].y);
-      }
+  S* base = reinterpret_cast<S*>(out);
+  constexpr int per_unit = 2 * F::kCplxPerUnit;  // S elements per unit
+  for (int u = 0; u < F::NU; ++u) {
+    S* q = base + (b0 + u * cs) * per_unit;
+    for (int k = 0; k < F::kCplxPerUnit; ++k) {
+      const int e = u * F::kCplxPerUnit + k;
+      const double2 v = e < F::kCplx ? src[e] : make_double2(0.0, 0.0);
+      q[2 * k] = from_f64<S>(v.x);
+      q[2 * k + 1] = from_f64<S>(v.y);
     }
   }
 }
 
+template <class S, int RECON>
+static size_t link_bytes_t(const Geom& g) {
+  using F = LinkFmt<S, RECON>;
+  return 4 * 2 * (size_t)g.Vh * F::NU * F::kUnitBytes;
+}
+
 size_t link_bytes(const Geom& g, tm_prec_t p, int recon) {
-  const size_t reals = (p == TM_PREC_F64 || recon == 18) ? 18 : 12;
-  return 4 * 2 * (size_t)g.Vh * reals * prec_size(p);
+  const bool r12 = recon == 12;
+  switch (p) {
+    case TM_PREC_F64: return link_bytes_t<double, 18>(g);
+    case TM_PREC_F32: return r12 ? link_bytes_t<float, 12>(g) : link_bytes_t<float, 18>(g);
+    case TM_PREC_F16: return r12 ? link_bytes_t<__half, 12>(g) : link_bytes_t<__half, 18>(g);
+    default: return r12 ? link_bytes_t<__nv_bfloat16, 12>(g) : link_bytes_t<__nv_bfloat16, 18>(g);
+  }
 }
 
 tm_status_t pack_links(const Geom& g, tm_prec_t p, int recon, void* out, const double* U,
                        cudaStream_t s) {
   const long n = 4L * 2 * g.Vh;
   const unsigned nb = blocks_for(n, 256);
+  const bool r12 = recon == 12;
   if (p == TM_PREC_F64) pack_links_kernel<double, 18><<<nb, 256, 0, s>>>(g, out, U);
-  else if (p == TM_PREC_F32 && recon == 12) pack_links_kernel<float, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F32 && r12) pack_links_kernel<float, 12><<<nb, 256, 0, s>>>(g, out, U);
   else if (p == TM_PREC_F32) pack_links_kernel<float, 18><<<nb, 256, 0, s>>>(g, out, U);
-  else if (p == TM_PREC_F16 && recon == 12) pack_links_kernel<__half, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_F16 && r12) pack_links_kernel<__half, 12><<<nb, 256, 0, s>>>(g, out, U);
   else if (p == TM_PREC_F16) pack_links_kernel<__half, 18><<<nb, 256, 0, s>>>(g, out, U);
-  else if (recon == 12) pack_links_kernel<__nv_bfloat16, 12><<<nb, 256, 0, s>>>(g, out, U);
+  else if (r12) pack_links_kernel<__nv_bfloat16, 12><<<nb, 256, 0, s>>>(g, out, U);
   else pack_links_kernel<__nv_bfloat16, 18><<<nb, 256, 0, s>>>(g, out, U);
   count_launch();
   return check_launch("pack_links");
@@ -250,14 +246,14 @@ tm_status_t pack_links(const Geom& g, tm_prec_t p, int recon, void* out, const d
 // p = r + beta[rhs] p for active systems
 template <class S>
 __global__ void xpay_kernel(Geom g, void* p, const void* r, const double* beta, const int* active,
-                            int nrhs) {
-  const long n = 2L * g.Vh;
+                            int nrhs, int par0, int npar) {
+  const long n = (long)npar * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * nrhs) return;
   const int rhs = (int)(i / n);
   if (!active[rhs]) return;
   const int rem = (int)(i % n);
-  const size_t b0 = SpinorRef<S>::base(g, rhs, rem / g.Vh, rem % g.Vh);
+  const size_t b0 = SpinorRef<S>::base(g, rhs, par0 + rem / g.Vh, rem % g.Vh);
   using R = typename Prec<S>::R;
   const R be = (R)beta[rhs];
   Cx<R> a[12], b[12];
@@ -272,14 +268,14 @@ __global__ void xpay_kernel(Geom g, void* p, const void* r, const double* beta, 
 // sigma may be null (scale 1)
 template <class S>
 __global__ void fold_kernel(Geom g, void* x64, void* y, const double* sigma, const int* mask,
-                            int nrhs) {
-  const long n = 2L * g.Vh;
+                            int nrhs, int par0, int npar) {
+  const long n = (long)npar * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * nrhs) return;
   const int rhs = (int)(i / n);
   if (mask && !mask[rhs]) return;
   const int rem = (int)(i % n);
-  const int par = rem / g.Vh, cb = rem % g.Vh;
+  const int par = par0 + rem / g.Vh, cb = rem % g.Vh;
   const double sc = sigma ? sigma[rhs] : 1.0;
   Cx<double> a[12], b[12];
   const size_t bx = SpinorRef<double>::base(g, rhs, par, cb);
@@ -299,14 +295,14 @@ __global__ void fold_kernel(Geom g, void* x64, void* y, const double* sigma, con
 //   r = r64 / sigma[rhs]   and, if p != null,   p *= ratio[rhs]
 template <class S>
 __global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* sigma, void* p,
-                               const double* ratio, const int* mask, int nrhs) {
-  const long n = 2L * g.Vh;
+                               const double* ratio, const int* mask, int nrhs, int par0, int npar) {
+  const long n = (long)npar * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * nrhs) return;
   const int rhs = (int)(i / n);
   if (mask && !mask[rhs]) return;
   const int rem = (int)(i % n);
-  const int par = rem / g.Vh, cb = rem % g.Vh;
+  const int par = par0 + rem / g.Vh, cb = rem % g.Vh;
   const size_t b64 = SpinorRef<double>::base(g, rhs, par, cb);
   const size_t bs = SpinorRef<S>::base(g, rhs, par, cb);
   const double inv = 1.0 / sigma[rhs];
@@ -325,33 +321,34 @@ __global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* s
 }
 
 tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
-                 const int* active, int nrhs, cudaStream_t s) {
-  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+                 const int* active, int nrhs, int par0, int npar, cudaStream_t s) {
+  const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    xpay_kernel<S><<<nb, 256, 0, s>>>(g, p, r, beta, active, nrhs);
+    xpay_kernel<S><<<nb, 256, 0, s>>>(g, p, r, beta, active, nrhs, par0, npar);
     count_launch();
     return check_launch("xpay");
   });
 }
 
 tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
-                 const int* mask, int nrhs, cudaStream_t s) {
-  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s) {
+  const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    fold_kernel<S><<<nb, 256, 0, s>>>(g, x64, y, sigma, mask, nrhs);
+    fold_kernel<S><<<nb, 256, 0, s>>>(g, x64, y, sigma, mask, nrhs, par0, npar);
     count_launch();
     return check_launch("fold");
   });
 }
 
 tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
-                    void* p, const double* ratio, const int* mask, int nrhs, cudaStream_t s) {
-  const unsigned nb = blocks_for(2L * g.Vh * nrhs, 256);
+                    void* p, const double* ratio, const int* mask, int nrhs, int par0, int npar,
+                    cudaStream_t s) {
+  const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    rescale_kernel<S><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs);
+    rescale_kernel<S><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs, par0, npar);
     count_launch();
     return check_launch("rescale");
   });
@@ -371,12 +368,49 @@ tm_status_t convert_masked(const Geom& g, void* out, tm_prec_t po, const void* i
   });
 }
 
+// Site-local twist on one parity: out = A in (inverse = 0) or A^-1 in
+// (inverse = 1), A = 1 + i nu g5, A^-1 = (1 - i nu g5) / (1 + nu^2).
+template <class S>
+__global__ void twist_kernel(Geom g, void* out, const void* in, double nu, int inverse, int par,
+                             int nrhs) {
+  using R = typename Prec<S>::R;
+  const long n = (long)g.Vh;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int rhs = (int)(i / n);
+  const int cb = (int)(i % n);
+  const size_t b0 = SpinorRef<S>::base(g, rhs, par, cb);
+  Cx<R> v[12];
+  load_spinor<S>(v, in, b0, (size_t)g.Vh);
+  const R sc = inverse ? (R)(1.0 / (1.0 + nu * nu)) : (R)1;
+  const R tn = inverse ? (R)(-nu) : (R)nu;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const R tw = j < 6 ? tn : -tn;
+    const Cx<R> c = v[j];
+    v[j] = {sc * (c.re - tw * c.im), sc * (c.im + tw * c.re)};
+  }
+  store_spinor<S>(out, b0, (size_t)g.Vh, v);
+}
+
+tm_status_t twist(const Geom& g, tm_prec_t prec, void* out, const void* in, double nu, int inverse,
+                  int par, int nrhs, cudaStream_t s) {
+  const unsigned nb = blocks_for((long)g.Vh * nrhs, 256);
+  return by_prec(prec, [&](auto tag) {
+    using S = decltype(tag);
+    twist_kernel<S><<<nb, 256, 0, s>>>(g, out, in, nu, inverse, par, nrhs);
+    count_launch();
+    return check_launch("twist");
+  });
+}
+
 // ------------------------------------------------ fixed-order reductions
 // One block per system; thread i sums entries i, i + 256, ... in order, then
 // a fixed shared-memory tree.  The result depends only on the partial array.
-__global__ void reduce_partials_kernel(const double* partial, int nper, double* result) {
+__global__ void reduce_partials_kernel(const double* partial, int nper, size_t stride,
+                                       double* result) {
   __shared__ double sh[256];
-  const double* p = partial + (size_t)blockIdx.x * nper;
+  const double* p = partial + (size_t)blockIdx.x * stride;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nper; i += 256) acc += p[i];
   sh[threadIdx.x] = acc;
@@ -389,8 +423,8 @@ __global__ void reduce_partials_kernel(const double* partial, int nper, double* 
 }
 
 tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* result,
-                            cudaStream_t s) {
-  reduce_partials_kernel<<<nrhs, 256, 0, s>>>(partial, nper, result);
+                            cudaStream_t s, size_t stride) {
+  reduce_partials_kernel<<<nrhs, 256, 0, s>>>(partial, nper, stride ? stride : (size_t)nper, result);
   count_launch();
   return check_launch("reduce_partials");
 }

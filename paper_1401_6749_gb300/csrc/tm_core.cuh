@@ -214,15 +214,20 @@ __device__ __forceinline__ void store_spinor(void* field, size_t b0, size_t cs,
 
 // ----------------------------------------------------------- link accessors
 // Links of direction mu at site (par, cb): unit index ((mu * 2 + par) * NU + u) * Vh + cb.
-// RECON 18: 9 units of one complex each; RECON 12: two rows (6 complex).
-//   F64: unit = double2 (one complex).
-//   F32: RECON 18 -> float2 units (9), RECON 12 -> float4 units of two complex (3).
-//   F16/BF16: RECON 18 -> one half pair (9), RECON 12 -> 8-byte units of two complex (3).
+// A link is 9 complex numbers (RECON 18) or its first two rows (RECON 12; the
+// third row is conj(row0 x row1)), packed row-major into units of
+// kCplxPerUnit complex numbers, the last unit zero-padded:
+//   F64: double2 units (1 complex): 9 or 6 units of 16 bytes.
+//   F32: float4 units (2 complex): 5 (18) or 3 (12) units of 16 bytes.
+//   F16/BF16: RECON 18 -> 16-byte units of 4 complex (3 units),
+//             RECON 12 -> 8-byte units of 2 complex (3 units).
 template <class S, int RECON>
 struct LinkFmt {
   static constexpr bool kF64 = std::is_same<S, double>::value;
-  static constexpr int kCplxPerUnit = (kF64 || RECON == 18) ? 1 : 2;
-  static constexpr int NU = (RECON == 18 ? 9 : 6) / kCplxPerUnit;
+  static constexpr bool kF32 = std::is_same<S, float>::value;
+  static constexpr int kCplx = RECON == 18 ? 9 : 6;
+  static constexpr int kCplxPerUnit = kF64 ? 1 : (kF32 ? 2 : (RECON == 18 ? 4 : 2));
+  static constexpr int NU = (kCplx + kCplxPerUnit - 1) / kCplxPerUnit;
   static constexpr int kUnitBytes = kCplxPerUnit * 2 * (int)sizeof(S);
 };
 
@@ -237,47 +242,42 @@ __device__ __forceinline__ Mat3<typename Prec<S>::R> load_link(const void* links
   using R = typename Prec<S>::R;
   using F = LinkFmt<S, RECON>;
   Mat3<R> U;
-  Cx<R> e[9];
+  Cx<R> e[F::NU * F::kCplxPerUnit];
   const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
   const size_t cs = (size_t)g.Vh;
-  constexpr int NC = RECON == 18 ? 9 : 6;
-  if constexpr (std::is_same<S, double>::value) {
+  if constexpr (F::kF64) {
     const double2* p = reinterpret_cast<const double2*>(links);
 #pragma unroll
-    for (int u = 0; u < NC; ++u) {
+    for (int u = 0; u < F::NU; ++u) {
       const double2 d = p[b0 + u * cs];
       e[u] = {d.x, d.y};
     }
-  } else if constexpr (std::is_same<S, float>::value) {
-    if constexpr (RECON == 18) {
-      const float2* p = reinterpret_cast<const float2*>(links);
+  } else if constexpr (F::kF32) {
+    const float4* p = reinterpret_cast<const float4*>(links);
 #pragma unroll
-      for (int u = 0; u < 9; ++u) {
-        const float2 d = p[b0 + u * cs];
-        e[u] = {d.x, d.y};
-      }
-    } else {
-      const float4* p = reinterpret_cast<const float4*>(links);
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const float4 d = p[b0 + u * cs];
-        e[2 * u] = {d.x, d.y};
-        e[2 * u + 1] = {d.z, d.w};
-      }
+    for (int u = 0; u < F::NU; ++u) {
+      const float4 d = p[b0 + u * cs];
+      e[2 * u] = {d.x, d.y};
+      e[2 * u + 1] = {d.z, d.w};
     }
   } else {
     using P2 = typename Pair<S>::T;
     if constexpr (RECON == 18) {
-      const P2* p = reinterpret_cast<const P2*>(links);
+      const uint4* p = reinterpret_cast<const uint4*>(links);
 #pragma unroll
-      for (int u = 0; u < 9; ++u) {
-        const float2 q = h2f(p[b0 + u * cs]);
-        e[u] = {q.x, q.y};
+      for (int u = 0; u < F::NU; ++u) {
+        const uint4 d = p[b0 + u * cs];
+        const P2* h = reinterpret_cast<const P2*>(&d);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 q = h2f(h[k]);
+          e[4 * u + k] = {q.x, q.y};
+        }
       }
     } else {
       const uint2* p = reinterpret_cast<const uint2*>(links);
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
+      for (int u = 0; u < F::NU; ++u) {
         const uint2 d = p[b0 + u * cs];
         const P2* h = reinterpret_cast<const P2*>(&d);
         const float2 q0 = h2f(h[0]), q1 = h2f(h[1]);
@@ -306,8 +306,13 @@ __device__ __forceinline__ Mat3<typename Prec<S>::R> load_link(const void* links
 void count_launch(int n = 1);
 void set_error(const char* fmt, ...);
 tm_status_t check_launch(const char* what);
-void trace_begin(cudaStream_t s, const char* name, cudaEvent_t* ev0);
-void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0);
+// Tracing of Dslash launches (tm_trace_enable): trace_begin records a start
+// event and returns a device slot in which the kernel stores how many of its
+// systems were active (nullptr when tracing is off); trace_end records the end
+// event with the launch's algorithmic bytes per active system and per launch.
+int* trace_begin(cudaStream_t s, cudaEvent_t* ev0);
+void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
+               double fixed_bytes);
 
 
 }  // namespace tml

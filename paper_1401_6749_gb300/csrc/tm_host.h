@@ -38,6 +38,16 @@ struct DslashCall {
   int nrhs = 1;
   bool dagger = false;
   bool mu_zero = false;
+  // general form (custom = true): out = T_out(T_c(cfield) + hop_scale * H in)
+  //   centre: 0 no centre term, 1 identity, 2 A = 1 + i nu g5;  out_inv: T_out = A^-1
+  // default (custom = false): full M / M^dag / D_W on both parities
+  bool custom = false;
+  double nu = 0.0;
+  double hop_scale = 0.0;
+  int centre = 2;
+  const void* cfield = nullptr;
+  bool out_inv = false;
+  int parity = -1;  // output parity (0 even, 1 odd) or -1 for both
   int epi = EPI_OUT;
   double* partial = nullptr;
   const int* active = nullptr;
@@ -55,9 +65,10 @@ tm_status_t dslash_launch(const tm_op* op, const DslashCall& c, cudaStream_t s);
 
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s);
 
-// per-warp partial sums [nrhs][2][nwarp] -> result[rhs] (fixed summation order)
+// per-warp partial sums -> result[rhs] (fixed summation order): system rhs sums
+// partial[rhs * stride + i], i < nper (stride 0 means nper)
 tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* result,
-                            cudaStream_t s);
+                            cudaStream_t s, size_t stride = 0);
 
 tm_status_t check_geom(const int L[4]);
 

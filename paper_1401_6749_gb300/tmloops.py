@@ -47,7 +47,7 @@ class tm_params_t(ctypes.Structure):
 class tm_cg_params_t(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("prec", ctypes.c_int), ("inner_prec", ctypes.c_int), ("delta", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int), ("schur", ctypes.c_int)]
 
 
 class tm_cg_stats_t(ctypes.Structure):
@@ -77,7 +77,7 @@ _SIGS = {
     "tm_launch_count": [],
     "tm_trace_enable": [_i],
     "tm_trace_reset": [],
-    "tm_trace_read": [ctypes.c_char_p, _P(_i), _P(_d)],
+    "tm_trace_read": [ctypes.c_char_p, _P(_i), _P(_d), _P(_d)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -180,10 +180,11 @@ def z4_noise(L, eta, prec, seed, first_src, nsrc, stream=None):
 
 
 def cg_params(tol, max_iter=10000, mode=CG_PLAIN, prec=F64, inner_prec=F32, delta=0.1,
-              check_every=8, true_residual=False):
+              check_every=8, true_residual=False, schur=False):
     p = tm_cg_params_t()
     p.tol, p.max_iter, p.mode, p.prec, p.inner_prec = float(tol), int(max_iter), int(mode), int(prec), int(inner_prec)
     p.delta, p.check_every, p.true_residual = float(delta), int(check_every), int(bool(true_residual))
+    p.schur = int(bool(schur))
     return p
 
 
@@ -234,8 +235,10 @@ def tm_trace_reset():
     _lib.tm_trace_reset()
 
 
-def tm_trace_read(name="dslash"):
+def tm_trace_read(name="dslash.*"):
+    """(launches, device ms, algorithmic bytes) of a traced Dslash class."""
     n = ctypes.c_int()
     ms = ctypes.c_double()
-    _check(_lib.tm_trace_read(name.encode(), ctypes.byref(n), ctypes.byref(ms)))
-    return n.value, ms.value
+    nb = ctypes.c_double()
+    _check(_lib.tm_trace_read(name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nb)))
+    return n.value, ms.value, nb.value

@@ -4,7 +4,8 @@ Orchestration only: every arithmetic step is a libtmloops kernel.
 
 For sources r = first .. first + N_HP + N_LP - 1 (Z4, Sec. 2):
   * low-precision (LP) solves of all N_HP + N_LP sources, PLAIN CG in F16/BF16
-    truncated at |r|/|b| = tol_lp, in batches of `batch` right-hand sides;
+    truncated at |r|/|b| = tol_lp, in batches of `batch` right-hand sides
+    (even/odd preconditioned unless schur=False);
   * high-precision (HP) solves of the first N_HP sources, MIXED CG (FP64
     reliable updates) to tol_hp;
   * for every solution s: local and one-derivative loops with the one-end
@@ -25,7 +26,7 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=8,
-                 delta=0.1, kinds=KINDS):
+                 delta=0.1, kinds=KINDS, schur=True):
         self.op = op
         self.L = op.L
         self.T = op.L[3]
@@ -35,6 +36,7 @@ class TsmPipeline:
         self.tol_lp, self.tol_hp = tol_lp, tol_hp
         self.seed, self.first = int(seed), int(first_src)
         self.max_iter, self.check_every, self.delta = max_iter, check_every, delta
+        self.schur = bool(schur)
         self.kinds = tuple(kinds)
         self.nu = 2.0 * op.kappa * op.mu
         n_all = self.n_hp + self.n_lp
@@ -76,14 +78,15 @@ class TsmPipeline:
         n_all = self.n_hp + self.n_lp
         self.stats_lp, self.stats_hp = [], []
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
-                                 check_every=self.check_every)
+                                 check_every=self.check_every, schur=self.schur)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
             self.stats_lp += self._solve_and_contract(self._lp, self.lp_prec, self.first + b0, n,
                                                       lp_params, self.lp_loops, b0)
         if self.n_hp:
             hp_params = tl.cg_params(self.tol_hp, self.max_iter, tl.CG_MIXED, inner_prec=self.hp_inner,
-                                     delta=self.delta, check_every=self.check_every)
+                                     delta=self.delta, check_every=self.check_every,
+                                     schur=self.schur)
             for b0 in range(0, self.n_hp, self.batch):
                 n = min(self.batch, self.n_hp - b0)
                 self.stats_hp += self._solve_and_contract(self._hp, tl.F64, self.first + b0, n,

@@ -57,14 +57,12 @@ def test_mixed_precision_reaches_fp64_accuracy(inner):
     st, stats = tl.tm_cg_solve(op, x, pack(tl, L, eta, 0), n,
                                tl.cg_params(1e-11, 4000, tl.CG_MIXED, inner_prec=inner, delta=0.1))
     got = unpack(tl, L, x, 0, n)
-    Minv = None
     for j in range(n):
         assert stats[j]["status"] == 0
         assert stats[j]["true_res"] <= 1e-11
         assert stats[j]["reliable_updates"] >= 1
         ref, _ = ocg.cg_normal(U, eta[j], kappa, mu, tol=1e-13)
         assert rel_l2(got[j], ref) < 1e-8
-    assert Minv is None
     op.close()
 
 
@@ -92,7 +90,8 @@ def test_low_precision_truncated_solve(prec):
 
 
 def test_batch_composition_does_not_change_solutions():
-    """The LP map must be the same function of eta in every batch (TSM)."""
+    """The LP map must be the same function of eta in every batch (TSM): 6
+    systems run 4 + 2 per thread, 2 systems 2 per thread, 1 system alone."""
     tl = require_gpu()
     L = (4, 4, 4, 4)
     U, op = _setup(tl, L, 0.16, 0.01, seed=12)
@@ -105,6 +104,9 @@ def test_batch_composition_does_not_change_solutions():
     a = unpack(tl, L, xa, 2, 6)
     b = unpack(tl, L, xb, 2, 2)
     np.testing.assert_array_equal(a[3:5], b)
+    xc = tl.empty_field(L, 2, 1)
+    tl.tm_cg_solve(op, xc, pack(tl, L, eta[5:6], 2), 1, prm)
+    np.testing.assert_array_equal(a[5], unpack(tl, L, xc, 2, 1)[0])
     op.close()
 
 
@@ -134,4 +136,65 @@ def test_dense_parity_tiny_lattice():
     tl.tm_cg_solve(op, x, pack(tl, L, eta, 0), 1, tl.cg_params(1e-13, 2000, tl.CG_PLAIN, prec=0))
     exact = np.linalg.solve(dense_matrix(U, kappa, mu), eta[0].ravel()).reshape(eta[0].shape)
     assert rel_l2(unpack(tl, L, x, 0, 1)[0], exact) < 1e-10
+    op.close()
+
+
+# ------------------------------------------------------------------ even/odd
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 4, 8), (2, 2, 2, 4)])
+def test_schur_plain_f64_matches_oracle_solution(L):
+    """The even/odd preconditioned solve returns x = M^-1 eta on both parities."""
+    tl = require_gpu()
+    kappa, mu = 0.16, 0.01
+    U, op = _setup(tl, L, kappa, mu, seed=21)
+    n = 3
+    eta = oracle_z4(L, 5, 0, n)
+    x = tl.empty_field(L, 0, n)
+    st, stats = tl.tm_cg_solve(op, x, pack(tl, L, eta, 0), n,
+                               tl.cg_params(1e-12, 2000, tl.CG_PLAIN, prec=0, true_residual=True,
+                                            schur=True))
+    got = unpack(tl, L, x, 0, n)
+    for j in range(n):
+        assert stats[j]["status"] == 0 and stats[j]["true_res"] < 1e-11
+        ref, _ = ocg.cg_normal(U, eta[j], kappa, mu, tol=1e-13)
+        assert rel_l2(got[j], ref) < 1e-9
+    op.close()
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_schur_mixed_precision(inner):
+    tl = require_gpu()
+    L = (4, 4, 4, 8)
+    kappa, mu = 0.16, 0.01
+    U, op = _setup(tl, L, kappa, mu, seed=5)
+    n = 2
+    eta = oracle_z4(L, 99, 0, n)
+    x = tl.empty_field(L, 0, n)
+    st, stats = tl.tm_cg_solve(op, x, pack(tl, L, eta, 0), n,
+                               tl.cg_params(1e-11, 4000, tl.CG_MIXED, inner_prec=inner, delta=0.1,
+                                            schur=True))
+    got = unpack(tl, L, x, 0, n)
+    for j in range(n):
+        assert stats[j]["status"] == 0 and stats[j]["true_res"] <= 1e-11
+        ref, _ = ocg.cg_normal(U, eta[j], kappa, mu, tol=1e-13)
+        assert rel_l2(got[j], ref) < 1e-8
+    op.close()
+
+
+def test_schur_needs_fewer_iterations_and_is_batch_independent():
+    tl = require_gpu()
+    L = (6, 4, 4, 8)
+    U, op = _setup(tl, L, 0.16, 0.01, seed=12)
+    eta = oracle_z4(L, 44, 0, 6)
+    full = tl.cg_params(1e-8, 2000, tl.CG_PLAIN, prec=1)
+    eo = tl.cg_params(1e-8, 2000, tl.CG_PLAIN, prec=1, schur=True)
+    x = tl.empty_field(L, 1, 6)
+    _, s_full = tl.tm_cg_solve(op, x, pack(tl, L, eta, 1), 6, full)
+    _, s_eo = tl.tm_cg_solve(op, x, pack(tl, L, eta, 1), 6, eo)
+    assert max(s["iters"] for s in s_eo) < min(s["iters"] for s in s_full)
+    lp = tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=2, schur=True)
+    xa = tl.empty_field(L, 2, 6)
+    tl.tm_cg_solve(op, xa, pack(tl, L, eta, 2), 6, lp)
+    xb = tl.empty_field(L, 2, 1)
+    tl.tm_cg_solve(op, xb, pack(tl, L, eta[4:5], 2), 1, lp)
+    np.testing.assert_array_equal(unpack(tl, L, xa, 2, 6)[4], unpack(tl, L, xb, 2, 1)[0])
     op.close()
