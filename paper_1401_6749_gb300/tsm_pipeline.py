@@ -73,8 +73,12 @@ class TsmPipeline:
         self._contract(x, w, g5w, prec, n, dst, row0)
         return stats
 
-    def run(self):
-        """One full TSM estimate; returns per-kind (mean, err) device tensors."""
+    def run(self, dist=None):
+        """One full TSM estimate; returns per-kind (mean, err) device tensors.
+
+        With a torch.distributed module whose world size exceeds one, every rank
+        runs its own sources (first_src set per rank) and the estimate combines
+        the sources of all ranks (one all-gather of the per-source loops)."""
         n_all = self.n_hp + self.n_lp
         self.stats_lp, self.stats_hp = [], []
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
@@ -91,20 +95,37 @@ class TsmPipeline:
                 n = min(self.batch, self.n_hp - b0)
                 self.stats_hp += self._solve_and_contract(self._hp, tl.F64, self.first + b0, n,
                                                           hp_params, self.hp_loops, b0)
+        if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+            return self.combine_global(dist)
         return self.combine()
 
+    def _combine_sets(self, k, hp, lphp, lp, n_hp, n_lp):
+        length = self.len[k.split("_")[0]]
+        scale = -2j * self.nu if k.endswith("vv") else 2.0
+        mean = torch.empty(2 * length, dtype=torch.float64, device="cuda")
+        err = torch.empty(2 * length, dtype=torch.float64, device="cuda")
+        if n_hp:
+            tl.tsm_combine(hp, lphp, n_hp, lp, n_lp, length, scale, mean, err)
+        else:
+            tl.tsm_combine(None, None, 0, lp, n_lp, length, scale, mean, err)
+        return mean, err
+
     def combine(self):
+        """TSM estimate (Eq. 4) from this process's sources."""
         res = {}
         for k in self.kinds:
-            length = self.len[k.split("_")[0]]
-            scale = -2j * self.nu if k.endswith("vv") else 2.0
-            mean = torch.empty(2 * length, dtype=torch.float64, device="cuda")
-            err = torch.empty(2 * length, dtype=torch.float64, device="cuda")
             lp = self.lp_loops[k]
-            if self.n_hp:
-                tl.tsm_combine(self.hp_loops[k][:self.n_hp], lp[:self.n_hp], self.n_hp,
-                               lp[self.n_hp:], self.n_lp, length, scale, mean, err)
-            else:
-                tl.tsm_combine(None, None, 0, lp, self.n_lp, length, scale, mean, err)
-            res[k] = (mean, err)
+            res[k] = self._combine_sets(k, self.hp_loops[k][:self.n_hp], lp[:self.n_hp],
+                                        lp[self.n_hp:], self.n_hp, self.n_lp)
+        return res
+
+    def combine_global(self, dist):
+        """TSM estimate over the sources of all ranks (one all-gather per kind)."""
+        from .distributed import gather_tsm_sets
+        world = dist.get_world_size()
+        res = {}
+        for k in self.kinds:
+            hp_all, lphp, lp = gather_tsm_sets(dist, self.hp_loops[k][:self.n_hp], self.lp_loops[k],
+                                               self.n_hp)
+            res[k] = self._combine_sets(k, hp_all, lphp, lp, world * self.n_hp, world * self.n_lp)
         return res
