@@ -30,11 +30,11 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=0.001, recon=18),
+                  seed=20140126, schur=True, delta=3e-5, recon=12),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126, schur=True, delta=0.001, recon=18),
+                 seed=20140126, schur=True, delta=3e-5, recon=12),
 }
 
 PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -249,12 +249,13 @@ def run_ours(args):
     tl.tm_trace_enable(False)
     clk = clocks.stop()
     classes = {}
-    for prec in ("f64", "f32", "f16", "bf16"):
-        for epi in ("out", "cgupd", "resid"):
-            n, tms, nbytes = tl.tm_trace_read("dslash.%s.%s" % (prec, epi))
-            if n:
-                classes["dslash.%s.%s" % (prec, epi)] = (n / args.steps, tms / args.steps,
-                                                          nbytes / args.steps)
+    names = ["dslash.%s.%s" % (p, e) for p in ("f64", "f32", "f16", "bf16") for e in ("out", "cgupd", "resid")]
+    names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in ("f64", "f32", "f16", "bf16")]
+    names += ["blas.xpay", "z4_noise"]
+    for name in names:
+        n, tms, nbytes = tl.tm_trace_read(name)
+        if n:
+            classes[name] = (n / args.steps, tms / args.steps, nbytes / args.steps)
     tl.tm_trace_reset()
     ms = _max_over_ranks(dist, ms)
     _log("timed: %.3f ms/step, %d launches/step, classes %s" % (ms, launches, classes))

@@ -39,9 +39,20 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _extra_flags():
+    """Extra nvcc flags from TMLOOPS_EXTRA_NVCC (tuning builds, e.g. -DTM_DSLASH_MINBLOCKS=8)."""
+    return os.environ.get("TMLOOPS_EXTRA_NVCC", "").split()
+
+
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
+    with open(STAMP) as f:
+        if f.read() != " ".join(NVCC_FLAGS + _extra_flags()):
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
@@ -56,7 +67,7 @@ def build(force=False, verbose=False, jobs=None):
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + NVCC_FLAGS + _extra_flags() + ["-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, res.stdout, res.stderr))
@@ -74,6 +85,8 @@ def build(force=False, verbose=False, jobs=None):
     if res.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(NVCC_FLAGS + _extra_flags()))
     return LIB
 
 

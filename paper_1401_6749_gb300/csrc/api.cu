@@ -56,8 +56,9 @@ tm_status_t check_geom(const int L[4]) {
 struct TraceRec {
   std::string name;
   cudaEvent_t a, b;
-  int slot;
+  int slot;        // device counter of active systems, or -1
   double bytes_per_rhs, fixed_bytes;
+  int nrhs;        // systems counted as active when slot < 0
 };
 static std::mutex g_trace_mu;
 static std::atomic<int> g_trace_on{0};
@@ -77,13 +78,14 @@ int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
 }
 
 void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
-               double fixed_bytes) {
+               double fixed_bytes, int nrhs_if_uncounted) {
   if (!ev0) return;
   cudaEvent_t ev1;
   if (cudaEventCreate(&ev1) != cudaSuccess) { cudaEventDestroy(ev0); return; }
   cudaEventRecord(ev1, s);
   std::lock_guard<std::mutex> lk(g_trace_mu);
-  g_trace.push_back({name, ev0, ev1, (int)(slot - g_trace_counts), bytes_per_rhs, fixed_bytes});
+  const int sl = slot ? (int)(slot - g_trace_counts) : -1;
+  g_trace.push_back({name, ev0, ev1, sl, bytes_per_rhs, fixed_bytes, nrhs_if_uncounted});
   ++g_trace_next;
 }
 
@@ -169,7 +171,7 @@ extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* to
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { set_error("tm_trace_read: elapsed time failed"); return TM_ERR_CUDA; }
     ms += t;
-    const int act = (r.slot >= 0 && r.slot < (int)counts.size()) ? counts[r.slot] : 0;
+    const int act = r.slot < 0 ? r.nrhs : (r.slot < (int)counts.size() ? counts[r.slot] : 0);
     bytes += act > 0 ? act * r.bytes_per_rhs + r.fixed_bytes : 0.0;
     ++n;
   }

@@ -15,7 +15,7 @@
 // order.
 #include <cstring>
 
-#include "tm_host.h"
+#include "dslash.cuh"
 
 namespace tml {
 
@@ -165,57 +165,174 @@ __global__ void local_final_kernel(const double* partial, int nchunk, int T, Gam
 // both live on the link (x, x+t).  So one 4x4 accumulator per direction:
 //   spatial: L^dag(x) [U_mu(x) R(x+mu) - U_mu(x-mu)^dag R(x-mu)]
 //   time:    L^dag(x) U_t(x) R(x+t) - L^dag(x+t) U_t(x)^dag R(x)   (boundary sign on both)
-constexpr int kOneDK = 4;           // sites per thread
-constexpr int kOneDLanes = 64;      // sites side by side in a block (x 4 directions)
+// Work split: a warp handles 32 sites of one direction mu and one half h of the
+// column index b (b = 2h, 2h + 1), so the link products are computed for two
+// spins only and each thread keeps 16 accumulators; FP64 loads L one Dirac row
+// at a time to stay within two resident blocks per SM.
+constexpr int kOneDK = 8;           // sites per thread
+constexpr int kOneDLanes = 32;      // sites side by side in a block (x 8 warps)
 constexpr int kOneDChunk = kOneDLanes * kOneDK;
 
 __device__ __forceinline__ int sel4(const int (&a)[4], int mu) {
   return mu == 0 ? a[0] : mu == 1 ? a[1] : mu == 2 ? a[2] : a[3];
 }
 
-// w = U r (ADJ: U^dag r) for the 4 spins of a spinor; SUB: w -= (...) instead
-template <bool ADJ, bool SUB = false, class R>
-__device__ __forceinline__ void link_times(Cx<R> (&w)[12], const Mat3<R>& U, const Cx<R> (&r)[12]) {
+// components 6h .. 6h + 5 (spins 2h, 2h + 1) of a site's spinor
+template <class S>
+__device__ __forceinline__ void load_spins2(Cx<typename Prec<S>::R> (&v)[6], const void* field, size_t b0,
+                                           size_t cs, int h) {
+  using R = typename Prec<S>::R;
+  const uint4* f = reinterpret_cast<const uint4*>(field);
+  if constexpr (std::is_same<S, double>::value) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < 6; ++j) {
+      const double2 d = reinterpret_cast<const double2*>(f)[b0 + (6 * h + j) * cs];
+      v[j] = {d.x, d.y};
+    }
+  } else if constexpr (std::is_same<S, float>::value) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float4 d = reinterpret_cast<const float4*>(f)[b0 + (3 * h + j) * cs];
+      v[2 * j] = {d.x, d.y};
+      v[2 * j + 1] = {d.z, d.w};
+    }
+  } else {
+    using P2 = typename Pair<S>::T;
+    Cx<R> e[8];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint4 d = f[b0 + (h + j) * cs];
+      const P2* q = reinterpret_cast<const P2*>(&d);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 z = h2f(q[k]);
+        e[4 * j + k] = {z.x, z.y};
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = h ? e[2 + j] : e[j];
+  }
+}
+
+// w (+/-)= U r or U^dag r for two spins (four FMAs per complex multiply-add)
+template <bool ADJ, bool SUB, class R>
+__device__ __forceinline__ void link_times2(Cx<R> (&w)[6], const Mat3<R>& U, const Cx<R> (&r)[6]) {
+  using O = Ar<R>;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      Cx<R> z = {0, 0};
+      R zr = SUB ? w[3 * a + c].re : (R)0, zi = SUB ? w[3 * a + c].im : (R)0;
+      const R sg = SUB ? (R)-1 : (R)1;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) z = z + (ADJ ? cmulc(U.m[d][c], r[3 * a + d]) : U.m[c][d] * r[3 * a + d]);
-      w[3 * a + c] = SUB ? w[3 * a + c] - z : z;
+      for (int d = 0; d < 3; ++d) {
+        const Cx<R> u = ADJ ? conjx(U.m[d][c]) : U.m[c][d];
+        const Cx<R> x = r[3 * a + d];
+        zr = O::fma(sg * u.re, x.re, zr);
+        zr = O::fma(-sg * u.im, x.im, zr);
+        zi = O::fma(sg * u.re, x.im, zi);
+        zi = O::fma(sg * u.im, x.re, zi);
+      }
+      w[3 * a + c] = {zr, zi};
     }
 }
 
-// acc_{ab} += sgn * sum_c conj(l_{ac}) w_{bc}
-template <class R>
-__device__ __forceinline__ void outer_acc(R (&acc)[32], const Cx<R> (&l)[12], const Cx<R> (&w)[12], R sgn) {
+// acc_{a, bb} += sgn * sum_c conj(l_{a c}) w_{bb c}, a = 0..3, bb = 0..1; FP64 reads
+// one row of L at a time
+template <class S, class R>
+__device__ __forceinline__ void outer_acc2(R (&acc)[16], const void* Lf, size_t b0, size_t cs,
+                                           const Cx<R> (&w)[6], R sgn) {
+  using O = Ar<R>;
+  Cx<R> ws[6];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int j = 0; j < 6; ++j) ws[j] = {sgn * w[j].re, sgn * w[j].im};
+  if constexpr (std::is_same<S, double>::value) {
+    const double2* f = reinterpret_cast<const double2*>(Lf);
+#pragma unroll 1
+    for (int a = 0; a < 4; ++a) {
+      Cx<R> l[3];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      Cx<R> m = {0, 0};
+      for (int c = 0; c < 3; ++c) {
+        const double2 d = f[b0 + (3 * a + c) * cs];
+        l[c] = {d.x, d.y};
+      }
+      // a runtime index into acc would move it to local memory: select instead
 #pragma unroll
-      for (int c = 0; c < 3; ++c) m = m + cmulc(l[3 * a + c], w[3 * b + c]);
-      acc[2 * (4 * a + b)] += sgn * m.re;
-      acc[2 * (4 * a + b) + 1] += sgn * m.im;
+      for (int aa = 0; aa < 4; ++aa) {
+        if (aa != a) continue;
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+          R mr = acc[2 * (2 * aa + bb)], mi = acc[2 * (2 * aa + bb) + 1];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            mr = O::fma(l[c].re, ws[3 * bb + c].re, mr);
+            mr = O::fma(l[c].im, ws[3 * bb + c].im, mr);
+            mi = O::fma(l[c].re, ws[3 * bb + c].im, mi);
+            mi = O::fma(-l[c].im, ws[3 * bb + c].re, mi);
+          }
+          acc[2 * (2 * aa + bb)] = mr;
+          acc[2 * (2 * aa + bb) + 1] = mi;
+        }
+      }
     }
+  } else {
+    Cx<R> l[12];
+    load_spinor<S>(l, Lf, b0, cs);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        R mr = acc[2 * (2 * a + bb)], mi = acc[2 * (2 * a + bb) + 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const Cx<R> x = l[3 * a + c];
+          mr = O::fma(x.re, ws[3 * bb + c].re, mr);
+          mr = O::fma(x.im, ws[3 * bb + c].im, mr);
+          mi = O::fma(x.re, ws[3 * bb + c].im, mi);
+          mi = O::fma(-x.im, ws[3 * bb + c].re, mi);
+        }
+        acc[2 * (2 * a + bb)] = mr;
+        acc[2 * (2 * a + bb) + 1] = mi;
+      }
+  }
 }
+
+// v[0..15] per lane in; lane l returns the warp sum of component l & 15
+template <class T>
+__device__ __forceinline__ T warp_transpose_reduce16(T (&v)[16]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(full, v[i], 16);
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const T send = up ? v[i] : v[i + w];
+      const T keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(full, send, w);
+    }
+  }
+  return v[0];
+}
+
+template <class S>
+constexpr int oned_min_blocks() { return std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value ? 3 : 2; }
 
 template <class S, int RECON>
-__global__ void __launch_bounds__(256) oneD_partial_kernel(Geom g, const void* links, const void* Lf,
-                                                           const void* Rf, int nchunk,
-                                                           double* partial) {
+__global__ void __launch_bounds__(256, oned_min_blocks<S>()) oneD_partial_kernel(
+    Geom g, const void* links, const void* Lf, const void* Rf, int nchunk, double* partial) {
   using R = typename Prec<S>::R;
   const int chunk = blockIdx.x;
   const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
   const int rhs = blockIdx.z;
-  const int mu = threadIdx.y;
+  const int mu = threadIdx.y >> 1, h = threadIdx.y & 1;
   const int opar = par ^ 1;
   const size_t cs = (size_t)g.Vh;
-  R acc[32];
+  R acc[16];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0;
+  for (int j = 0; j < 16; ++j) acc[j] = 0;
   const int Lmu = sel4(g.L, mu), smu = sel4(g.stride, mu);
 #pragma unroll 1
   for (int k = 0; k < kOneDK; ++k) {
@@ -225,41 +342,41 @@ __global__ void __launch_bounds__(256) oneD_partial_kernel(Geom g, const void* l
     const Site s = site_of(g, par, cb);
     const int cmu = sel4(s.c, mu);
     const int lf = cmu + 1 < Lmu ? s.lex + smu : s.lex - (Lmu - 1) * smu;
-    Cx<R> l[12], r[12], w[12];
-    const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
+    const size_t bx = SpinorRef<S>::base(g, rhs, par, cb);
+    const size_t bf = SpinorRef<S>::base(g, rhs, opar, lf >> 1);
+    Cx<R> r[6], w[6];
     if (mu < 3) {
       const int lb = cmu > 0 ? s.lex - smu : s.lex + (Lmu - 1) * smu;
-      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
-      link_times<false>(w, U, r);
-      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lb >> 1), cs);
-      const Mat3<R> Ub = load_link<S, RECON>(links, g, mu, opar, lb >> 1);
-      link_times<true, true>(w, Ub, r);
-      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
-      outer_acc(acc, l, w, (R)1);
+      {
+        const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
+        load_spins2<S>(r, Rf, bf, cs, h);
+        link_times2<false, false>(w, U, r);
+      }
+      {
+        const Mat3<R> Ub = load_link<S, RECON>(links, g, mu, opar, lb >> 1);
+        load_spins2<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lb >> 1), cs, h);
+        link_times2<true, true>(w, Ub, r);
+      }
+      outer_acc2<S>(acc, Lf, bx, cs, w, (R)1);
     } else {
       const R sf = (g.antiperiodic && cmu == Lmu - 1) ? (R)-1 : (R)1;
-      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
-      link_times<false>(w, U, r);
-      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, par, cb), cs);
-      outer_acc(acc, l, w, sf);
-      load_spinor<S>(r, Rf, SpinorRef<S>::base(g, rhs, par, cb), cs);
-      link_times<true>(w, U, r);
-      load_spinor<S>(l, Lf, SpinorRef<S>::base(g, rhs, opar, lf >> 1), cs);
-      outer_acc(acc, l, w, -sf);
+      const Mat3<R> U = load_link<S, RECON>(links, g, mu, par, cb);
+      load_spins2<S>(r, Rf, bf, cs, h);
+      link_times2<false, false>(w, U, r);
+      outer_acc2<S>(acc, Lf, bx, cs, w, sf);
+      load_spins2<S>(r, Rf, bx, cs, h);
+      link_times2<true, false>(w, U, r);
+      outer_acc2<S>(acc, Lf, bf, cs, w, -sf);
     }
   }
-  const R v = warp_transpose_reduce(acc);
-  // 8 warps: warps 2*mu and 2*mu + 1 hold direction mu
-  __shared__ double sh[8][32];
-  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  sh[warp][threadIdx.x & 31] = (double)v;
-  __syncthreads();
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if (tid < 128) {
-    const int m2 = tid >> 5, j = tid & 31;
-    const double s2 = sh[2 * m2][j] + sh[2 * m2 + 1][j];
+  const R v = warp_transpose_reduce16(acc);
+  const int lane = threadIdx.x & 31;
+  if (lane < 16) {
+    // local component 2 (2a + bb) + re/im  ->  global 2 (4a + 2h + bb) + re/im
+    const int ab = lane >> 1, a = ab >> 1, bb = ab & 1;
+    const int comp = 2 * (4 * a + 2 * h + bb) + (lane & 1);
     const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
-    partial[slot * 128 + tid] = s2;  // [mu][32]
+    partial[slot * 128 + mu * 32 + comp] = (double)v;
   }
 }
 
@@ -389,6 +506,8 @@ tm_status_t local_contract_into(const Geom& g, const void* left, const void* rig
                                 int nrhs, int p_g5, double* out, double* scratch, cudaStream_t s) {
   const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
   const dim3 grid(nchunk, 2 * g.L[3], nrhs);
+  static const char* const kNames[4] = {"local.f64", "local.f32", "local.f16", "local.bf16"};
+  TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nrhs);
   tm_status_t st = by_prec_c(prec, [&](auto tag) {
     using S = decltype(tag);
     local_partial_kernel<S><<<grid, 256, 0, s>>>(g, left, right, nchunk, scratch);
@@ -439,9 +558,13 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   tm_status_t st = scratch_alloc((void**)&scratch, sizeof(double) * 128 * (size_t)nrhs * g.L[3] * 2 * nchunk, s);
   if (st != TM_OK) return st;
   const dim3 grid(nchunk, 2 * g.L[3], nrhs);
-  const dim3 block(kOneDLanes, 4);
+  const dim3 block(kOneDLanes, 8);
   const bool r12 = op->recon == 12;
   const void* links = op->links[prec];
+  static const char* const kNames[4] = {"oneD.f64", "oneD.f32", "oneD.f16", "oneD.bf16"};
+  const double esz = (double)prec_size(prec);
+  const double lreals = (prec == TM_PREC_F64 || !r12) ? 18.0 : 12.0;
+  TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * esz * 2.0 * g.Vh, 4.0 * lreals * esz * 2.0 * g.Vh, nrhs);
   switch (prec) {
     case TM_PREC_F64:
       oneD_partial_kernel<double, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch); break;

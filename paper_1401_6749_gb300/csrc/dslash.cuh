@@ -139,8 +139,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Minimum resident blocks per SM requested from the compiler (caps the
+// registers per thread).  The narrow formats are latency/issue bound and gain
+// from occupancy: measured at 32^3 x 64, 16 systems, 8 blocks (64 registers)
+// is fastest for FP16/BF16 in the solver's half-lattice launches, 6 for FP32;
+// FP64 is arithmetic bound and keeps its registers.  TM_DSLASH_MINBLOCKS
+// overrides at build time.
+template <class S>
+constexpr int dslash_min_blocks() {
+#ifdef TM_DSLASH_MINBLOCKS
+  return TM_DSLASH_MINBLOCKS;
+#else
+  return std::is_same<S, double>::value ? 1 : (std::is_same<S, float>::value ? 6 : 8);
+#endif
+}
+
 template <class S, int RECON, bool DAG, int EPI, int NR>
-__global__ void __launch_bounds__(128) dslash_kernel(const DslashArgs a) {
+__global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(const DslashArgs a) {
   using R = typename Prec<S>::R;
   using O = Ar<R>;
   const Geom& g = a.g;

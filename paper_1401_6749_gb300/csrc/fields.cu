@@ -323,6 +323,7 @@ __global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* s
 tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
                  const int* active, int nrhs, int par0, int npar, cudaStream_t s) {
   const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
+  TraceScope tr(s, "blas.xpay", 3.0 * 24.0 * prec_size(prec) * npar * g.Vh, 0.0, nrhs);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
     xpay_kernel<S><<<nb, 256, 0, s>>>(g, p, r, beta, active, nrhs, par0, npar);
@@ -502,6 +503,7 @@ extern "C" tm_status_t z4_noise(const tm_geom_t* gg, void* eta, tm_prec_t prec, 
   const Geom g = make_geom(gg->L, 1);
   const unsigned nb = blocks_for(2L * g.Vh * nsrc, 256);
   const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  TraceScope tr((cudaStream_t)s, "z4_noise", 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nsrc);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
     z4_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, eta, key, first_src, nsrc);

@@ -312,7 +312,22 @@ tm_status_t check_launch(const char* what);
 // event with the launch's algorithmic bytes per active system and per launch.
 int* trace_begin(cudaStream_t s, cudaEvent_t* ev0);
 void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
-               double fixed_bytes);
+               double fixed_bytes, int nrhs_if_uncounted = 0);
+
+// RAII form for kernels that do not count their active systems: all nrhs
+// systems are taken as active.
+struct TraceScope {
+  cudaStream_t s;
+  const char* name;
+  cudaEvent_t ev = nullptr;
+  double per_rhs, fixed;
+  int nrhs;
+  TraceScope(cudaStream_t st, const char* n, double bytes_per_rhs, double fixed_bytes, int nr)
+      : s(st), name(n), per_rhs(bytes_per_rhs), fixed(fixed_bytes), nrhs(nr) {
+    trace_begin(s, &ev);
+  }
+  ~TraceScope() { trace_end(s, name, ev, nullptr, per_rhs, fixed, nrhs); }
+};
 
 
 }  // namespace tml

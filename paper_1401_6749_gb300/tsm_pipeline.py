@@ -25,7 +25,7 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
-                 tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=8,
+                 tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
                  delta=0.1, kinds=KINDS, schur=True):
         self.op = op
         self.L = op.L
@@ -81,8 +81,10 @@ class TsmPipeline:
         the sources of all ranks (one all-gather of the per-source loops)."""
         n_all = self.n_hp + self.n_lp
         self.stats_lp, self.stats_hp = [], []
+        # the truncated solves stop after a handful of iterations: poll often so
+        # that no masked-out iterations are launched past convergence
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
-                                 check_every=self.check_every, schur=self.schur)
+                                 check_every=min(2, self.check_every), schur=self.schur)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
             self.stats_lp += self._solve_and_contract(self._lp, self.lp_prec, self.first + b0, n,
