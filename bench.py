@@ -414,6 +414,65 @@ def run_dslash(args):
     op.close()
 
 
+# ------------------------------------------------------- widened rows
+def run_next(args):
+    """Time the widened rows on 16 systems at the workload's lattice: the HPE
+    remainder (BH)^4 s (Sec. 2.4), time-diluted Z4 sources (Sec. 2.3) and
+    momentum-projected local loops with 8 momenta; prints one JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_6749_gb300 import synth
+    from paper_1401_6749_gb300 import tmloops as tl
+    c = CONFIGS[args.config]
+    L = c["L"]
+    V = int(np.prod(L))
+    n = 16
+    prec = tl.PREC[c["lp_prec"]]
+    esz = tl.ELEM_SIZE[prec]
+    U = synth.gauge_field(L, c["gauge_seed"], device="cuda")
+    op = tl.Operator(L, c["kappa"], c["mu"], torch.from_numpy(U.view(np.float64)).cuda(), recon=c["recon"])
+    del U
+    a = tl.empty_field(L, prec, n)
+    b = tl.empty_field(L, prec, n)
+    tl.z4_noise(L, a, prec, 7, 0, n)
+    moms = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+    T = L[3]
+    out = torch.empty(n * len(moms) * 16 * T * 2, dtype=torch.float64, device="cuda")
+    jobs = {
+        "hpe_BH4": lambda: tl.tm_hpe_apply(op, b, a, n, 4, prec),
+        "z4_time_diluted": lambda: tl.z4_noise_diluted(L, b, prec, 7, 0, n, 3, 8),
+        "local_mom8": lambda: tl.loop_contract_local_mom(L, a, b, prec, n, tl.LOOP_STD, moms, out),
+    }
+    res = {}
+    for name, fn in jobs.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = {"ms": round(e0.elapsed_time(e1) / args.steps, 4)}
+    spin = 24 * esz * V
+    link = 4 * (18 if c["recon"] == 18 else 12) * esz * V
+    nbytes = {"hpe_BH4": 4 * (n * 2 * spin + link), "z4_time_diluted": n * spin, "local_mom8": n * 2 * spin}
+    peak, src = _peaks()
+    for k, v in res.items():
+        gbs = nbytes[k] / (v["ms"] * 1e-3) / 1e9
+        v["GBps"] = round(gbs, 1)
+        v["frac_of_hbm"] = round(gbs / peak, 4)
+    t0 = time.perf_counter()
+    tl.tm_hpe_exact(L, c["kappa"], c["mu"])
+    res["hpe_exact_terms_host_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    print(json.dumps({"mode": "next", "lattice": list(L), "nrhs": n, "prec": c["lp_prec"],
+                      "peak_source": src, "kernels": res}), flush=True)
+    op.close()
+
+
 # ----------------------------------------------------------------- oracle
 def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
     """Time the FP64 oracle, as it stands, on a bounded sample: one M^dag M
@@ -494,6 +553,7 @@ def main():
     ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
+    ap.add_argument("--next", action="store_true", help="time HPE, time dilution, momentum projection")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16"])
@@ -513,6 +573,8 @@ def main():
         c["hp_inner"] = args.hp_inner
     if args.dslash:
         run_dslash(args)
+    elif args.next:
+        run_next(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -120,6 +120,28 @@ tm_status_t tm_dslash(tm_op_t *op, void *out, const void *in, int nrhs, int dagg
 tm_status_t z4_noise(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t seed,
                      uint32_t first_src, int nsrc, tm_stream_t s);
 
+/* Time dilution with coherent sources (Sec. 2.3): the same Z4 noise as
+ * z4_noise on the time slices t = t0 (mod dt), zero on all others (dt = T: one
+ * slice; dt < T: coherent sources on slices dt apart).  The diluted sources
+ * t0 = 0 .. dt-1 add up to the undiluted one.  1 <= dt, 0 <= t0 < dt.     */
+tm_status_t z4_noise_diluted(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t seed,
+                             uint32_t first_src, int nsrc, int t0, int dt, tm_stream_t s);
+
+/* Hopping Parameter Expansion (Sec. 2.4, Eqs. 7-8).  With B = (1 + i nu g5)^-1
+ * and H = M - B^-1 (-kappa times the hops of M),
+ *   M^-1 = B - B H B + (BH)^2 B - (BH)^3 B + (BH)^4 M^-1.
+ * tm_hpe_apply: out = (BH)^order in (nrhs internal fields of precision prec;
+ *   out and in must not overlap; uses stream-ordered scratch of one field set).
+ * tm_hpe_exact: the exact part of the local loops, Tr_t[Gamma_g (B - BHB +
+ *   (BH)^2 B - (BH)^3 B)] for every time slice, written to the HOST array
+ *   out[16][T][2]; the odd orders vanish on the diagonal and the rest is gauge
+ *   independent when every extent is >= 4 (TM_ERR_UNSUPPORTED otherwise).
+ * The HPE estimate of Tr_t[Gamma M^-1] is tm_hpe_exact plus the standard
+ * contraction (L = eta, R = (BH)^4 s, TM_LOOP_STD) averaged over sources.   */
+tm_status_t tm_hpe_apply(tm_op_t *op, void *out, const void *in, int nrhs, int order,
+                         tm_prec_t prec, tm_stream_t s);
+tm_status_t tm_hpe_exact(const tm_params_t *p, double *out);
+
 /* Conjugate gradient on the normal equations (Sec. 2.1: "a CG solver"):
  *   M^dag M x = M^dag eta,  x_0 = 0,  so that x = M^{-1} eta = s (Eq. 3);
  * stop when the iterated residual satisfies |r| <= tol |M^dag eta|.
@@ -186,6 +208,15 @@ tm_status_t loop_contract_local(const tm_geom_t *g, const void *left, const void
 tm_status_t loop_contract_oneD(tm_op_t *op, const void *left, const void *right,
                                tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
                                double *out, tm_stream_t s);
+
+/* Momentum-projected local loops:
+ *   out[r][q][g][t] = sum_{x_t = t} exp(-i p_q . x) L_r(x)^dag (P Gamma_g) R_r(x),
+ *   p_q = 2 pi (n_x / X, n_y / Y, n_z / Z),  mom = host array [n_mom][3] of (n_x, n_y, n_z)
+ * (the paper computes zero-momentum loops; 1 <= n_mom <= 64, nrhs * n_mom <= 65535).
+ * out: device [nrhs][n_mom][16][T][2].                                      */
+tm_status_t loop_contract_local_mom(const tm_geom_t *g, const void *left, const void *right,
+                                    tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                    const int *mom, int n_mom, double *out, tm_stream_t s);
 
 /* Same computation and result as loop_contract_local, for callers that cannot
  * allocate device memory: e.g. an application whose own memory manager has

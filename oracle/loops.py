@@ -92,3 +92,19 @@ def oneD_loops(U, L, R, mode, antiperiodic=True):
                 + _bilinear_per_site(L_m, G16, _colour(U_xm, R)))
         out.append(0.25 * _slice_sum(site))
     return np.stack(out, axis=-3)
+
+
+def local_loops_mom(L, R, mode, momenta):
+    """Momentum-projected local loops: sum_{x in t} exp(-i p.x) L^dag (P Gamma) R(x),
+    p = 2 pi (n_x/X, n_y/Y, n_z/Z); returns (..., n_mom, 16, T)."""
+    L = np.asarray(L)
+    R = np.asarray(R)
+    T, Z, Y, X = L.shape[-6:-2]
+    G16 = np.einsum("ab,gbc->gac", mode_matrix(mode), gamma_basis())
+    site = _bilinear_per_site(L, G16, R)          # (g, ..., T, Z, Y, X)
+    z, y, x = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    out = []
+    for n in momenta:
+        ph = np.exp(-2j * np.pi * (n[0] * x / X + n[1] * y / Y + n[2] * z / Z))
+        out.append(_slice_sum(site * ph))
+    return np.stack(out, axis=-3)

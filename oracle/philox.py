@@ -73,3 +73,12 @@ def z4_noise(L, seed, first_src, nsrc):
                 k = ((w0 >> sh) & np.uint64(3)).astype(np.int64)
                 out[j, :, alpha, c] = phases[k]
     return out.reshape(nsrc, T, Z, Y, X, 4, 3)
+
+
+def z4_noise_diluted(L, seed, first_src, nsrc, t0, dt):
+    """Time dilution with coherent sources (Sec. 2.3): the Z4 source on the time
+    slices t = t0 (mod dt), zero elsewhere."""
+    eta = z4_noise(L, seed, first_src, nsrc)
+    T = int(L[3])
+    mask = ((np.arange(T) - t0) % dt == 0).astype(np.float64)
+    return eta * mask[None, :, None, None, None, None, None]

@@ -19,42 +19,6 @@
 
 namespace tml {
 
-// ------------------------------------------------------- Gamma tables
-// gamma_mu rows as (column, i^k): upper rows from A_mu, lower rows from B_mu.
-struct GammaTab {
-  unsigned char perm[16][4];
-  unsigned char k[16][4];
-};
-
-static GammaTab make_gamma_tab() {
-  // DeGrand-Rossi gamma_1..4 as phased permutations (row -> column, phase i^k)
-  const int gp[4][4] = {{3, 2, 1, 0}, {3, 2, 1, 0}, {2, 3, 0, 1}, {2, 3, 0, 1}};
-  const int gk[4][4] = {{1, 1, 3, 3}, {2, 0, 0, 2}, {1, 3, 3, 1}, {0, 0, 0, 0}};
-  GammaTab t;
-  for (int n = 0; n < 16; ++n) {
-    int perm[4] = {0, 1, 2, 3}, ph[4] = {0, 0, 0, 0};
-    for (int m = 0; m < 4; ++m) {
-      if (!((n >> m) & 1)) continue;
-      // (X gamma_m): row a -> column gp[m][perm[a]], phase ph[a] + gk[m][perm[a]]
-      for (int a = 0; a < 4; ++a) {
-        const int c = perm[a];
-        ph[a] = (ph[a] + gk[m][c]) & 3;
-        perm[a] = gp[m][c];
-      }
-    }
-    for (int a = 0; a < 4; ++a) {
-      t.perm[n][a] = (unsigned char)perm[a];
-      t.k[n][a] = (unsigned char)ph[a];
-    }
-  }
-  return t;
-}
-
-static const GammaTab& gamma_tab() {
-  static const GammaTab t = make_gamma_tab();
-  return t;
-}
-
 // ------------------------------------------------------- warp butterfly
 // v[0..31] per lane in, lane l returns the warp sum of component l.
 template <class T>
@@ -78,13 +42,26 @@ __device__ __forceinline__ T warp_transpose_reduce(T (&v)[32]) {
 constexpr int kLocalK = 4;          // sites per thread
 constexpr int kLocalChunk = 256 * kLocalK;
 
-template <class S>
+// momenta of a projected contraction: p = 2 pi (n_x / X, n_y / Y, n_z / Z)
+constexpr int kMaxMom = 64;
+struct MomList {
+  int n;
+  int p[kMaxMom][3];
+};
+
+// MOM: the site's R is multiplied by exp(-i p.x), block z = rhs * n + momentum
+template <class S, bool MOM = false>
 __global__ void __launch_bounds__(256) local_partial_kernel(Geom g, const void* Lf, const void* Rf,
-                                                            int nchunk, double* partial) {
+                                                            int nchunk, double* partial,
+                                                            MomList mom = MomList{}) {
   using R = typename Prec<S>::R;
-  const int chunk = blockIdx.x;
+  // MOM: the momentum is the fastest block index, so the blocks of one chunk
+  // (one set of sites) for all momenta run together and re-read L, R from L2
+  const int q = MOM ? (int)blockIdx.x % mom.n : 0;
+  const int chunk = MOM ? (int)blockIdx.x / mom.n : (int)blockIdx.x;
   const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
   const int rhs = blockIdx.z;
+  const int slot_rhs = MOM ? rhs * mom.n + q : rhs;  // index of this contraction's output
   R acc[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0;
@@ -96,6 +73,21 @@ __global__ void __launch_bounds__(256) local_partial_kernel(Geom g, const void* 
       Cx<R> l[12], r[12];
       load_spinor<S>(l, Lf, b0, (size_t)g.Vh);
       load_spinor<S>(r, Rf, b0, (size_t)g.Vh);
+      if constexpr (MOM) {
+        const Site st = site_of(g, par, t * g.V3h + i);
+        // phase -2 pi sum_k n_k x_k / L_k, reduced exactly modulo one turn first
+        const long num = (long)((mom.p[q][0] * st.c[0]) % g.L[0]) * g.L[1] * g.L[2] +
+                         (long)((mom.p[q][1] * st.c[1]) % g.L[1]) * g.L[0] * g.L[2] +
+                         (long)((mom.p[q][2] * st.c[2]) % g.L[2]) * g.L[0] * g.L[1];
+        const long den = (long)g.L[0] * g.L[1] * g.L[2];
+        const double frac = (double)(num % den) / (double)den;
+        R sn, cn;
+        if constexpr (std::is_same<R, double>::value) sincospi(-2.0 * frac, &sn, &cn);
+        else sincospif(-2.0f * (float)frac, &sn, &cn);
+        const Cx<R> ph = {cn, sn};
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = ph * r[k];
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -116,7 +108,7 @@ __global__ void __launch_bounds__(256) local_partial_kernel(Geom g, const void* 
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s += sh[w][threadIdx.x];
-    const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
+    const size_t slot = (((size_t)slot_rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
     partial[slot * 32 + threadIdx.x] = s;
   }
 }
@@ -540,6 +532,51 @@ extern "C" tm_status_t loop_contract_local(const tm_geom_t* gg, const void* left
   tm_status_t st = scratch_alloc((void**)&scratch, local_scratch_bytes(g, nrhs), s);
   if (st != TM_OK) return st;
   st = local_contract_into(g, left, right, prec, nrhs, mode != TM_LOOP_STD, out, scratch, s);
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+extern "C" tm_status_t loop_contract_local_mom(const tm_geom_t* gg, const void* left, const void* right,
+                                               tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
+                                               const int* mom, int n_mom, double* out, tm_stream_t strm) {
+  if (!gg || !left || !right || !out || !mom || nrhs < 0) { set_error("loop_contract_local_mom: null argument"); return TM_ERR_ARG; }
+  if (!valid_mode(mode)) { set_error("loop_contract_local_mom: unknown mode %d", (int)mode); return TM_ERR_ARG; }
+  if (n_mom < 1 || n_mom > kMaxMom) { set_error("loop_contract_local_mom: 1 <= n_mom <= %d", kMaxMom); return TM_ERR_ARG; }
+  if ((int)prec < 0 || (int)prec > 3) { set_error("loop_contract_local_mom: unknown precision"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nrhs == 0) return TM_OK;
+  if ((long)nrhs * n_mom > 65535) { set_error("loop_contract_local_mom: nrhs * n_mom must be <= 65535"); return TM_ERR_ARG; }
+  const cudaStream_t s = (cudaStream_t)strm;
+  const Geom g = make_geom(gg->L, 1);
+  MomList ml;
+  ml.n = n_mom;
+  for (int q = 0; q < n_mom; ++q)
+    for (int k = 0; k < 3; ++k) {
+      const int Lk = g.L[k];
+      ml.p[q][k] = ((mom[3 * q + k] % Lk) + Lk) % Lk;  // p and p + L are the same momentum
+    }
+  const int n2 = nrhs * n_mom;
+  double* scratch = nullptr;
+  tm_status_t st = scratch_alloc((void**)&scratch, local_scratch_bytes(g, n2), s);
+  if (st != TM_OK) return st;
+  const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
+  const dim3 grid(nchunk * n_mom, 2 * g.L[3], nrhs);
+  {
+    static const char* const kNames[4] = {"localmom.f64", "localmom.f32", "localmom.f16", "localmom.bf16"};
+    TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, n2);
+    st = by_prec_c(prec, [&](auto tag) {
+      using S = decltype(tag);
+      local_partial_kernel<S, true><<<grid, 256, 0, s>>>(g, left, right, nchunk, scratch, ml);
+      count_launch();
+      return check_launch("loop_contract_local_mom");
+    });
+  }
+  if (st == TM_OK) {
+    local_final_kernel<<<dim3(g.L[3], n2), 32, 0, s>>>(scratch, nchunk, g.L[3], gamma_tab(),
+                                                        mode != TM_LOOP_STD, out);
+    count_launch();
+    st = check_launch("loop_contract_local_mom final");
+  }
   cudaFreeAsync(scratch, s);
   return st;
 }

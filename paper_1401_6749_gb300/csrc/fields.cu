@@ -151,23 +151,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// dt > 0: time dilution, noise only on slices t = t0 (mod dt), zero elsewhere
 template <class S>
-__global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc) {
+__global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc, int t0, int dt) {
   const long V = 2L * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V * nsrc) return;
   const int j = (int)(i / V);
   const int lex = (int)(i % V);
-  const uint4 w = philox4x32_10(make_uint4((uint32_t)lex, first + (uint32_t)j, 0u, 0u), key);
+  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
+  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+  const bool on = dt <= 0 || ((t - t0) % dt + dt) % dt == 0;
+  const uint4 w = on ? philox4x32_10(make_uint4((uint32_t)lex, first + (uint32_t)j, 0u, 0u), key)
+                     : make_uint4(0u, 0u, 0u, 0u);
   Cx<double> v[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int q = (int)((w.x >> (2 * k)) & 3u);  // component k = 3*alpha + colour
-    v[k] = q == 0 ? Cx<double>{1, 0} : q == 1 ? Cx<double>{0, 1} : q == 2 ? Cx<double>{-1, 0}
+    v[k] = !on ? Cx<double>{0, 0}
+         : q == 0 ? Cx<double>{1, 0} : q == 1 ? Cx<double>{0, 1} : q == 2 ? Cx<double>{-1, 0}
                                                                           : Cx<double>{0, -1};
   }
-  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
-  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
   const int par = (x + y + z + t) & 1;
   store_spinor_f64<S>(eta, SpinorRef<S>::base(g, j, par, lex >> 1), (size_t)g.Vh, v);
 }
@@ -495,8 +499,25 @@ extern "C" tm_status_t tm_gamma5(const tm_geom_t* gg, void* out, const void* in,
   });
 }
 
+static tm_status_t z4_launch(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,
+                             uint32_t first_src, int nsrc, int t0, int dt, tm_stream_t s);
+
 extern "C" tm_status_t z4_noise(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,
                                 uint32_t first_src, int nsrc, tm_stream_t s) {
+  return z4_launch(gg, eta, prec, seed, first_src, nsrc, 0, 0, s);
+}
+
+extern "C" tm_status_t z4_noise_diluted(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,
+                                        uint32_t first_src, int nsrc, int t0, int dt, tm_stream_t s) {
+  if (!gg || dt < 1 || t0 < 0 || t0 >= dt) {
+    set_error("z4_noise_diluted: need 1 <= dt and 0 <= t0 < dt");
+    return TM_ERR_ARG;
+  }
+  return z4_launch(gg, eta, prec, seed, first_src, nsrc, t0, dt, s);
+}
+
+static tm_status_t z4_launch(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,
+                             uint32_t first_src, int nsrc, int t0, int dt, tm_stream_t s) {
   if (!gg || !eta || nsrc < 0) { set_error("z4_noise: null argument"); return TM_ERR_ARG; }
   if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
   if (nsrc == 0) return TM_OK;
@@ -506,7 +527,7 @@ extern "C" tm_status_t z4_noise(const tm_geom_t* gg, void* eta, tm_prec_t prec, 
   TraceScope tr((cudaStream_t)s, "z4_noise", 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nsrc);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    z4_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, eta, key, first_src, nsrc);
+    z4_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, eta, key, first_src, nsrc, t0, dt);
     count_launch();
     return check_launch("z4_noise");
   });

@@ -72,4 +72,41 @@ tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* r
 
 tm_status_t check_geom(const int L[4]);
 
+// ------------------------------------------------------- Gamma tables
+// gamma_mu rows as (column, i^k): upper rows from A_mu, lower rows from B_mu.
+struct GammaTab {
+  unsigned char perm[16][4];
+  unsigned char k[16][4];
+};
+
+inline GammaTab make_gamma_tab() {
+  // DeGrand-Rossi gamma_1..4 as phased permutations (row -> column, phase i^k)
+  const int gp[4][4] = {{3, 2, 1, 0}, {3, 2, 1, 0}, {2, 3, 0, 1}, {2, 3, 0, 1}};
+  const int gk[4][4] = {{1, 1, 3, 3}, {2, 0, 0, 2}, {1, 3, 3, 1}, {0, 0, 0, 0}};
+  GammaTab t;
+  for (int n = 0; n < 16; ++n) {
+    int perm[4] = {0, 1, 2, 3}, ph[4] = {0, 0, 0, 0};
+    for (int m = 0; m < 4; ++m) {
+      if (!((n >> m) & 1)) continue;
+      // (X gamma_m): row a -> column gp[m][perm[a]], phase ph[a] + gk[m][perm[a]]
+      for (int a = 0; a < 4; ++a) {
+        const int c = perm[a];
+        ph[a] = (ph[a] + gk[m][c]) & 3;
+        perm[a] = gp[m][c];
+      }
+    }
+    for (int a = 0; a < 4; ++a) {
+      t.perm[n][a] = (unsigned char)perm[a];
+      t.k[n][a] = (unsigned char)ph[a];
+    }
+  }
+  return t;
+}
+
+inline const GammaTab& gamma_tab() {
+  static const GammaTab t = make_gamma_tab();
+  return t;
+}
+
+
 }  // namespace tml

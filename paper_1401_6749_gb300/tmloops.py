@@ -73,6 +73,10 @@ _SIGS = {
     "loop_contract_oneD": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp],
     "loop_contract_local_noalloc": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
     "tsm_combine": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp, _vp],
+    "z4_noise_diluted": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _i, _i, _vp],
+    "tm_hpe_apply": [_vp, _vp, _vp, _i, _i, _i, _vp],
+    "tm_hpe_exact": [_P(tm_params_t), _vp],
+    "loop_contract_local_mom": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp],
     "tm_last_error": [],
     "tm_launch_count": [],
     "tm_trace_enable": [_i],
@@ -221,6 +225,36 @@ def tsm_combine(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, length, scale, mean, err, st
     scale = complex(scale)
     _check(_lib.tsm_combine(_ptr(l_hp), _ptr(l_lp_on_hp), int(n_hp), _ptr(l_lp), int(n_lp),
                             int(length), scale.real, scale.imag, _ptr(mean), _ptr(err), _stream(stream)))
+
+
+def z4_noise_diluted(L, eta, prec, seed, first_src, nsrc, t0, dt, stream=None):
+    _check(_lib.z4_noise_diluted(ctypes.byref(geom(L)), _ptr(eta), int(prec), int(seed), int(first_src),
+                                 int(nsrc), int(t0), int(dt), _stream(stream)))
+
+
+def tm_hpe_apply(op, out, inp, nrhs, order, prec, stream=None):
+    _check(_lib.tm_hpe_apply(op.handle, _ptr(out), _ptr(inp), int(nrhs), int(order), int(prec),
+                             _stream(stream)))
+
+
+def tm_hpe_exact(L, kappa, mu, antiperiodic=True):
+    """Exact HPE part of the local loops: numpy complex (16, T) (host computation)."""
+    import numpy as np
+    p = tm_params_t()
+    for i in range(4):
+        p.L[i] = int(L[i])
+    p.kappa, p.mu, p.antiperiodic_t, p.recon = float(kappa), float(mu), int(bool(antiperiodic)), 18
+    out = np.zeros((16, int(L[3]), 2), dtype=np.float64)
+    _check(_lib.tm_hpe_exact(ctypes.byref(p), out.ctypes.data_as(ctypes.c_void_p)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def loop_contract_local_mom(L, left, right, prec, nrhs, mode, momenta, out, stream=None):
+    import numpy as np
+    mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+    _check(_lib.loop_contract_local_mom(ctypes.byref(geom(L)), _ptr(left), _ptr(right), int(prec),
+                                        int(nrhs), int(mode), mom.ctypes.data_as(ctypes.c_void_p),
+                                        int(mom.shape[0]), _ptr(out), _stream(stream)))
 
 
 def tm_launch_count():
