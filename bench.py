@@ -339,10 +339,24 @@ def run_ours(args):
         e2e = {"value": round(ems * 1e-3 / (world * n_src), 6), "unit": "s/source",
                "h2d_bytes_per_step": int(U_host.numel() * 8), "d2h_bytes_per_step": int(res_bytes)}
 
-    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1).  The
+    # oracle's CG is unpreconditioned: its iteration counts per source are
+    # those of the unpreconditioned solver, measured here on one LP and one HP
+    # source (equal in exact arithmetic)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline(c, it_lp, it_hp)
+        e1 = tl.empty_field(L, tl.PREC[c["lp_prec"]], 1)
+        x1 = tl.empty_field(L, tl.PREC[c["lp_prec"]], 1)
+        tl.z4_noise(L, e1, tl.PREC[c["lp_prec"]], c["seed"], 0, 1)
+        _, s_lp = tl.tm_cg_solve(op, x1, e1, 1, tl.cg_params(c["tol_lp"], 20000, tl.CG_PLAIN,
+                                                             prec=tl.PREC[c["lp_prec"]]))
+        e2 = tl.empty_field(L, tl.F64, 1)
+        x2 = tl.empty_field(L, tl.F64, 1)
+        tl.z4_noise(L, e2, tl.F64, c["seed"], 0, 1)
+        _, s_hp = tl.tm_cg_solve(op, x2, e2, 1, tl.cg_params(c["tol_hp"], 20000, tl.CG_MIXED,
+                                                             inner_prec=tl.F32, delta=0.1))
+        n_lp_all = c["n_hp"] + c["n_lp"]
+        cpu = cpu_baseline(c, [s_lp[0]["iters"]] * n_lp_all, [s_hp[0]["iters"]] * c["n_hp"])
 
     if rank == 0:
         line = {
@@ -479,8 +493,9 @@ def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
     application (one CG iteration's operator work) and one source's local and
     one-derivative contractions in both one-end estimators, on a 16^3 x 32
     lattice with the workload's kappa and mu.  The per-site cost is scaled to
-    the workload's volume and combined with the measured iteration counts of
-    the LP and HP solves to give seconds per source."""
+    the workload's volume and combined with the iteration counts of the
+    oracle's (unpreconditioned) CG for the LP and HP solves to give seconds
+    per source."""
     import numpy as np
     from oracle import loops as oloops
     from oracle.operator import apply_DW, apply_M
@@ -506,7 +521,7 @@ def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
     return {"value": round(per_src, 3), "unit": "s/source", "cores": 1, "kind": "oracle",
             "sample": "numpy FP64 oracle on %dx%dx%dx%d: one M^dag M application %.2f s, "
                       "local+oneD contractions (vv, gen) of one source %.2f s; scaled by volume "
-                      "(x%g) and by the measured CG iterations of the step (%d LP + %d HP)"
+                      "(x%g) and by the unpreconditioned CG iterations of the step (%d LP + %d HP)"
                       % (Ls + (t_iter, t_con, scale, sum(it_lp), sum(it_hp)))}
 
 
@@ -545,8 +560,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ref-lp-iters", type=float, default=7)
-    ap.add_argument("--ref-hp-iters", type=float, default=60)
+    # unpreconditioned CG iterations per source of the 32^3 x 64 workload (the
+    # oracle's CG), as measured by the GPU path: LP to 1e-2, HP to 1e-9
+    ap.add_argument("--ref-lp-iters", type=float, default=16)
+    ap.add_argument("--ref-hp-iters", type=float, default=105)
     ap.add_argument("--schur", type=int, default=None, help="override even/odd preconditioning")
     ap.add_argument("--delta", type=float, default=None, help="override the reliable-update delta")
     ap.add_argument("--recon", type=int, default=None, choices=[12, 18])
