@@ -90,6 +90,31 @@ template <> struct Pair<__half> { using T = __half2; };
 template <> struct Pair<__nv_bfloat16> { using T = __nv_bfloat162; };
 
 // ----------------------------------------------------------------- geometry
+// Division of a 32-bit unsigned n by an invariant d with one multiply-high
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> 1)) >> (l - 1),
+// t = mulhi(m, n), exact for every n < 2^32 and d >= 2.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.l = l;
+  f.m = d <= 1 ? 0u : (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  if (f.d == 1) return n;
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
 struct Geom {
   int L[4];   // X, Y, Z, T
   int Xh;     // X / 2
@@ -97,6 +122,7 @@ struct Geom {
   int V3h;    // X*Y*Z / 2 (sites per parity and time slice)
   int stride[4];  // lexicographic strides 1, X, XY, XYZ
   int antiperiodic;
+  FastDiv dXh, dY, dZ;  // dividers for the checkerboard-index decomposition
 };
 
 inline Geom make_geom(const int L[4], int antiperiodic) {
@@ -110,6 +136,9 @@ inline Geom make_geom(const int L[4], int antiperiodic) {
   g.V3h = g.stride[3] / 2;
   g.Vh = g.V3h * L[3];
   g.antiperiodic = antiperiodic;
+  g.dXh = make_fastdiv((uint32_t)g.Xh);
+  g.dY = make_fastdiv((uint32_t)L[1]);
+  g.dZ = make_fastdiv((uint32_t)L[2]);
   return g;
 }
 
@@ -121,12 +150,13 @@ struct Site {
 
 __device__ __forceinline__ Site site_of(const Geom& g, int par, int cb) {
   Site s;
-  const int xh = cb % g.Xh;
-  int rest = cb / g.Xh;
-  s.c[1] = rest % g.L[1];
-  rest /= g.L[1];
-  s.c[2] = rest % g.L[2];
-  s.c[3] = rest / g.L[2];
+  const uint32_t q0 = fdiv((uint32_t)cb, g.dXh);
+  const int xh = cb - (int)q0 * g.Xh;
+  const uint32_t q1 = fdiv(q0, g.dY);
+  s.c[1] = (int)q0 - (int)q1 * g.L[1];
+  const uint32_t q2 = fdiv(q1, g.dZ);
+  s.c[2] = (int)q1 - (int)q2 * g.L[2];
+  s.c[3] = (int)q2;
   s.c[0] = 2 * xh + ((par + s.c[1] + s.c[2] + s.c[3]) & 1);
   s.lex = s.c[0] + g.stride[1] * s.c[1] + g.stride[2] * s.c[2] + g.stride[3] * s.c[3];
   return s;
