@@ -30,11 +30,11 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=3e-5, recon=12),
+                  seed=20140126, schur=True, delta=3e-5, recon=12, overlap=False),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126, schur=True, delta=3e-5, recon=12),
+                 seed=20140126, schur=True, delta=3e-5, recon=12, overlap=False),
 }
 
 PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -44,9 +44,10 @@ METRIC = "Dslash HBM GB/s and % roofline; TSM loop sec/source at fixed error vs 
 def workload_name(c):
     X, Y, Z, T = c["L"]
     return ("TSM loops %dx%dx%dx%d kappa=%g mu=%g: %d LP (%s, |r|<=%g) + %d HP (mixed %s/FP64, "
-            "|r|<=%g, delta=%g), batches of %d, %s CG, local+oneD x (one-end, generalised one-end)" % (
+            "|r|<=%g, delta=%g%s), batches of %d, %s CG, local+oneD x (one-end, generalised one-end)" % (
                 X, Y, Z, T, c["kappa"], c["mu"], c["n_lp"] + c["n_hp"], c["lp_prec"], c["tol_lp"],
-                c["n_hp"], c["hp_inner"], c["tol_hp"], c["delta"], c["batch"],
+                c["n_hp"], c["hp_inner"], c["tol_hp"], c["delta"],
+                ", on a second stream" if c.get("overlap") else "", c["batch"],
                 "even/odd-preconditioned" if c["schur"] else "unpreconditioned"))
 
 
@@ -220,7 +221,7 @@ def run_ours(args):
     mk = lambda o: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
                                hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
                                seed=c["seed"], first_src=rank * n_src, schur=c["schur"],
-                               delta=c["delta"])
+                               delta=c["delta"], overlap=c["overlap"])
     pipe = mk(op)
     _log("inputs ready")
     for _ in range(args.warmup):
@@ -567,6 +568,7 @@ def main():
     ap.add_argument("--schur", type=int, default=None, help="override even/odd preconditioning")
     ap.add_argument("--delta", type=float, default=None, help="override the reliable-update delta")
     ap.add_argument("--recon", type=int, default=None, choices=[12, 18])
+    ap.add_argument("--overlap", type=int, default=None, help="override HP/LP stream overlap")
     ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
@@ -580,6 +582,8 @@ def main():
         c["schur"] = bool(args.schur)
     if args.delta is not None:
         c["delta"] = args.delta
+    if args.overlap is not None:
+        c["overlap"] = bool(args.overlap)
     if args.recon is not None:
         c["recon"] = args.recon
     else:

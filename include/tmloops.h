@@ -90,6 +90,11 @@ typedef struct tm_op tm_op_t;
  * even/odd link arrays for every precision.  Blocks until done.            */
 tm_status_t tm_op_create(tm_op_t **op, const tm_params_t *p, const double *U_lex, tm_stream_t s);
 tm_status_t tm_op_destroy(tm_op_t *op);
+/* A second handle on the same operator: shares the source's link arrays (no
+ * copy) but has its own solver work space, so that solves on different host
+ * threads and streams can run concurrently.  Destroy clones before their
+ * source.  Calls on one handle must not overlap.                          */
+tm_status_t tm_op_clone(tm_op_t **out, const tm_op_t *src);
 
 /* Bytes of nrhs internal spinor fields of precision prec on geometry g. */
 size_t tm_spinor_bytes(const tm_geom_t *g, tm_prec_t prec, int nrhs);

@@ -81,3 +81,43 @@ def dense_matrix(U, kappa, mu, antiperiodic=True, dagger=False):
     basis = np.eye(n, dtype=np.complex128).reshape((n,) + tuple(site_shape) + (4, 3))
     cols = apply_M(U, basis, kappa, mu, antiperiodic, dagger)
     return cols.reshape(n, n).T.copy()
+
+
+def apply_M_sites(U, psi, kappa, mu, sites, antiperiodic=True, dagger=False):
+    """(M psi) evaluated only at the given sites, by the same formula as apply_M.
+
+    sites: integer array (n, 4) of (x, y, z, t); psi (..., T, Z, Y, X, 4, 3).
+    Returns (..., n, 4, 3).  For checks of full-size results at sampled sites.
+    """
+    psi = np.asarray(psi, dtype=np.complex128)
+    sites = np.asarray(sites, dtype=np.int64)
+    T, Z, Y, X = psi.shape[-6:-2]
+    ext = np.array([X, Y, Z, T])
+    nu = 2.0 * kappa * mu
+    sgn = -1.0 if dagger else 1.0
+
+    def at(field, c):  # field value at coordinates c (n, 4)
+        return field[..., c[:, 3], c[:, 2], c[:, 1], c[:, 0], :, :]
+
+    centre = at(psi, sites)
+    out = centre + sgn * 1j * nu * np.einsum("ab,...bc->...ac", GAMMA5, centre)
+    for m in range(4):
+        fwd = sites.copy()
+        fwd[:, m] = (fwd[:, m] + 1) % ext[m]
+        bwd = sites.copy()
+        bwd[:, m] = (bwd[:, m] - 1) % ext[m]
+        bc_f = np.ones(len(sites))
+        bc_b = np.ones(len(sites))
+        if antiperiodic and m == 3:
+            bc_f[sites[:, 3] == T - 1] = -1.0
+            bc_b[sites[:, 3] == 0] = -1.0
+        Uf = U[m][sites[:, 3], sites[:, 2], sites[:, 1], sites[:, 0]]        # U_mu(x)
+        Ub = U[m][bwd[:, 3], bwd[:, 2], bwd[:, 1], bwd[:, 0]]                # U_mu(x - mu)
+        f = np.einsum("nab,...nsb->...nsa", Uf, at(psi, fwd)) * bc_f[:, None, None]
+        b = np.einsum("nba,...nsb->...nsa", Ub.conj(), at(psi, bwd)) * bc_b[:, None, None]
+        p_minus, p_plus = ID4 - GAMMA[m], ID4 + GAMMA[m]
+        if not dagger:
+            out = out - kappa * (_spin(p_minus, f) + _spin(p_plus, b))
+        else:
+            out = out - kappa * (_spin(p_plus, f) + _spin(p_minus, b))
+    return out

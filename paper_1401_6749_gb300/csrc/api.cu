@@ -74,7 +74,7 @@ int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
   if (!g_trace_counts || g_trace_next >= kTraceSlots) return nullptr;
   if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return nullptr; }
   cudaEventRecord(*ev0, s);
-  return g_trace_counts + g_trace_next;
+  return g_trace_counts + g_trace_next++;  // slot reserved for this launch
 }
 
 void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
@@ -86,7 +86,6 @@ void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, dou
   std::lock_guard<std::mutex> lk(g_trace_mu);
   const int sl = slot ? (int)(slot - g_trace_counts) : -1;
   g_trace.push_back({name, ev0, ev1, sl, bytes_per_rhs, fixed_bytes, nrhs_if_uncounted});
-  ++g_trace_next;
 }
 
 // Systems per thread of the FP32/FP16/BF16 Dslash: TM_DSLASH_NR = 1, 2 or 4
@@ -196,6 +195,7 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   op->work_bytes = 0;
   op->host_flags = nullptr;
   op->host_flags_n = 0;
+  op->owns_links = true;
   for (int i = 0; i < 4; ++i) op->links[i] = nullptr;
   const cudaStream_t st = (cudaStream_t)s;
   for (int i = 0; i < 4; ++i) {
@@ -218,10 +218,23 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   return TM_OK;
 }
 
+extern "C" tm_status_t tm_op_clone(tm_op_t** out, const tm_op_t* src) {
+  if (!out || !src) { set_error("tm_op_clone: null argument"); return TM_ERR_ARG; }
+  tm_op* op = new tm_op();
+  *op = *src;
+  op->work = nullptr;
+  op->work_bytes = 0;
+  op->host_flags = nullptr;
+  op->host_flags_n = 0;
+  op->owns_links = false;
+  *out = op;
+  return TM_OK;
+}
+
 extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
   if (!op) return TM_OK;
   for (int i = 0; i < 4; ++i)
-    if (op->links[i]) cudaFree(op->links[i]);
+    if (op->links[i] && op->owns_links) cudaFree(op->links[i]);
   if (op->work) cudaFree(op->work);
   if (op->host_flags) cudaFreeHost(op->host_flags);
   delete op;

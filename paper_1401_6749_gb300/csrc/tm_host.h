@@ -19,6 +19,7 @@ struct tm_op {
   // pinned host mirror of the solver's per-system flags
   int* host_flags;
   int host_flags_n;
+  bool owns_links;    // false for clones, which share the links of their source
 };
 
 namespace tml {

@@ -61,6 +61,7 @@ _P = ctypes.POINTER
 _SIGS = {
     "tm_op_create": [_P(_vp), _P(tm_params_t), _vp, _vp],
     "tm_op_destroy": [_vp],
+    "tm_op_clone": [_P(_vp), _vp],
     "tm_spinor_bytes": [_P(tm_geom_t), _i, _i],
     "tm_spinor_pack": [_P(tm_geom_t), _vp, _i, _vp, _i, _vp],
     "tm_spinor_unpack": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
@@ -140,6 +141,17 @@ class Operator:
         h = ctypes.c_void_p()
         _check(_lib.tm_op_create(ctypes.byref(h), ctypes.byref(p), _ptr(U), _stream(stream)))
         self.handle = h
+
+    def clone(self):
+        """Handle sharing these links with its own solver work space (for a
+        concurrent solve on another thread and stream); close it before self."""
+        c = Operator.__new__(Operator)
+        c.L, c.kappa, c.mu = self.L, self.kappa, self.mu
+        h = ctypes.c_void_p()
+        _check(_lib.tm_op_clone(ctypes.byref(h), self.handle))
+        c.handle = h
+        c._source = self  # keeps the link owner alive
+        return c
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -16,6 +16,8 @@ The LP solve of a source is the same function of the source in every batch
 (per-system arithmetic, fixed-order reductions), so the correction term of
 Eq. 4 is unbiased.
 """
+import threading
+
 import torch
 
 from . import tmloops as tl
@@ -26,8 +28,15 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
-                 delta=0.1, kinds=KINDS, schur=True):
+                 delta=0.1, kinds=KINDS, schur=True, overlap=False):
+        """overlap: run the high-precision solves and contractions on a second
+        stream from a host thread, concurrently with the low-precision batches
+        (FP64 work uses other units than the FP32 arithmetic of the LP solves);
+        needs its own operator handle (a clone sharing the links)."""
         self.op = op
+        self.overlap = bool(overlap)
+        self.op_hp = op.clone() if self.overlap else op
+        self.hp_stream = torch.cuda.Stream() if self.overlap else None
         self.L = op.L
         self.T = op.L[3]
         self.n_hp, self.n_lp = int(n_hp), int(n_lp)
@@ -53,25 +62,35 @@ class TsmPipeline:
         self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(4)] if self.n_hp else None
         self.stats_lp, self.stats_hp = [], []
 
-    def _contract(self, x, w, g5w, prec, n, dst, row0):
+    def _contract(self, op, x, w, g5w, prec, n, dst, row0, stream):
         for k in self.kinds:
             kind, mode = k.split("_")
             left, right = (x, x) if mode == "vv" else (x, g5w)
             out = dst[k][row0:row0 + n]
             if kind == "local":
-                tl.loop_contract_local(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out)
+                tl.loop_contract_local(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
             else:
-                tl.loop_contract_oneD(self.op, left, right, prec, n, tl.LOOP_MODE[mode], out)
+                tl.loop_contract_oneD(op, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
 
-    def _solve_and_contract(self, fields, prec, first, n, params, dst, row0):
+    def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None):
         eta, x, w, g5w = fields
-        tl.z4_noise(self.L, eta, prec, self.seed, first, n)
-        st, stats = tl.tm_cg_solve(self.op, x, eta, n, params, raise_on_noconv=False)
+        tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
+        st, stats = tl.tm_cg_solve(op, x, eta, n, params, stream, raise_on_noconv=False)
         if any("gen" in k for k in self.kinds):
-            tl.tm_dslash(self.op, w, x, n, mu_zero=True, prec=prec)
-            tl.tm_gamma5(self.L, g5w, w, prec, n)
-        self._contract(x, w, g5w, prec, n, dst, row0)
+            tl.tm_dslash(op, w, x, n, mu_zero=True, prec=prec, stream=stream)
+            tl.tm_gamma5(self.L, g5w, w, prec, n, stream)
+        self._contract(op, x, w, g5w, prec, n, dst, row0, stream)
         return stats
+
+    def _run_hp(self, stream):
+        hp_params = tl.cg_params(self.tol_hp, self.max_iter, tl.CG_MIXED, inner_prec=self.hp_inner,
+                                 delta=self.delta, check_every=self.check_every, schur=self.schur)
+        stats = []
+        for b0 in range(0, self.n_hp, self.batch):
+            n = min(self.batch, self.n_hp - b0)
+            stats += self._solve_and_contract(self.op_hp, self._hp, tl.F64, self.first + b0, n,
+                                              hp_params, self.hp_loops, b0, stream)
+        self.stats_hp = stats
 
     def run(self, dist=None):
         """One full TSM estimate; returns per-kind (mean, err) device tensors.
@@ -81,22 +100,26 @@ class TsmPipeline:
         the sources of all ranks (one all-gather of the per-source loops)."""
         n_all = self.n_hp + self.n_lp
         self.stats_lp, self.stats_hp = [], []
+        main = torch.cuda.current_stream()
+        worker = None
+        if self.n_hp and self.overlap:
+            # the HP stream starts after everything queued before this step
+            self.hp_stream.wait_stream(main)
+            worker = threading.Thread(target=self._run_hp, args=(self.hp_stream,))
+            worker.start()
         # the truncated solves stop after a handful of iterations: poll often so
         # that no masked-out iterations are launched past convergence
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
                                  check_every=min(2, self.check_every), schur=self.schur)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
-            self.stats_lp += self._solve_and_contract(self._lp, self.lp_prec, self.first + b0, n,
-                                                      lp_params, self.lp_loops, b0)
-        if self.n_hp:
-            hp_params = tl.cg_params(self.tol_hp, self.max_iter, tl.CG_MIXED, inner_prec=self.hp_inner,
-                                     delta=self.delta, check_every=self.check_every,
-                                     schur=self.schur)
-            for b0 in range(0, self.n_hp, self.batch):
-                n = min(self.batch, self.n_hp - b0)
-                self.stats_hp += self._solve_and_contract(self._hp, tl.F64, self.first + b0, n,
-                                                          hp_params, self.hp_loops, b0)
+            self.stats_lp += self._solve_and_contract(self.op, self._lp, self.lp_prec, self.first + b0, n,
+                                                      lp_params, self.lp_loops, b0, main)
+        if worker is not None:
+            worker.join()
+            main.wait_stream(self.hp_stream)
+        elif self.n_hp:
+            self._run_hp(main)
         if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
             return self.combine_global(dist)
         return self.combine()

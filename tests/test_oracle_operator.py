@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle.gamma import GAMMA, GAMMA5, gamma_basis
-from oracle.operator import apply_DW, apply_M, dense_matrix
+from oracle.operator import apply_DW, apply_M, apply_M_sites, dense_matrix
 from paper_1401_6749_gb300 import synth
 
 
@@ -133,3 +133,18 @@ def test_dense_matrix_adjoint():
     blk = A[:12, :12]
     expect = np.kron(np.eye(4) + 1j * nu * GAMMA5, np.eye(3))
     np.testing.assert_allclose(blk, expect, atol=1e-15)
+
+
+def test_sampled_sites_match_whole_lattice():
+    L = (4, 6, 2, 8)
+    U = synth.gauge_field(L, seed=13)
+    psi = synth.random_spinor(L, 2, seed=14)
+    rng = np.random.default_rng(0)
+    sites = np.stack([rng.integers(0, n, 40) for n in L], axis=1)
+    sites[0] = (3, 5, 1, 7)                       # every coordinate at its upper edge
+    sites[1] = (0, 0, 0, 0)
+    for dagger in (False, True):
+        full = apply_M(U, psi, 0.16, 0.02, dagger=dagger)
+        ref = full[:, sites[:, 3], sites[:, 2], sites[:, 1], sites[:, 0]]
+        np.testing.assert_allclose(apply_M_sites(U, psi, 0.16, 0.02, sites, dagger=dagger), ref,
+                                   atol=1e-13)
