@@ -166,7 +166,13 @@ tm_status_t tm_hpe_exact(const tm_params_t *p, double *out);
  * stops on its own.  stats (host array of nrhs, may be NULL) receives per-system
  * results.  Blocks the calling thread until all systems have stopped.
  * Returns TM_ERR_NOCONV if any system hit max_iter, TM_ERR_NAN on non-finite
- * norms.  x and eta must not overlap.                                       */
+ * norms.  x and eta must not overlap.
+ * graph = 1: the check_every iterations between two host polls (every kernel
+ *   of them plus the copy of the convergence flags) are captured once into a
+ *   CUDA graph and replayed, one graph launch per poll; the results are
+ *   bit-identical to graph = 0 (converged systems are masked on the device
+ *   either way).  Launches inside the graph are not traced individually: each
+ *   replay is one trace record "cg.graph".                                  */
 typedef enum { TM_CG_PLAIN = 0, TM_CG_MIXED = 1 } tm_cg_mode_t;
 
 typedef struct {
@@ -179,6 +185,7 @@ typedef struct {
   int check_every;       /* host polls the convergence flags every N iterations (>= 1) */
   int true_residual;     /* PLAIN: compute |b - M^dag M x| / |b| at the end */
   int schur;             /* 1: even/odd preconditioned solve (see below), 0: plain M */
+  int graph;             /* 1: replay the iterations between polls as one CUDA graph */
 } tm_cg_params_t;
 
 typedef struct {
@@ -191,6 +198,23 @@ typedef struct {
 
 tm_status_t tm_cg_solve(tm_op_t *op, void *x, const void *eta, int nrhs,
                         const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
+
+/* Several independent batched solves advanced together (an uneven batch:
+ * different lattices, kappa, mu and numbers of systems, as in a sweep over
+ * volumes and quark masses; each set is the solve tm_cg_solve describes, with
+ * the common parameters p).  Set i solves ops[i] on the nrhs[i] systems of the
+ * internal fields x[i] / eta[i] and writes stats[i][0 .. nrhs[i]-1] (stats or
+ * any stats[i] may be NULL).  The sets run on streams forked from s and joined
+ * back into it, so that small lattices share the GPU; with p->graph = 1 the
+ * iterations of ALL sets between two polls are one CUDA graph launch.  Every
+ * set needs its own operator handle (tm_op_clone shares the links): a handle
+ * used twice is TM_ERR_ARG.  Results of each set are bit-identical to
+ * tm_cg_solve of that set alone.  Returns the worst status over the sets.
+ * This grouping is this library's own (the paper solves one source at a time). */
+tm_status_t tm_cg_solve_group(int nsets, tm_op_t *const *ops, void *const *x,
+                              const void *const *eta, const int *nrhs,
+                              const tm_cg_params_t *p, tm_cg_stats_t *const *stats,
+                              tm_stream_t s);
 
 /* Loop contractions (Sec. 2.2; Sec. 1 and Table 2 for the operator classes).
  * For each right-hand side r and time slice t,

@@ -25,7 +25,23 @@ void set_error(const char* fmt, ...) {
   g_last_error = buf;
 }
 
-void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+static thread_local int t_capturing = 0;
+static thread_local int t_captured = 0;
+
+void count_launch(int n) {
+  if (t_capturing) t_captured += n;
+  else g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed);
+}
+
+void capture_begin() {
+  t_capturing = 1;
+  t_captured = 0;
+}
+
+int capture_end() {
+  t_capturing = 0;
+  return t_captured;
+}
 
 tm_status_t check_launch(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -69,7 +85,7 @@ constexpr int kTraceSlots = 1 << 20;
 
 int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
   *ev0 = nullptr;
-  if (!g_trace_on.load(std::memory_order_relaxed)) return nullptr;
+  if (t_capturing || !g_trace_on.load(std::memory_order_relaxed)) return nullptr;
   std::lock_guard<std::mutex> lk(g_trace_mu);
   if (!g_trace_counts || g_trace_next >= kTraceSlots) return nullptr;
   if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return nullptr; }

@@ -25,6 +25,7 @@
 // with M_hat^dag = A(-nu) - kappa^2 (H^dag)_oe A(-nu)^-1 (H^dag)_eo.  The CG vectors
 // live on the odd sites; the even half of the vector an operator is applied to
 // holds the intermediate A^-1 H_eo v.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -316,39 +317,73 @@ static tm_status_t memset_d(void* dst, size_t n, cudaStream_t s) {
   return TM_OK;
 }
 
-}  // namespace tml
+// ---------------------------------------------------------------- one solve
+// One batched solve (one operator, nrhs systems) split into stream-ordered
+// phases, so that several solves can advance together and the iterations
+// between two host polls can be captured into a CUDA graph.
+struct CgRun {
+  tm_op* op = nullptr;
+  void* x = nullptr;
+  const void* eta = nullptr;
+  int nrhs = 0;
+  tm_cg_params_t prm{};
+  tm_cg_stats_t* stats = nullptr;
+  cudaStream_t s = nullptr;
 
-using namespace tml;
+  bool mixed = false, schur = false;
+  tm_prec_t lo = TM_PREC_F64, hi = TM_PREC_F64;
+  int par0 = 0, npar = 2, nwarp = 0;
+  void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
+  void *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr;
+  double* partial = nullptr;
+  CgState st{};
+  CgScalars sc{};
+  void* xs = nullptr;          // iterate of the inner CG
+  void* bb_field = nullptr;    // right-hand side Op^dag eta(_hat)
+  void* scratch_hi = nullptr;
+  const double* part0 = nullptr;
+  int nper = 0;
+  size_t pstride = 0;
 
-extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nrhs,
-                                   const tm_cg_params_t* prm, tm_cg_stats_t* stats, tm_stream_t strm) {
-  if (!op || !x || !eta || !prm || nrhs < 0) { set_error("tm_cg_solve: null argument"); return TM_ERR_ARG; }
-  if (x == eta) { set_error("tm_cg_solve: x and eta must not overlap"); return TM_ERR_ARG; }
+  SolveOp A() const { return SolveOp{op, schur, nrhs, s}; }
+  tm_status_t reduce() const { return reduce_partials(part0, nper, nrhs, st.red, s, pstride); }
+
+  tm_status_t setup();
+  tm_status_t iteration();
+  tm_status_t poll() const;    // active flags -> the operator's pinned host flags
+  bool any_active() const;
+  tm_status_t finish(tm_status_t* worst);
+};
+
+static tm_status_t check_params(const tm_cg_params_t* prm) {
+  if (!prm) { set_error("tm_cg_solve: null argument"); return TM_ERR_ARG; }
   if (!(prm->tol >= 0.0) || prm->max_iter < 0) { set_error("tm_cg_solve: tol must be >= 0 and max_iter >= 0"); return TM_ERR_ARG; }
   const bool mixed = prm->mode == TM_CG_MIXED;
   if (prm->mode != TM_CG_PLAIN && !mixed) { set_error("tm_cg_solve: unknown mode %d", (int)prm->mode); return TM_ERR_ARG; }
   if (mixed && !(prm->delta > 0.0 && prm->delta < 1.0)) { set_error("tm_cg_solve: delta must be in (0, 1)"); return TM_ERR_ARG; }
   if (prm->schur != 0 && prm->schur != 1) { set_error("tm_cg_solve: schur must be 0 or 1"); return TM_ERR_ARG; }
+  if (prm->graph != 0 && prm->graph != 1) { set_error("tm_cg_solve: graph must be 0 or 1"); return TM_ERR_ARG; }
   const tm_prec_t lo = mixed ? prm->inner_prec : prm->prec;
   if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: unknown precision"); return TM_ERR_ARG; }
-  if (nrhs == 0) return TM_OK;
-  const cudaStream_t s = (cudaStream_t)strm;
+  return TM_OK;
+}
+
+tm_status_t CgRun::setup() {
+  mixed = prm.mode == TM_CG_MIXED;
+  schur = prm.schur == 1;
+  lo = mixed ? prm.inner_prec : prm.prec;
+  hi = mixed ? TM_PREC_F64 : lo;
   const Geom& g = op->g;
-  const bool schur = prm->schur == 1;
-  const SolveOp A{op, schur, nrhs, s};
   // the CG vectors cover both parities, or only the odd one (Schur)
-  const int par0 = schur ? 1 : 0, npar = schur ? 1 : 2;
+  par0 = schur ? 1 : 0;
+  npar = schur ? 1 : 2;
   const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
   const size_t F = tm_spinor_bytes(&gg, lo, nrhs);
   const size_t F64 = tm_spinor_bytes(&gg, TM_PREC_F64, nrhs);
-  const int nwarp = nwarp_of(g);
+  nwarp = nwarp_of(g);
   const size_t P = sizeof(double) * (size_t)nrhs * 2 * (size_t)nwarp;
 
   // lay out the work space (first pass sizes, second pass assigns)
-  void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
-  void *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr;
-  double* partial = nullptr;
-  CgState st{};
   for (int pass = 0; pass < 2; ++pass) {
     Carver c{pass ? (char*)op->work : nullptr};
     if (mixed) {
@@ -373,36 +408,32 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
     st.status = (int*)c.take(sizeof(int) * nrhs);
     if (pass == 0) TM_TRY(ensure_work(op, c.off, 5 * nrhs));
   }
-  CgScalars sc;
-  sc.tol2 = prm->tol * prm->tol;
-  sc.delta2 = mixed ? prm->delta * prm->delta : 0.0;
+  sc.tol2 = prm.tol * prm.tol;
+  sc.delta2 = mixed ? prm.delta * prm.delta : 0.0;
   sc.n12 = 12.0 * (double)g.Vh * npar;
-  sc.max_iter = prm->max_iter;
+  sc.max_iter = prm.max_iter;
   sc.nrhs = nrhs;
   sc.mixed = mixed ? 1 : 0;
   // reductions over the parities the vectors live on
-  const double* part0 = partial + (schur ? nwarp : 0);
-  const int nper = npar * nwarp;
-  const size_t pstride = 2 * (size_t)nwarp;
-  auto reduce = [&]() { return reduce_partials(part0, nper, nrhs, st.red, s, pstride); };
-  const tm_prec_t hi = mixed ? TM_PREC_F64 : lo;
-  void* xs = mixed ? y : x;          // iterate of the inner CG
-  void* bb_field = mixed ? b64 : b;  // right-hand side Op^dag eta(_hat)
-  void* scratch_hi = mixed ? tmp64 : t;
+  part0 = partial + (schur ? nwarp : 0);
+  nper = npar * nwarp;
+  pstride = 2 * (size_t)nwarp;
+  xs = mixed ? y : x;
+  bb_field = mixed ? b64 : b;
+  scratch_hi = mixed ? tmp64 : t;
+  const SolveOp Op = A();
 
   // b = Op^dag eta (Schur: Op^dag eta_hat), |b|^2
   {
     const void* src = eta;
     if (schur) {
-      TM_TRY(A.prepare(hi, eta, scratch_hi));
+      TM_TRY(Op.prepare(hi, eta, scratch_hi));
       src = scratch_hi;
-    } else if (eta != scratch_hi) {
-      src = eta;
     }
     DslashCall e;
     e.out = bb_field; e.partial = partial;
     if (schur) {
-      TM_TRY(A.apply_dag(hi, scratch_hi, e));
+      TM_TRY(Op.apply_dag(hi, scratch_hi, e));
     } else {
       e.in = src;
       e.nrhs = nrhs;
@@ -421,47 +452,58 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
     TM_TRY(memset_d(x, F, s));
   }
   TM_TRY(memcpy_d2d(p, r, F, s));
+  return TM_OK;
+}
 
-  const int check_every = prm->check_every > 0 ? prm->check_every : 1;
-  int* hflags = op->host_flags;
-  for (int it = 0; it < prm->max_iter; ++it) {
-    TM_TRY(A.apply(lo, p, t, partial, st.active));  // t = Op p, |t|^2
+// one CG iteration of every active system (inactive systems are masked out on
+// the device, so extra iterations after convergence change nothing)
+tm_status_t CgRun::iteration() {
+  const Geom& g = op->g;
+  const SolveOp Op = A();
+  TM_TRY(Op.apply(lo, p, t, partial, st.active));  // t = Op p, |t|^2
+  TM_TRY(reduce());
+  TM_TRY(scalar_launch(cg_alpha_kernel, st, sc, s));
+  DslashCall e;  // r -= alpha Op^dag t, x += alpha p, |r|^2
+  e.epi = EPI_CGUPD; e.partial = partial; e.active = st.active; e.alpha = st.alpha;
+  e.p = p; e.x = xs; e.r = r;
+  TM_TRY(Op.apply_dag(lo, t, e));
+  TM_TRY(reduce());
+  if (!mixed) {
+    TM_TRY(scalar_launch(cg_beta_plain_kernel, st, sc, s));
+  } else {
+    TM_TRY(scalar_launch(cg_beta_mixed_kernel, st, sc, s));
+    // reliable update for the systems that asked for one: x += sigma y,
+    // r = b - Op^dag Op x in FP64
+    TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, par0, npar, s));
+    TM_TRY(Op.apply(TM_PREC_F64, x, tmp64, nullptr, st.ru));
+    DslashCall e4;
+    e4.out = r64; e4.b = b64; e4.epi = EPI_RESID; e4.partial = partial; e4.active = st.ru;
+    TM_TRY(Op.apply_dag(TM_PREC_F64, tmp64, e4));
     TM_TRY(reduce());
-    TM_TRY(scalar_launch(cg_alpha_kernel, st, sc, s));
-    DslashCall e;  // r -= alpha Op^dag t, x += alpha p, |r|^2
-    e.epi = EPI_CGUPD; e.partial = partial; e.active = st.active; e.alpha = st.alpha;
-    e.p = p; e.x = xs; e.r = r;
-    TM_TRY(A.apply_dag(lo, t, e));
-    TM_TRY(reduce());
-    if (!mixed) {
-      TM_TRY(scalar_launch(cg_beta_plain_kernel, st, sc, s));
-    } else {
-      TM_TRY(scalar_launch(cg_beta_mixed_kernel, st, sc, s));
-      // reliable update for the systems that asked for one: x += sigma y,
-      // r = b - Op^dag Op x in FP64
-      TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, par0, npar, s));
-      TM_TRY(A.apply(TM_PREC_F64, x, tmp64, nullptr, st.ru));
-      DslashCall e4;
-      e4.out = r64; e4.b = b64; e4.epi = EPI_RESID; e4.partial = partial; e4.active = st.ru;
-      TM_TRY(A.apply_dag(TM_PREC_F64, tmp64, e4));
-      TM_TRY(reduce());
-      TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
-      TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s));
-    }
-    TM_TRY(xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s));
-    if ((it + 1) % check_every == 0 || it + 1 == prm->max_iter) {
-      if (cudaMemcpyAsync(hflags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
-        return TM_ERR_CUDA;
-      }
-      bool any = false;
-      for (int i = 0; i < nrhs; ++i) any = any || hflags[i] != 0;
-      if (!any) break;
-    }
+    TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
+    TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s));
   }
-  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, par0, npar, s));
+  return xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s);
+}
 
+tm_status_t CgRun::poll() const {
+  if (cudaMemcpyAsync(op->host_flags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+bool CgRun::any_active() const {
+  for (int i = 0; i < nrhs; ++i)
+    if (op->host_flags[i] != 0) return true;
+  return false;
+}
+
+tm_status_t CgRun::finish(tm_status_t* worst_out) {
+  const Geom& g = op->g;
+  const SolveOp Op = A();
+  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, par0, npar, s));
   std::vector<double> h_bb(nrhs), h_rr(nrhs), h_sig(nrhs);
   std::vector<int> h_it(nrhs), h_nru(nrhs), h_status(nrhs);
   auto fetch = [&]() -> bool {
@@ -482,7 +524,7 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   // for plain solves that ask for it, it is recomputed here
   bool all_ok = true;
   for (int i = 0; i < nrhs; ++i) all_ok = all_ok && h_status[i] == TM_OK;
-  const bool recompute = (mixed && !all_ok) || (!mixed && prm->true_residual);
+  const bool recompute = (mixed && !all_ok) || (!mixed && prm.true_residual);
   std::vector<double> h_true(nrhs, -1.0);
   if (mixed && all_ok) {
     for (int i = 0; i < nrhs; ++i) h_true[i] = h_rr[i] * h_sig[i] * h_sig[i];
@@ -490,10 +532,10 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   if (recompute) {
     void* tmp = mixed ? tmp64 : t;
     void* res = mixed ? r64 : r;
-    TM_TRY(A.apply(hi, x, tmp, nullptr, nullptr));
+    TM_TRY(Op.apply(hi, x, tmp, nullptr, nullptr));
     DslashCall e4;
     e4.out = res; e4.b = bb_field; e4.epi = EPI_RESID; e4.partial = partial;
-    TM_TRY(A.apply_dag(hi, tmp, e4));
+    TM_TRY(Op.apply_dag(hi, tmp, e4));
     TM_TRY(reduce());
     if (cudaMemcpyAsync(h_true.data(), st.red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -501,8 +543,8 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
       return TM_ERR_CUDA;
     }
   }
-  if (schur) TM_TRY(A.reconstruct(hi, eta, x));
-  const bool want_true = mixed || prm->true_residual;
+  if (schur) TM_TRY(Op.reconstruct(hi, eta, x));
+  const bool want_true = mixed || prm.true_residual;
   tm_status_t worst = TM_OK;
   for (int i = 0; i < nrhs; ++i) {
     const double bbi = h_bb[i];
@@ -516,7 +558,226 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
     if (h_status[i] == TM_ERR_NAN) worst = TM_ERR_NAN;
     else if (h_status[i] == TM_ERR_NOCONV && worst == TM_OK) worst = TM_ERR_NOCONV;
   }
+  *worst_out = worst;
+  return TM_OK;
+}
+
+// ------------------------------------------------------------- the driver
+// Streams and events of a group solve: one set runs on the caller's stream;
+// several sets each get a stream forked from it (fork/join by events, which
+// is also how the sets' branches enter one captured graph).
+struct GroupStreams {
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> s;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  bool forked = false;
+
+  tm_status_t init(cudaStream_t m, int n) {
+    main = m;
+    s.assign(n, m);
+    if (n <= 1) return TM_OK;
+    forked = true;
+    join_ev.assign(n, nullptr);
+    bool ok = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i) {
+      ok = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      set_error("tm_cg_solve_group: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return TM_ERR_CUDA;
+    }
+    return TM_OK;
+  }
+  tm_status_t fork() {
+    if (!forked) return TM_OK;
+    bool ok = cudaEventRecord(fork_ev, main) == cudaSuccess;
+    for (size_t i = 0; i < s.size() && ok; ++i) ok = cudaStreamWaitEvent(s[i], fork_ev, 0) == cudaSuccess;
+    if (!ok) { set_error("tm_cg_solve_group: fork: %s", cudaGetErrorString(cudaGetLastError())); return TM_ERR_CUDA; }
+    return TM_OK;
+  }
+  tm_status_t join() {
+    if (!forked) return TM_OK;
+    bool ok = true;
+    for (size_t i = 0; i < s.size() && ok; ++i) {
+      ok = cudaEventRecord(join_ev[i], s[i]) == cudaSuccess;
+      ok = ok && cudaStreamWaitEvent(main, join_ev[i], 0) == cudaSuccess;
+    }
+    if (!ok) { set_error("tm_cg_solve_group: join: %s", cudaGetErrorString(cudaGetLastError())); return TM_ERR_CUDA; }
+    return TM_OK;
+  }
+  ~GroupStreams() {
+    if (!forked) return;
+    for (size_t i = 0; i < s.size(); ++i) {
+      if (s[i] && s[i] != main) cudaStreamDestroy(s[i]);
+      if (join_ev[i]) cudaEventDestroy(join_ev[i]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+  }
+};
+
+struct GraphHolder {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~GraphHolder() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+// Enqueue k iterations of every set plus the poll of its flags.
+static tm_status_t enqueue_block(std::vector<CgRun>& runs, GroupStreams& gs, int k) {
+  TM_TRY(gs.fork());
+  for (auto& run : runs) {
+    for (int i = 0; i < k; ++i) TM_TRY(run.iteration());
+    TM_TRY(run.poll());
+  }
+  return gs.join();
+}
+
+// A private stream ordered after the caller's (the legacy default stream
+// cannot be captured); the caller's stream waits for it at the end.
+struct PrivateStream {
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev = nullptr;
+  tm_status_t open(cudaStream_t u) {
+    user = u;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess) {
+      set_error("tm_cg_solve: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return TM_ERR_CUDA;
+    }
+    return TM_OK;
+  }
+  ~PrivateStream() {
+    if (s && ev && cudaEventRecord(ev, s) == cudaSuccess) cudaStreamWaitEvent(user, ev, 0);
+    if (s) cudaStreamDestroy(s);
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+
+static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* prm, cudaStream_t s_user,
+                               tm_status_t* worst) {
+  PrivateStream ps;
+  cudaStream_t s0 = s_user;
+  if (prm->graph) {
+    TM_TRY(ps.open(s_user));
+    s0 = ps.s;
+  }
+  GroupStreams gs;
+  TM_TRY(gs.init(s0, (int)runs.size()));
+  for (size_t i = 0; i < runs.size(); ++i) runs[i].s = gs.s[i];
+  TM_TRY(gs.fork());
+  for (auto& run : runs) TM_TRY(run.setup());
+  TM_TRY(gs.join());
+
+  const int check_every = prm->check_every > 0 ? prm->check_every : 1;
+  GraphHolder gh;
+  int per_replay = 0;
+  for (int done = 0; done < prm->max_iter;) {
+    const int k = std::min(check_every, prm->max_iter - done);
+    if (prm->graph && k == check_every) {
+      if (!gh.exec) {
+        // capture k iterations of every set (and the flag copies) once; the
+        // device-side masks make every replay the same sequence of launches
+        capture_begin();
+        tm_status_t cs = TM_OK;
+        if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          capture_end();
+          set_error("tm_cg_solve: graph capture failed: %s", cudaGetErrorString(cudaGetLastError()));
+          return TM_ERR_CUDA;
+        }
+        cs = enqueue_block(runs, gs, k);
+        const cudaError_t ce = cudaStreamEndCapture(s0, &gh.graph);
+        per_replay = capture_end();
+        if (cs != TM_OK) return cs;
+        if (ce != cudaSuccess || cudaGraphInstantiate(&gh.exec, gh.graph, 0) != cudaSuccess) {
+          set_error("tm_cg_solve: graph capture failed: %s", cudaGetErrorString(cudaGetLastError()));
+          return TM_ERR_CUDA;
+        }
+      }
+      TraceScope ts(s0, "cg.graph", 0.0, 0.0, 0);
+      if (cudaGraphLaunch(gh.exec, s0) != cudaSuccess) {
+        set_error("tm_cg_solve: graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return TM_ERR_CUDA;
+      }
+      count_launch(per_replay);
+    } else {
+      TM_TRY(enqueue_block(runs, gs, k));
+    }
+    if (cudaStreamSynchronize(s0) != cudaSuccess) {
+      set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+      return TM_ERR_CUDA;
+    }
+    done += k;
+    bool any = false;
+    for (const auto& run : runs) any = any || run.any_active();
+    if (!any) break;
+  }
+
+  TM_TRY(gs.fork());
+  *worst = TM_OK;
+  for (auto& run : runs) {
+    tm_status_t w = TM_OK;
+    TM_TRY(run.finish(&w));
+    if (w == TM_ERR_NAN) *worst = TM_ERR_NAN;
+    else if (w == TM_ERR_NOCONV && *worst == TM_OK) *worst = TM_ERR_NOCONV;
+  }
+  return gs.join();
+}
+
+static tm_status_t report(tm_status_t worst) {
   if (worst == TM_ERR_NAN) set_error("tm_cg_solve: non-finite residual norm");
   else if (worst == TM_ERR_NOCONV) set_error("tm_cg_solve: max_iter reached before tolerance");
   return worst;
+}
+
+}  // namespace tml
+
+using namespace tml;
+
+extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nrhs,
+                                   const tm_cg_params_t* prm, tm_cg_stats_t* stats, tm_stream_t strm) {
+  if (!op || !x || !eta || !prm || nrhs < 0) { set_error("tm_cg_solve: null argument"); return TM_ERR_ARG; }
+  if (x == eta) { set_error("tm_cg_solve: x and eta must not overlap"); return TM_ERR_ARG; }
+  TM_TRY(check_params(prm));
+  if (nrhs == 0) return TM_OK;
+  std::vector<CgRun> runs(1);
+  runs[0].op = op; runs[0].x = x; runs[0].eta = eta; runs[0].nrhs = nrhs;
+  runs[0].prm = *prm; runs[0].stats = stats;
+  tm_status_t worst = TM_OK;
+  TM_TRY(solve_group(runs, prm, (cudaStream_t)strm, &worst));
+  return report(worst);
+}
+
+extern "C" tm_status_t tm_cg_solve_group(int nsets, tm_op_t* const* ops, void* const* x,
+                                         const void* const* eta, const int* nrhs,
+                                         const tm_cg_params_t* prm, tm_cg_stats_t* const* stats,
+                                         tm_stream_t strm) {
+  if (nsets < 0 || (nsets > 0 && (!ops || !x || !eta || !nrhs))) {
+    set_error("tm_cg_solve_group: null argument");
+    return TM_ERR_ARG;
+  }
+  TM_TRY(check_params(prm));
+  std::vector<CgRun> runs;
+  for (int i = 0; i < nsets; ++i) {
+    if (!ops[i] || !x[i] || !eta[i] || nrhs[i] < 0) { set_error("tm_cg_solve_group: null argument in set %d", i); return TM_ERR_ARG; }
+    if (x[i] == eta[i]) { set_error("tm_cg_solve_group: x and eta of set %d overlap", i); return TM_ERR_ARG; }
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) {
+        set_error("tm_cg_solve_group: sets %d and %d share an operator handle (use tm_op_clone)", j, i);
+        return TM_ERR_ARG;
+      }
+    if (nrhs[i] == 0) continue;
+    CgRun r;
+    r.op = ops[i]; r.x = x[i]; r.eta = eta[i]; r.nrhs = nrhs[i];
+    r.prm = *prm; r.stats = stats ? stats[i] : nullptr;
+    runs.push_back(r);
+  }
+  if (runs.empty()) return TM_OK;
+  tm_status_t worst = TM_OK;
+  TM_TRY(solve_group(runs, prm, (cudaStream_t)strm, &worst));
+  return report(worst);
 }

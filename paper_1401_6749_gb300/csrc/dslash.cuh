@@ -116,6 +116,8 @@ struct DslashArgs {
   DslashCall c;
   double nu;         // twist of T_c / T_out
   double hop_scale;  // s_hop
+  double inv;        // 1 / (1 + nu^2), the scale of A^-1
+  float nu_f, hop_scale_f, inv_f;  // the same in FP32 for the narrow formats
   int nwarp;
   int rhs_groups;    // number of NR-wide right-hand-side groups
   int* trace_count;  // tracing: number of active systems of this launch
@@ -229,9 +231,11 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
     TM_HOPS(2)
     TM_HOPS(3)
 #undef TM_HOPS
-    const R shop = (R)a.hop_scale;
-    const R nu = (R)a.nu;
-    const R inv = (R)(1.0 / (1.0 + a.nu * a.nu));
+    // FP32 copies for the narrow formats: no FP64 arithmetic in their kernels
+    constexpr bool kF64 = std::is_same<R, double>::value;
+    const R shop = kF64 ? (R)a.hop_scale : (R)a.hop_scale_f;
+    const R nu = kF64 ? (R)a.nu : (R)a.nu_f;
+    const R inv = kF64 ? (R)a.inv : (R)a.inv_f;
     const void* cfield = a.c.cfield ? a.c.cfield : a.c.in;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -317,6 +321,10 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
     a.c.cfield = nullptr;
     a.c.out_inv = false;
   }
+  a.inv = 1.0 / (1.0 + a.nu * a.nu);
+  a.nu_f = (float)a.nu;
+  a.hop_scale_f = (float)a.hop_scale;
+  a.inv_f = (float)a.inv;
   a.nwarp = nwarp_of(op->g);
   const int bx = 128;
   a.rhs_groups = (c.nrhs + NR - 1) / NR;

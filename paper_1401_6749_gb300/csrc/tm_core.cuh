@@ -333,7 +333,12 @@ __device__ __forceinline__ Mat3<typename Prec<S>::R> load_link(const void* links
 }
 
 // ------------------------------------------------------------ bookkeeping
+// While this thread captures a CUDA graph, launches are counted per captured
+// graph (capture_begin / capture_end return how many one replay runs) and are
+// not traced; the caller counts each replay.
 void count_launch(int n = 1);
+void capture_begin();
+int capture_end();
 void set_error(const char* fmt, ...);
 tm_status_t check_launch(const char* what);
 // Tracing of Dslash launches (tm_trace_enable): trace_begin records a start

@@ -47,7 +47,8 @@ class tm_params_t(ctypes.Structure):
 class tm_cg_params_t(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("prec", ctypes.c_int), ("inner_prec", ctypes.c_int), ("delta", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int), ("schur", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int), ("schur", ctypes.c_int),
+                ("graph", ctypes.c_int)]
 
 
 class tm_cg_stats_t(ctypes.Structure):
@@ -70,6 +71,8 @@ _SIGS = {
     "tm_dslash": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
     "z4_noise": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _vp],
     "tm_cg_solve": [_vp, _vp, _vp, _i, _P(tm_cg_params_t), _P(tm_cg_stats_t), _vp],
+    "tm_cg_solve_group": [_i, _P(_vp), _P(_vp), _P(_vp), _P(_i), _P(tm_cg_params_t), _P(_P(tm_cg_stats_t)),
+                          _vp],
     "loop_contract_local": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
     "loop_contract_oneD": [_vp, _vp, _vp, _i, _i, _i, _vp, _vp],
     "loop_contract_local_noalloc": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
@@ -196,11 +199,11 @@ def z4_noise(L, eta, prec, seed, first_src, nsrc, stream=None):
 
 
 def cg_params(tol, max_iter=10000, mode=CG_PLAIN, prec=F64, inner_prec=F32, delta=0.1,
-              check_every=8, true_residual=False, schur=False):
+              check_every=8, true_residual=False, schur=False, graph=False):
     p = tm_cg_params_t()
     p.tol, p.max_iter, p.mode, p.prec, p.inner_prec = float(tol), int(max_iter), int(mode), int(prec), int(inner_prec)
     p.delta, p.check_every, p.true_residual = float(delta), int(check_every), int(bool(true_residual))
-    p.schur = int(bool(schur))
+    p.schur, p.graph = int(bool(schur)), int(bool(graph))
     return p
 
 
@@ -211,6 +214,25 @@ def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
                           _stream(stream))
     out = [dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status,
                 rel_res=s.rel_res, true_res=s.true_res) for s in list(stats)[:int(nrhs)]]
+    if st != 0 and (st != 3 or raise_on_noconv):
+        _check(st)
+    return st, out
+
+
+def tm_cg_solve_group(ops, xs, etas, nrhs, params, stream=None, raise_on_noconv=True):
+    """Several solves (one per operator) advanced together; returns
+    (status, [per-set list of per-system dicts])."""
+    n = len(ops)
+    if not (len(xs) == len(etas) == len(nrhs) == n):
+        raise ValueError("ops, xs, etas and nrhs must have the same length")
+    arr = lambda vals: (_vp * max(n, 1))(*vals)
+    stats = [(tm_cg_stats_t * max(int(k), 1))() for k in nrhs]
+    sp = (_P(tm_cg_stats_t) * max(n, 1))(*[ctypes.cast(s, _P(tm_cg_stats_t)) for s in stats])
+    st = _lib.tm_cg_solve_group(n, arr([o.handle for o in ops]), arr([_ptr(x) for x in xs]),
+                                arr([_ptr(e) for e in etas]), (_i * max(n, 1))(*[int(k) for k in nrhs]),
+                                ctypes.byref(params), sp, _stream(stream))
+    out = [[dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status, rel_res=s.rel_res,
+                 true_res=s.true_res) for s in list(ss)[:int(k)]] for ss, k in zip(stats, nrhs)]
     if st != 0 and (st != 3 or raise_on_noconv):
         _check(st)
     return st, out
