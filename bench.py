@@ -30,11 +30,11 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=3e-5, recon=12, overlap=False),
+                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126, schur=True, delta=3e-5, recon=12, overlap=False),
+                 seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False),
 }
 
 PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -418,7 +418,7 @@ def run_dslash(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     esz = tl.ELEM_SIZE[prec]
-    link_reals = 18 if (prec == tl.F64 or args.recon == 18) else 12
+    link_reals = tl.link_reals(args.recon, prec)
     nbytes = n * 2 * 24 * esz * V + 4 * link_reals * esz * V
     peak, src = _peaks()
     gbs = nbytes / (ms * 1e-3) / 1e9
@@ -426,6 +426,59 @@ def run_dslash(args):
                       "recon": link_reals, "ms_per_launch": round(ms, 4), "bytes_per_launch": nbytes,
                       "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "peak_source": src,
                       "l2": "in+out fields %.0f MB" % (2 * n * 24 * esz * V / 1e6)}), flush=True)
+    op.close()
+
+
+def run_contract(args):
+    """Time the loop contractions alone on nrhs Z4 fields (seeds 7 and 8):
+    loop_contract_local and loop_contract_oneD (one-end mode), per launch
+    averaged over --steps launches after --warmup.  Algorithmic bytes per
+    launch: nrhs x 2 spinors (+ the links once for oneD); useful flops per site
+    and system: 384 (local, the 4 x 4 spin matrix) and 4224 (oneD: per mu two
+    link products of a 4-spinor and the spin outer products, the time
+    direction with two of each)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_6749_gb300 import synth
+    from paper_1401_6749_gb300 import tmloops as tl
+    L = tuple(int(v) for v in args.lattice.split(","))
+    prec = tl.PREC[args.prec]
+    n = args.nrhs
+    V = int(np.prod(L))
+    U = synth.gauge_field(L, 1234, device="cuda")
+    op = tl.Operator(L, 0.161, 0.003, torch.from_numpy(U.view(np.float64)).cuda(), recon=args.recon)
+    del U
+    a = tl.empty_field(L, prec, n)
+    b = tl.empty_field(L, prec, n)
+    tl.z4_noise(L, a, prec, 7, 0, n)
+    tl.z4_noise(L, b, prec, 8, 0, n)
+    T = L[3]
+    out = torch.empty(n * 64 * T * 2, dtype=torch.float64, device="cuda")
+    jobs = {"local": (lambda: tl.loop_contract_local(L, a, b, prec, n, tl.LOOP_VV, out), 384.0, False),
+            "oneD": (lambda: tl.loop_contract_oneD(op, a, b, prec, n, tl.LOOP_VV, out), 4224.0, True)}
+    esz = tl.ELEM_SIZE[prec]
+    link_reals = tl.link_reals(args.recon, prec)
+    peak, src = _peaks()
+    res = {}
+    for name, (fn, flops, links) in jobs.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nbytes = n * 2 * 24 * esz * V + (4 * link_reals * esz * V if links else 0)
+        res[name] = {"ms_per_launch": round(ms, 4), "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                     "TFLOPs": round(flops * V * n / (ms * 1e-3) / 1e12, 2)}
+    print(json.dumps({"mode": "contract", "lattice": list(L), "nrhs": n, "prec": args.prec,
+                      "recon": link_reals, "peak_source": src, "kernels": res}), flush=True)
     op.close()
 
 
@@ -473,7 +526,7 @@ def run_next(args):
         torch.cuda.synchronize()
         res[name] = {"ms": round(e0.elapsed_time(e1) / args.steps, 4)}
     spin = 24 * esz * V
-    link = 4 * (18 if c["recon"] == 18 else 12) * esz * V
+    link = 4 * tl.link_reals(c["recon"], prec) * esz * V
     nbytes = {"hpe_BH4": 4 * (n * 2 * spin + link), "z4_time_diluted": n * spin, "local_mom8": n * 2 * spin}
     peak, src = _peaks()
     for k, v in res.items():
@@ -486,6 +539,82 @@ def run_next(args):
     print(json.dumps({"mode": "next", "lattice": list(L), "nrhs": n, "prec": c["lp_prec"],
                       "peak_source": src, "kernels": res}), flush=True)
     op.close()
+
+
+def run_solvers(args):
+    """Time whole solves, graph replay against eager launches:
+      * 24^3 x 48, kappa = 0.161, mu = 0.004: 12 and 24 Z4 sources in one
+        batched mixed-precision solve (FP32 iteration, FP64 reliable updates,
+        tol 1e-10, even/odd);
+      * the uneven batch 8^4 / 12^4 / 16^3 x 32 / 24^3 x 48 (kappa 0.155 ..
+        0.162, mu 0.01 .. 0.003, 4 / 8 / 16 / 32 sources): the TSM solves (FP16
+        to 1e-2 and mixed to 1e-9) of the four lattices one after the other,
+        as one group, and as one group replayed as graphs.
+    Prints one JSON line with ms per solve (median over --steps)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_6749_gb300 import synth
+    from paper_1401_6749_gb300 import tmloops as tl
+
+    def make_op(L, k, m, seed):
+        U = synth.gauge_field(L, seed, device="cuda")
+        return tl.Operator(L, k, m, torch.from_numpy(U.view(np.float64)).cuda(), recon=0)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return round(float(np.median(ts)), 3)
+
+    res = {}
+    L = (24, 24, 24, 48)
+    op = make_op(L, 0.161, 0.004, 1236)
+    for n in (12, 24):
+        eta = tl.empty_field(L, tl.F64, n)
+        tl.z4_noise(L, eta, tl.F64, 20140126, 0, n)
+        x = tl.empty_field(L, tl.F64, n)
+        for graph in (False, True):
+            prm = tl.cg_params(1e-10, 20000, tl.CG_MIXED, inner_prec=tl.F32, delta=1e-5, check_every=4,
+                               schur=True, graph=graph)
+            res[f"24x48_mixed_n{n}_{'graph' if graph else 'eager'}_ms"] = timed(
+                lambda: tl.tm_cg_solve(op, x, eta, n, prm))
+        del eta, x
+    op.close()
+    ragged = [((8, 8, 8, 8), 0.155, 0.01, 4), ((12, 12, 12, 12), 0.158, 0.007, 8),
+              ((16, 16, 16, 32), 0.160, 0.005, 16), ((24, 24, 24, 48), 0.162, 0.003, 32)]
+    ops = [make_op(Lr, k, m, 1238) for Lr, k, m, _ in ragged]
+    ns = [n for *_, n in ragged]
+    for name, fp, base in (("lp", tl.F16, dict(tol=1e-2, mode=tl.CG_PLAIN, prec=tl.F16, check_every=2)),
+                           ("hp", tl.F64, dict(tol=1e-9, mode=tl.CG_MIXED, inner_prec=tl.F32, delta=3e-5,
+                                               check_every=4))):
+        etas = [tl.empty_field(Lr, fp, n) for (Lr, *_), n in zip(ragged, ns)]
+        xs = [tl.empty_field(Lr, fp, n) for (Lr, *_), n in zip(ragged, ns)]
+        for (Lr, *_), e, n in zip(ragged, etas, ns):
+            tl.z4_noise(Lr, e, fp, 20140126, 0, n)
+        kw = dict(base)
+        tol = kw.pop("tol")
+        eager = tl.cg_params(tol, 20000, schur=True, graph=False, **kw)
+        graph = tl.cg_params(tol, 20000, schur=True, graph=True, **kw)
+
+        def seq(prm):
+            for o, x, e, n in zip(ops, xs, etas, ns):
+                tl.tm_cg_solve(o, x, e, n, prm)
+        res[f"uneven_{name}_sequential_ms"] = timed(lambda: seq(eager))
+        res[f"uneven_{name}_sequential_graph_ms"] = timed(lambda: seq(graph))
+        res[f"uneven_{name}_group_ms"] = timed(lambda: tl.tm_cg_solve_group(ops, xs, etas, ns, eager))
+        res[f"uneven_{name}_group_graph_ms"] = timed(lambda: tl.tm_cg_solve_group(ops, xs, etas, ns, graph))
+    for o in ops:
+        o.close()
+    print(json.dumps({"mode": "solvers", "steps": args.steps, "warmup": args.warmup, "results": res}),
+          flush=True)
 
 
 # ----------------------------------------------------------------- oracle
@@ -567,12 +696,15 @@ def main():
     ap.add_argument("--ref-hp-iters", type=float, default=105)
     ap.add_argument("--schur", type=int, default=None, help="override even/odd preconditioning")
     ap.add_argument("--delta", type=float, default=None, help="override the reliable-update delta")
-    ap.add_argument("--recon", type=int, default=None, choices=[12, 18])
+    ap.add_argument("--recon", type=int, default=None, choices=[0, 12, 18],
+                    help="reals per link in the narrow copies; 0 = per precision")
     ap.add_argument("--overlap", type=int, default=None, help="override HP/LP stream overlap")
     ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
     ap.add_argument("--next", action="store_true", help="time HPE, time dilution, momentum projection")
+    ap.add_argument("--solvers", action="store_true", help="time graph-replayed and grouped solves")
+    ap.add_argument("--contract", action="store_true", help="time the loop contractions alone")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16"])
@@ -587,7 +719,7 @@ def main():
     if args.recon is not None:
         c["recon"] = args.recon
     else:
-        args.recon = 12 if args.dslash else c["recon"]
+        args.recon = c["recon"]
     if args.lp_prec is not None:
         c["lp_prec"] = args.lp_prec
     if args.hp_inner is not None:
@@ -596,6 +728,10 @@ def main():
         run_dslash(args)
     elif args.next:
         run_next(args)
+    elif args.solvers:
+        run_solvers(args)
+    elif args.contract:
+        run_contract(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

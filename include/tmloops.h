@@ -80,7 +80,10 @@ typedef struct {
   int antiperiodic_t;
   int recon;  /* 12 or 18: real numbers stored per link in the F32/F16/BF16
                  copies (12 = two rows, third = conj(row0 x row1)); the F64
-                 copy always stores 18 */
+                 copy always stores 18.  0: per precision, as measured fastest
+                 on GB300: 12 for F32 (its Dslash streams more bytes per flop),
+                 18 for F16/BF16 (their Dslash is bound by FP32 issue, and the
+                 third-row reconstruction costs more than the extra bytes) */
 } tm_params_t;
 
 typedef struct tm_op tm_op_t;

@@ -117,7 +117,7 @@ int dslash_nr_override() {
 
 // ------------------------------------------------------------ dispatch
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
-  const bool r12 = op->recon == 12;
+  const bool r12 = (int)prec >= 0 && (int)prec < 4 && op->recon_p[prec] == 12;
   switch (prec) {
     case TM_PREC_F64: return dslash_launch<double, 18>(op, c, s);
     case TM_PREC_F32: return r12 ? dslash_launch<float, 12>(op, c, s) : dslash_launch<float, 18>(op, c, s);
@@ -201,12 +201,19 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   if (!out || !p || !U_lex) { set_error("tm_op_create: null argument"); return TM_ERR_ARG; }
   *out = nullptr;
   if (check_geom(p->L) != TM_OK) return TM_ERR_ARG;
-  if (p->recon != 12 && p->recon != 18) { set_error("recon must be 12 or 18, got %d", p->recon); return TM_ERR_ARG; }
+  if (p->recon != 0 && p->recon != 12 && p->recon != 18) {
+    set_error("recon must be 0, 12 or 18, got %d", p->recon);
+    return TM_ERR_ARG;
+  }
   tm_op* op = new tm_op();
   op->g = make_geom(p->L, p->antiperiodic_t ? 1 : 0);
   op->kappa = p->kappa;
   op->mu = p->mu;
-  op->recon = p->recon;
+  // per precision; F64 always stores the full matrix
+  op->recon_p[TM_PREC_F64] = 18;
+  op->recon_p[TM_PREC_F32] = p->recon ? p->recon : 12;
+  op->recon_p[TM_PREC_F16] = p->recon ? p->recon : 18;
+  op->recon_p[TM_PREC_BF16] = p->recon ? p->recon : 18;
   op->work = nullptr;
   op->work_bytes = 0;
   op->host_flags = nullptr;
@@ -216,13 +223,13 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   const cudaStream_t st = (cudaStream_t)s;
   for (int i = 0; i < 4; ++i) {
     const tm_prec_t pr = (tm_prec_t)i;
-    const size_t nb = link_bytes(op->g, pr, p->recon);
+    const size_t nb = link_bytes(op->g, pr, op->recon_p[i]);
     if (cudaMalloc(&op->links[i], nb) != cudaSuccess) {
       set_error("tm_op_create: cudaMalloc of %zu bytes failed", nb);
       tm_op_destroy(op);
       return TM_ERR_CUDA;
     }
-    const tm_status_t st2 = pack_links(op->g, pr, p->recon, op->links[i], U_lex, st);
+    const tm_status_t st2 = pack_links(op->g, pr, op->recon_p[i], op->links[i], U_lex, st);
     if (st2 != TM_OK) { tm_op_destroy(op); return st2; }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) {

@@ -586,6 +586,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
                                           double* out, tm_stream_t strm) {
   if (!op || !left || !right || !out || nrhs < 0) { set_error("loop_contract_oneD: null argument"); return TM_ERR_ARG; }
   if (!valid_mode(mode)) { set_error("loop_contract_oneD: unknown mode %d", (int)mode); return TM_ERR_ARG; }
+  if ((int)prec < 0 || (int)prec > 3) { set_error("loop_contract_oneD: unknown precision %d", (int)prec); return TM_ERR_ARG; }
   if (nrhs == 0) return TM_OK;
   if (nrhs > 65535) { set_error("loop_contract_oneD: nrhs must be <= 65535"); return TM_ERR_ARG; }
   const cudaStream_t s = (cudaStream_t)strm;
@@ -596,7 +597,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   if (st != TM_OK) return st;
   const dim3 grid(nchunk, 2 * g.L[3], nrhs);
   const dim3 block(kOneDLanes, 8);
-  const bool r12 = op->recon == 12;
+  const bool r12 = op->recon_p[prec] == 12;
   const void* links = op->links[prec];
   static const char* const kNames[4] = {"oneD.f64", "oneD.f32", "oneD.f16", "oneD.bf16"};
   const double esz = (double)prec_size(prec);

@@ -61,19 +61,96 @@ __device__ __forceinline__ Cx<R> add_ph(Cx<R> a, Cx<R> b) {
   else return {O::add(a.re, b.im), O::sub(a.im, b.re)};
 }
 
-// acc += bsign * (1 + SGN g_MU) W psi, where W = U (ADJ = false) or U^dag.
-template <int MU, int SGN, bool ADJ, class R>
-__device__ __forceinline__ void hop(Cx<R> (&acc)[12], const Cx<R> (&psi)[12], const Mat3<R>& U,
-                                    R bsign) {
+// Spin projection h = psi_up + SGN A_mu psi_dn (rows 0 and 1 of (1 + SGN g_MU) psi).
+template <int MU, int SGN, class R>
+__device__ __forceinline__ void project(Cx<R> (&h0)[3], Cx<R> (&h1)[3], const Cx<R> (&psi)[12]) {
   using G = GBlock<MU>;
-  using O = Ar<R>;
   constexpr int s2 = SGN > 0 ? 0 : 2;  // extra phase i^2 = -1 for SGN = -1
-  Cx<R> h0[3], h1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     h0[c] = add_ph<G::ak0 + s2>(psi[c], psi[3 * (2 + G::ac0) + c]);
     h1[c] = add_ph<G::ak1 + s2>(psi[3 + c], psi[3 * (2 + G::ac1) + c]);
   }
+}
+
+// FP16 / BF16 storage: sm_100+ adds a 16-bit operand to an FP32 one in one
+// instruction with one rounding (add/sub.rn.f32.f16|bf16), so psi_up enters
+// the projection unconverted: the result is bit-identical to converting it
+// first, with 12 conversions fewer per hop.
+template <class S> struct Mixed;
+template <> struct Mixed<__half> {
+  static __device__ __forceinline__ float add(unsigned short a, float c) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+  }
+  static __device__ __forceinline__ float sub(unsigned short a, float c) {
+    float d;
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+  }
+};
+template <> struct Mixed<__nv_bfloat16> {
+  static __device__ __forceinline__ float add(unsigned short a, float c) {
+    float d;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+  }
+  static __device__ __forceinline__ float sub(unsigned short a, float c) {
+    float d;
+    asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+    return d;
+  }
+};
+
+// complex k (= 3 spin + colour) of a raw 16-bit spinor: one 32-bit word, re in
+// the low half
+__device__ __forceinline__ unsigned raw_word(const uint4 (&q)[3], int k) {
+  const uint4& v = q[k >> 2];
+  return (k & 3) == 0 ? v.x : (k & 3) == 1 ? v.y : (k & 3) == 2 ? v.z : v.w;
+}
+
+// a + i^K b with a raw (16-bit) and b in FP32
+template <int K, class S>
+__device__ __forceinline__ Cx<float> add_ph_raw(unsigned a, Cx<float> b) {
+  using M = Mixed<S>;
+  constexpr int k = ((K % 4) + 4) % 4;
+  const unsigned short ar = (unsigned short)(a & 0xffffu), ai = (unsigned short)(a >> 16);
+  if constexpr (k == 0) return {M::add(ar, b.re), M::add(ai, b.im)};
+  else if constexpr (k == 1) return {M::sub(ar, b.im), M::add(ai, b.re)};
+  else if constexpr (k == 2) return {M::sub(ar, b.re), M::sub(ai, b.im)};
+  else return {M::add(ar, b.im), M::sub(ai, b.re)};
+}
+
+// a raw 16-bit complex (one 32-bit word) converted to FP32
+template <class S>
+__device__ __forceinline__ Cx<float> raw_to_f32(unsigned w) {
+  const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
+  if constexpr (std::is_same<S, __half>::value)
+    return {__half2float(__ushort_as_half(lo)), __half2float(__ushort_as_half(hi))};
+  else
+    return {__bfloat162float(__ushort_as_bfloat16(lo)), __bfloat162float(__ushort_as_bfloat16(hi))};
+}
+
+template <int MU, int SGN, class S>
+__device__ __forceinline__ void project_raw(Cx<float> (&h0)[3], Cx<float> (&h1)[3], const uint4 (&q)[3]) {
+  using G = GBlock<MU>;
+  constexpr int s2 = SGN > 0 ? 0 : 2;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h0[c] = add_ph_raw<G::ak0 + s2, S>(raw_word(q, c), raw_to_f32<S>(raw_word(q, 3 * (2 + G::ac0) + c)));
+    h1[c] = add_ph_raw<G::ak1 + s2, S>(raw_word(q, 3 + c), raw_to_f32<S>(raw_word(q, 3 * (2 + G::ac1) + c)));
+  }
+}
+
+// acc += bsign * (1 + SGN g_MU) W psi given the projection (h0, h1) of psi,
+// where W = U (ADJ = false) or U^dag.
+template <int MU, int SGN, bool ADJ, class R>
+__device__ __forceinline__ void hop_acc(Cx<R> (&acc)[12], const Cx<R> (&h0)[3], const Cx<R> (&h1)[3],
+                                        const Mat3<R>& U, R bsign) {
+  using G = GBlock<MU>;
+  using O = Ar<R>;
+  constexpr int s2 = SGN > 0 ? 0 : 2;
   Cx<R> w0[3], w1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -110,6 +187,27 @@ __device__ __forceinline__ void hop(Cx<R> (&acc)[12], const Cx<R> (&psi)[12], co
   }
 }
 
+// acc += bsign * (1 + SGN g_MU) W psi with psi the field's site at b0
+template <class S, int MU, int SGN, bool ADJ>
+__device__ __forceinline__ void hop_site(Cx<typename Prec<S>::R> (&acc)[12], const void* field, size_t b0,
+                                         size_t cs, const Mat3<typename Prec<S>::R>& U,
+                                         typename Prec<S>::R bsign) {
+  using R = typename Prec<S>::R;
+  Cx<R> h0[3], h1[3];
+  if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+    const uint4* f = reinterpret_cast<const uint4*>(field);
+    uint4 q[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) q[j] = f[b0 + j * cs];
+    project_raw<MU, SGN, S>(h0, h1, q);
+  } else {
+    Cx<R> psi[12];
+    load_spinor<S>(psi, field, b0, cs);
+    project<MU, SGN>(h0, h1, psi);
+  }
+  hop_acc<MU, SGN, ADJ>(acc, h0, h1, U, bsign);
+}
+
 struct DslashArgs {
   Geom g;
   const void* links;
@@ -143,8 +241,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Minimum resident blocks per SM requested from the compiler (caps the
 // registers per thread).  The narrow formats are latency/issue bound and gain
-// from occupancy: measured at 32^3 x 64, 16 systems, 8 blocks (64 registers)
-// is fastest for FP16/BF16 in the solver's half-lattice launches, 6 for FP32;
+// from occupancy: measured at 32^3 x 64, 16 systems, 7 blocks (72 registers)
+// is fastest for FP16/BF16 (8 blocks = 64 registers spills), 6 for FP32;
 // FP64 is arithmetic bound and keeps its registers.  TM_DSLASH_MINBLOCKS
 // overrides at build time.
 template <class S>
@@ -152,7 +250,7 @@ constexpr int dslash_min_blocks() {
 #ifdef TM_DSLASH_MINBLOCKS
   return TM_DSLASH_MINBLOCKS;
 #else
-  return std::is_same<S, double>::value ? 1 : (std::is_same<S, float>::value ? 6 : 8);
+  return std::is_same<S, double>::value ? 1 : (std::is_same<S, float>::value ? 6 : 7);
 #endif
 }
 
@@ -211,18 +309,16 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
         const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                         \
         _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
           if (!act[j]) continue;                                                                 \
-          Cx<R> psi[12];                                                                         \
-          load_spinor<S>(psi, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), cs);  \
-          hop<MU, SF, false>(acc[j], psi, Uf, sf);                                               \
+          hop_site<S, MU, SF, false>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), \
+                                     cs, Uf, sf);                                                \
         }                                                                                        \
       }                                                                                          \
       {                                                                                          \
         const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);                   \
         _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
           if (!act[j]) continue;                                                                 \
-          Cx<R> psi[12];                                                                         \
-          load_spinor<S>(psi, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), cs);  \
-          hop<MU, SB, true>(acc[j], psi, Ub, sbk);                                               \
+          hop_site<S, MU, SB, true>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), \
+                                    cs, Ub, sbk);                                                \
         }                                                                                        \
       }                                                                                          \
     }

@@ -11,7 +11,7 @@ struct tm_op {
   tml::Geom g;
   double kappa;
   double mu;
-  int recon;          // link format of the F32/F16/BF16 copies (12 or 18)
+  int recon_p[4];     // link format (12 or 18 reals) of the copy of each precision
   void* links[4];     // indexed by tm_prec_t; F64 always 18-real
   // solver work space, grown on demand, owned by the operator
   void* work;

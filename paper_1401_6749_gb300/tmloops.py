@@ -131,6 +131,16 @@ def empty_field(L, prec, nrhs, device="cuda"):
     return torch.empty(tm_spinor_bytes(L, prec, nrhs), dtype=torch.uint8, device=device)
 
 
+def link_reals(recon, prec):
+    """Reals stored per link in the operator's copy of precision prec
+    (recon 0 = per precision: 12 for F32, 18 for F16/BF16; F64 always 18)."""
+    if prec == F64:
+        return 18
+    if recon == 0:
+        return 12 if prec == F32 else 18
+    return int(recon)
+
+
 class Operator:
     """Owner of a tm_op_t handle (gauge links in every precision)."""
 

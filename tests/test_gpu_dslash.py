@@ -46,7 +46,7 @@ def test_pack_unpack_roundtrip(prec):
 
 
 @pytest.mark.parametrize("L", LATTICES)
-@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 18), (2, 12), (3, 12), (2, 18)])
+@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 18), (2, 12), (3, 12), (2, 18), (3, 18), (2, 0)])
 @pytest.mark.parametrize("dagger,mu_zero", [(False, False), (True, False), (False, True)])
 def test_dslash_matches_oracle(L, prec, recon, dagger, mu_zero):
     tl = require_gpu()
@@ -117,3 +117,22 @@ def test_argument_errors_are_reported():
     with pytest.raises(tl.TmError):
         tl.tm_dslash(op, f, f, 1)                  # in-place is rejected
     tl.z4_noise((2, 2, 2, 2), f, 1, 1, 0, 0)       # zero sources: no-op
+
+
+@pytest.mark.parametrize("prec,same_as", [(1, 12), (2, 18), (3, 18)])
+def test_per_precision_link_format(prec, same_as):
+    """recon = 0 keeps 12 reals per link for F32 and 18 for F16/BF16: the
+    results are those of the operator built with that format."""
+    tl = require_gpu()
+    L = (6, 4, 4, 8)
+    U = synth.gauge_field(L, seed=21)
+    op0 = tl.Operator(L, 0.16, 0.02, to_dev(U), recon=0)
+    opx = tl.Operator(L, 0.16, 0.02, to_dev(U), recon=same_as)
+    fin = pack(tl, L, synth.random_spinor(L, 3, seed=22), prec)
+    a, b = tl.empty_field(L, prec, 3), tl.empty_field(L, prec, 3)
+    tl.tm_dslash(op0, a, fin, 3, prec=prec)
+    tl.tm_dslash(opx, b, fin, 3, prec=prec)
+    assert bool((a == b).all())
+    assert tl.link_reals(0, prec) == same_as
+    op0.close()
+    opx.close()
