@@ -30,14 +30,14 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False),
+                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False),
+                 seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
 }
 
-PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "ff": 8}
 METRIC = "Dslash HBM GB/s and % roofline; TSM loop sec/source at fixed error vs FP64 CG"
 
 
@@ -221,7 +221,7 @@ def run_ours(args):
     mk = lambda o: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
                                hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
                                seed=c["seed"], first_src=rank * n_src, schur=c["schur"],
-                               delta=c["delta"], overlap=c["overlap"])
+                               delta=c["delta"], overlap=c["overlap"], hp_loop_prec=tl.PREC[c["hp_loops"]])
     pipe = mk(op)
     _log("inputs ready")
     for _ in range(args.warmup):
@@ -250,9 +250,10 @@ def run_ours(args):
     tl.tm_trace_enable(False)
     clk = clocks.stop()
     classes = {}
-    names = ["dslash.%s.%s" % (p, e) for p in ("f64", "f32", "f16", "bf16") for e in ("out", "cgupd", "resid")]
-    names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in ("f64", "f32", "f16", "bf16")]
-    names += ["blas.xpay", "z4_noise"]
+    precs = ("f64", "f32", "f16", "bf16", "ff")
+    names = ["dslash.%s.%s" % (p, e) for p in precs for e in ("out", "cgupd", "resid")]
+    names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in precs]
+    names += ["blas.xpay", "z4_noise", "cg.graph"]
     for name in names:
         n, tms, nbytes = tl.tm_trace_read(name)
         if n:
@@ -364,7 +365,10 @@ def run_ours(args):
             "metric": METRIC, "value": round(ms * 1e-3 / (world * n_src), 6), "unit": "s/source",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
-            "dtype_detail": "LP solves f16 (f32 arithmetic); HP solves f32 inner + f64 reliable updates; loops f64 accumulation",
+            "dtype_detail": ("LP solves f16 (f32 arithmetic); HP solves f32 inner + f64 reliable updates, "
+                             "f64 solution accumulation and dot products; HP loops (D_W s and contractions) "
+                             + ("float-float (~48-bit) arithmetic on the f64 solutions" if c["hp_loops"] == "ff"
+                                else "f64") + "; loop sums f64"),
             "data": "synthetic: smooth random SU(3) links U = exp(0.3 i H), Z4 sources",
             "config": {"workload": workload_name(c), "lattice": list(L), "n_sources": n_src,
                        "l2": "inputs larger than L2 (fields of 100-400 MB each)",
@@ -701,13 +705,15 @@ def main():
     ap.add_argument("--overlap", type=int, default=None, help="override HP/LP stream overlap")
     ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
+    ap.add_argument("--hp-loops", default=None, choices=["f64", "ff"],
+                    help="precision of the HP loops (D_W s and contractions)")
     ap.add_argument("--dslash", action="store_true", help="time tm_dslash alone")
     ap.add_argument("--next", action="store_true", help="time HPE, time dilution, momentum projection")
     ap.add_argument("--solvers", action="store_true", help="time graph-replayed and grouped solves")
     ap.add_argument("--contract", action="store_true", help="time the loop contractions alone")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--nrhs", type=int, default=16)
-    ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16", "ff"])
     args = ap.parse_args()
     c = CONFIGS[args.config]
     if args.schur is not None:
@@ -724,6 +730,8 @@ def main():
         c["lp_prec"] = args.lp_prec
     if args.hp_inner is not None:
         c["hp_inner"] = args.hp_inner
+    if args.hp_loops is not None:
+        c["hp_loops"] = args.hp_loops
     if args.dslash:
         run_dslash(args)
     elif args.next:

@@ -63,7 +63,12 @@ typedef enum {
   TM_PREC_F64 = 0,
   TM_PREC_F32 = 1,
   TM_PREC_F16 = 2,  /* IEEE binary16 storage, FP32 arithmetic */
-  TM_PREC_BF16 = 3  /* bfloat16 storage, FP32 arithmetic */
+  TM_PREC_BF16 = 3, /* bfloat16 storage, FP32 arithmetic */
+  TM_PREC_FF = 4    /* float-float: each real is a pair (hi, lo) of FP32 values
+                       (8 bytes) summing to it, about 48 significant bits, FP32
+                       exponent range; float-float arithmetic on the FP32 pipes.
+                       For the Dslash, the contractions and the layout helpers;
+                       not a solver precision (tm_cg_solve returns TM_ERR_ARG). */
 } tm_prec_t;
 
 typedef struct { int L[4]; } tm_geom_t;

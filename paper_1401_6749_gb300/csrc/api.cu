@@ -117,9 +117,10 @@ int dslash_nr_override() {
 
 // ------------------------------------------------------------ dispatch
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
-  const bool r12 = (int)prec >= 0 && (int)prec < 4 && op->recon_p[prec] == 12;
+  const bool r12 = (int)prec >= 0 && (int)prec < kNumPrec && op->recon_p[prec] == 12;
   switch (prec) {
     case TM_PREC_F64: return dslash_launch<double, 18>(op, c, s);
+    case TM_PREC_FF: return dslash_launch<FFloat, 18>(op, c, s);
     case TM_PREC_F32: return r12 ? dslash_launch<float, 12>(op, c, s) : dslash_launch<float, 18>(op, c, s);
     case TM_PREC_F16: return r12 ? dslash_launch<__half, 12>(op, c, s) : dslash_launch<__half, 18>(op, c, s);
     case TM_PREC_BF16:
@@ -211,6 +212,7 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   op->mu = p->mu;
   // per precision; F64 always stores the full matrix
   op->recon_p[TM_PREC_F64] = 18;
+  op->recon_p[TM_PREC_FF] = 18;
   op->recon_p[TM_PREC_F32] = p->recon ? p->recon : 12;
   op->recon_p[TM_PREC_F16] = p->recon ? p->recon : 18;
   op->recon_p[TM_PREC_BF16] = p->recon ? p->recon : 18;
@@ -219,9 +221,9 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   op->host_flags = nullptr;
   op->host_flags_n = 0;
   op->owns_links = true;
-  for (int i = 0; i < 4; ++i) op->links[i] = nullptr;
+  for (int i = 0; i < kNumPrec; ++i) op->links[i] = nullptr;
   const cudaStream_t st = (cudaStream_t)s;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kNumPrec; ++i) {
     const tm_prec_t pr = (tm_prec_t)i;
     const size_t nb = link_bytes(op->g, pr, op->recon_p[i]);
     if (cudaMalloc(&op->links[i], nb) != cudaSuccess) {
@@ -256,7 +258,7 @@ extern "C" tm_status_t tm_op_clone(tm_op_t** out, const tm_op_t* src) {
 
 extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
   if (!op) return TM_OK;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < kNumPrec; ++i)
     if (op->links[i] && op->owns_links) cudaFree(op->links[i]);
   if (op->work) cudaFree(op->work);
   if (op->host_flags) cudaFreeHost(op->host_flags);

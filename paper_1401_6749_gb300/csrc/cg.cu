@@ -364,7 +364,7 @@ static tm_status_t check_params(const tm_cg_params_t* prm) {
   if (prm->schur != 0 && prm->schur != 1) { set_error("tm_cg_solve: schur must be 0 or 1"); return TM_ERR_ARG; }
   if (prm->graph != 0 && prm->graph != 1) { set_error("tm_cg_solve: graph must be 0 or 1"); return TM_ERR_ARG; }
   const tm_prec_t lo = mixed ? prm->inner_prec : prm->prec;
-  if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: unknown precision"); return TM_ERR_ARG; }
+  if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: precision must be F64, F32, F16 or BF16"); return TM_ERR_ARG; }
   return TM_OK;
 }
 

@@ -23,7 +23,6 @@ namespace tml {
 // v[0..31] per lane in, lane l returns the warp sum of component l.
 template <class T>
 __device__ __forceinline__ T warp_transpose_reduce(T (&v)[32]) {
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int w = 16; w >= 1; w >>= 1) {
@@ -32,7 +31,7 @@ __device__ __forceinline__ T warp_transpose_reduce(T (&v)[32]) {
     for (int i = 0; i < w; ++i) {
       const T send = up ? v[i] : v[i + w];
       const T keep = up ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(full, send, w);
+      v[i] = keep + shfl_xor(send, w);
     }
   }
   return v[0];
@@ -81,10 +80,16 @@ __global__ void __launch_bounds__(256) local_partial_kernel(Geom g, const void* 
                          (long)((mom.p[q][2] * st.c[2]) % g.L[2]) * g.L[0] * g.L[1];
         const long den = (long)g.L[0] * g.L[1] * g.L[2];
         const double frac = (double)(num % den) / (double)den;
-        R sn, cn;
-        if constexpr (std::is_same<R, double>::value) sincospi(-2.0 * frac, &sn, &cn);
-        else sincospif(-2.0f * (float)frac, &sn, &cn);
-        const Cx<R> ph = {cn, sn};
+        Cx<R> ph;
+        if constexpr (kWide<R>) {
+          double sn, cn;
+          sincospi(-2.0 * frac, &sn, &cn);
+          ph = {(R)cn, (R)sn};
+        } else {
+          float sn, cn;
+          sincospif(-2.0f * (float)frac, &sn, &cn);
+          ph = {cn, sn};
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) r[k] = ph * r[k];
       }
@@ -181,6 +186,12 @@ __device__ __forceinline__ void load_spins2(Cx<typename Prec<S>::R> (&v)[6], con
       const double2 d = reinterpret_cast<const double2*>(f)[b0 + (6 * h + j) * cs];
       v[j] = {d.x, d.y};
     }
+  } else if constexpr (std::is_same<S, FFloat>::value) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float4 d = reinterpret_cast<const float4*>(f)[b0 + (6 * h + j) * cs];
+      v[j] = {FF{d.x, d.y}, FF{d.z, d.w}};
+    }
   } else if constexpr (std::is_same<S, float>::value) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -215,15 +226,15 @@ __device__ __forceinline__ void link_times2(Cx<R> (&w)[6], const Mat3<R>& U, con
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       R zr = SUB ? w[3 * a + c].re : (R)0, zi = SUB ? w[3 * a + c].im : (R)0;
-      const R sg = SUB ? (R)-1 : (R)1;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const Cx<R> u = ADJ ? conjx(U.m[d][c]) : U.m[c][d];
+        const Cx<R> u0 = ADJ ? conjx(U.m[d][c]) : U.m[c][d];
+        const Cx<R> u = SUB ? Cx<R>{-u0.re, -u0.im} : u0;  // subtract: negated (exactly) link
         const Cx<R> x = r[3 * a + d];
-        zr = O::fma(sg * u.re, x.re, zr);
-        zr = O::fma(-sg * u.im, x.im, zr);
-        zi = O::fma(sg * u.re, x.im, zi);
-        zi = O::fma(sg * u.im, x.re, zi);
+        zr = O::fma(u.re, x.re, zr);
+        zr = O::fma(-u.im, x.im, zr);
+        zi = O::fma(u.re, x.im, zi);
+        zi = O::fma(u.im, x.re, zi);
       }
       w[3 * a + c] = {zr, zi};
     }
@@ -238,15 +249,19 @@ __device__ __forceinline__ void outer_acc2(R (&acc)[16], const void* Lf, size_t 
   Cx<R> ws[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) ws[j] = {sgn * w[j].re, sgn * w[j].im};
-  if constexpr (std::is_same<S, double>::value) {
-    const double2* f = reinterpret_cast<const double2*>(Lf);
+  if constexpr (kWide<R>) {
 #pragma unroll 1
     for (int a = 0; a < 4; ++a) {
       Cx<R> l[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double2 d = f[b0 + (3 * a + c) * cs];
-        l[c] = {d.x, d.y};
+        if constexpr (std::is_same<S, double>::value) {
+          const double2 d = reinterpret_cast<const double2*>(Lf)[b0 + (3 * a + c) * cs];
+          l[c] = {d.x, d.y};
+        } else {
+          const float4 d = reinterpret_cast<const float4*>(Lf)[b0 + (3 * a + c) * cs];
+          l[c] = {FF{d.x, d.y}, FF{d.z, d.w}};
+        }
       }
       // a runtime index into acc would move it to local memory: select instead
 #pragma unroll
@@ -292,10 +307,9 @@ __device__ __forceinline__ void outer_acc2(R (&acc)[16], const void* Lf, size_t 
 // v[0..15] per lane in; lane l returns the warp sum of component l & 15
 template <class T>
 __device__ __forceinline__ T warp_transpose_reduce16(T (&v)[16]) {
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(full, v[i], 16);
+  for (int i = 0; i < 16; ++i) v[i] += shfl_xor(v[i], 16);
 #pragma unroll
   for (int w = 8; w >= 1; w >>= 1) {
     const bool up = (lane & w) != 0;
@@ -303,7 +317,7 @@ __device__ __forceinline__ T warp_transpose_reduce16(T (&v)[16]) {
     for (int i = 0; i < w; ++i) {
       const T send = up ? v[i] : v[i + w];
       const T keep = up ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(full, send, w);
+      v[i] = keep + shfl_xor(send, w);
     }
   }
   return v[0];
@@ -475,8 +489,13 @@ static tm_status_t by_prec_c(tm_prec_t p, F&& f) {
     case TM_PREC_F32: return f(float{});
     case TM_PREC_F16: return f(__half{});
     case TM_PREC_BF16: return f(__nv_bfloat16{});
+    case TM_PREC_FF: return f(FFloat{});
     default: set_error("unknown precision %d", (int)p); return TM_ERR_ARG;
   }
+}
+
+static const char* prec_name(const char* const (&names)[kNumPrec], tm_prec_t p) {
+  return names[(unsigned)p < (unsigned)kNumPrec ? (int)p : 0];
 }
 
 static tm_status_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
@@ -498,8 +517,8 @@ tm_status_t local_contract_into(const Geom& g, const void* left, const void* rig
                                 int nrhs, int p_g5, double* out, double* scratch, cudaStream_t s) {
   const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
   const dim3 grid(nchunk, 2 * g.L[3], nrhs);
-  static const char* const kNames[4] = {"local.f64", "local.f32", "local.f16", "local.bf16"};
-  TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nrhs);
+  static const char* const kNames[kNumPrec] = {"local.f64", "local.f32", "local.f16", "local.bf16", "local.ff"};
+  TraceScope tr(s, prec_name(kNames, prec), 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nrhs);
   tm_status_t st = by_prec_c(prec, [&](auto tag) {
     using S = decltype(tag);
     local_partial_kernel<S><<<grid, 256, 0, s>>>(g, left, right, nchunk, scratch);
@@ -542,7 +561,7 @@ extern "C" tm_status_t loop_contract_local_mom(const tm_geom_t* gg, const void* 
   if (!gg || !left || !right || !out || !mom || nrhs < 0) { set_error("loop_contract_local_mom: null argument"); return TM_ERR_ARG; }
   if (!valid_mode(mode)) { set_error("loop_contract_local_mom: unknown mode %d", (int)mode); return TM_ERR_ARG; }
   if (n_mom < 1 || n_mom > kMaxMom) { set_error("loop_contract_local_mom: 1 <= n_mom <= %d", kMaxMom); return TM_ERR_ARG; }
-  if ((int)prec < 0 || (int)prec > 3) { set_error("loop_contract_local_mom: unknown precision"); return TM_ERR_ARG; }
+  if ((int)prec < 0 || (int)prec >= kNumPrec) { set_error("loop_contract_local_mom: unknown precision"); return TM_ERR_ARG; }
   if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
   if (nrhs == 0) return TM_OK;
   if ((long)nrhs * n_mom > 65535) { set_error("loop_contract_local_mom: nrhs * n_mom must be <= 65535"); return TM_ERR_ARG; }
@@ -562,8 +581,9 @@ extern "C" tm_status_t loop_contract_local_mom(const tm_geom_t* gg, const void* 
   const int nchunk = (g.V3h + kLocalChunk - 1) / kLocalChunk;
   const dim3 grid(nchunk * n_mom, 2 * g.L[3], nrhs);
   {
-    static const char* const kNames[4] = {"localmom.f64", "localmom.f32", "localmom.f16", "localmom.bf16"};
-    TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, n2);
+    static const char* const kNames[kNumPrec] = {"localmom.f64", "localmom.f32", "localmom.f16", "localmom.bf16",
+                                                  "localmom.ff"};
+    TraceScope tr(s, prec_name(kNames, prec), 2.0 * 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, n2);
     st = by_prec_c(prec, [&](auto tag) {
       using S = decltype(tag);
       local_partial_kernel<S, true><<<grid, 256, 0, s>>>(g, left, right, nchunk, scratch, ml);
@@ -586,7 +606,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
                                           double* out, tm_stream_t strm) {
   if (!op || !left || !right || !out || nrhs < 0) { set_error("loop_contract_oneD: null argument"); return TM_ERR_ARG; }
   if (!valid_mode(mode)) { set_error("loop_contract_oneD: unknown mode %d", (int)mode); return TM_ERR_ARG; }
-  if ((int)prec < 0 || (int)prec > 3) { set_error("loop_contract_oneD: unknown precision %d", (int)prec); return TM_ERR_ARG; }
+  if ((int)prec < 0 || (int)prec >= kNumPrec) { set_error("loop_contract_oneD: unknown precision %d", (int)prec); return TM_ERR_ARG; }
   if (nrhs == 0) return TM_OK;
   if (nrhs > 65535) { set_error("loop_contract_oneD: nrhs must be <= 65535"); return TM_ERR_ARG; }
   const cudaStream_t s = (cudaStream_t)strm;
@@ -599,13 +619,15 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   const dim3 block(kOneDLanes, 8);
   const bool r12 = op->recon_p[prec] == 12;
   const void* links = op->links[prec];
-  static const char* const kNames[4] = {"oneD.f64", "oneD.f32", "oneD.f16", "oneD.bf16"};
+  static const char* const kNames[kNumPrec] = {"oneD.f64", "oneD.f32", "oneD.f16", "oneD.bf16", "oneD.ff"};
   const double esz = (double)prec_size(prec);
-  const double lreals = (prec == TM_PREC_F64 || !r12) ? 18.0 : 12.0;
-  TraceScope tr(s, kNames[prec & 3], 2.0 * 24.0 * esz * 2.0 * g.Vh, 4.0 * lreals * esz * 2.0 * g.Vh, nrhs);
+  const double lreals = r12 ? 12.0 : 18.0;
+  TraceScope tr(s, prec_name(kNames, prec), 2.0 * 24.0 * esz * 2.0 * g.Vh, 4.0 * lreals * esz * 2.0 * g.Vh, nrhs);
   switch (prec) {
     case TM_PREC_F64:
       oneD_partial_kernel<double, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch); break;
+    case TM_PREC_FF:
+      oneD_partial_kernel<FFloat, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch); break;
     case TM_PREC_F32:
       if (r12) oneD_partial_kernel<float, 12><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
       else oneD_partial_kernel<float, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);

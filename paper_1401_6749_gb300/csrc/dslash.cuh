@@ -43,6 +43,12 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
+template <> struct Ar<FF> {
+  static __device__ __forceinline__ FF add(FF a, FF b) { return a + b; }
+  static __device__ __forceinline__ FF sub(FF a, FF b) { return a - b; }
+  static __device__ __forceinline__ FF mul(FF a, FF b) { return a * b; }
+  static __device__ __forceinline__ FF fma(FF a, FF b, FF c) { return ff_fma(a, b, c); }
+};
 template <> struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
@@ -250,7 +256,9 @@ constexpr int dslash_min_blocks() {
 #ifdef TM_DSLASH_MINBLOCKS
   return TM_DSLASH_MINBLOCKS;
 #else
-  return std::is_same<S, double>::value ? 1 : (std::is_same<S, float>::value ? 6 : 7);
+  return std::is_same<S, double>::value ? 1
+       : std::is_same<S, FFloat>::value ? 2
+       : (std::is_same<S, float>::value ? 6 : 7);
 #endif
 }
 
@@ -328,10 +336,12 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
     TM_HOPS(3)
 #undef TM_HOPS
     // FP32 copies for the narrow formats: no FP64 arithmetic in their kernels
-    constexpr bool kF64 = std::is_same<R, double>::value;
-    const R shop = kF64 ? (R)a.hop_scale : (R)a.hop_scale_f;
-    const R nu = kF64 ? (R)a.nu : (R)a.nu_f;
-    const R inv = kF64 ? (R)a.inv : (R)a.inv_f;
+    R shop, nu, inv;
+    if constexpr (kWide<R>) {
+      shop = (R)a.hop_scale; nu = (R)a.nu; inv = (R)a.inv;
+    } else {
+      shop = a.hop_scale_f; nu = a.nu_f; inv = a.inv_f;
+    }
     const void* cfield = a.c.cfield ? a.c.cfield : a.c.in;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -428,11 +438,12 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   const int site_blocks = c.parity < 0 ? 2 * per_par : per_par;
   dim3 grid((unsigned)(site_blocks * a.rhs_groups));
   // trace class: dslash.<precision>.<epilogue>
-  static const char* const kNames[4][3] = {
+  static const char* const kNames[5][3] = {
       {"dslash.f64.out", "dslash.f64.cgupd", "dslash.f64.resid"},
       {"dslash.f32.out", "dslash.f32.cgupd", "dslash.f32.resid"},
       {"dslash.f16.out", "dslash.f16.cgupd", "dslash.f16.resid"},
-      {"dslash.bf16.out", "dslash.bf16.cgupd", "dslash.bf16.resid"}};
+      {"dslash.bf16.out", "dslash.bf16.cgupd", "dslash.bf16.resid"},
+      {"dslash.ff.out", "dslash.ff.cgupd", "dslash.ff.resid"}};
   const char* name = kNames[Prec<S>::id][EPI];
   // algorithmic bytes: every array once; per active system the neighbour field
   // (one parity's worth per output parity), the centre field, the epilogue's
@@ -442,7 +453,7 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   const int centre = a.c.centre != 0 ? 1 : 0;
   const int epi_streams = EPI == EPI_OUT ? 1 : (EPI == EPI_CGUPD ? 5 : 2);
   const double per_rhs = out_sites * 24.0 * e * (1 + centre + epi_streams);
-  const int link_reals = std::is_same<S, double>::value ? 18 : RECON;
+  const int link_reals = RECON;
   const double fixed = 4.0 * 2.0 * op->g.Vh * link_reals * e;
   cudaEvent_t ev = nullptr;
   a.trace_count = trace_begin(st, &ev);
@@ -452,13 +463,14 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   return check_launch("dslash");
 }
 
-// systems per thread: FP64 is arithmetic-bound and register-heavy (1); the
-// narrower formats share the site work over up to 4 systems
+// systems per thread: FP64 and float-float are arithmetic-bound and
+// register-heavy (1); the narrower formats share the site work over up to 4
+// systems
 int dslash_nr_override();
 
 template <class S, int RECON, bool DAG, int EPI>
 tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
-  if constexpr (std::is_same<S, double>::value) {
+  if constexpr (std::is_same<S, double>::value || std::is_same<S, FFloat>::value) {
     return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
   } else {
     // measured at 32^3 x 64 with 16 systems: one system per thread is fastest

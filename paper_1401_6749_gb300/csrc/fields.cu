@@ -15,6 +15,11 @@ __device__ __forceinline__ void store_spinor_f64(void* field, size_t b0, size_t 
                                                  const Cx<double> (&v)[12]) {
   if constexpr (std::is_same<S, double>::value) {
     store_spinor<double>(field, b0, cs, v);
+  } else if constexpr (std::is_same<S, FFloat>::value) {
+    Cx<FF> w[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) w[j] = {FF(v[j].re), FF(v[j].im)};
+    store_spinor<FFloat>(field, b0, cs, w);
   } else if constexpr (std::is_same<S, float>::value) {
     Cx<float> w[12];
 #pragma unroll
@@ -57,6 +62,7 @@ tm_status_t by_prec(tm_prec_t p, F&& f) {
     case TM_PREC_F32: return f(float{});
     case TM_PREC_F16: return f(__half{});
     case TM_PREC_BF16: return f(__nv_bfloat16{});
+    case TM_PREC_FF: return f(FFloat{});
     default: set_error("unknown precision %d", (int)p); return TM_ERR_ARG;
   }
 }
@@ -180,6 +186,10 @@ __global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc
 template <class S>
 __device__ __forceinline__ S from_f64(double v) {
   if constexpr (std::is_same<S, double>::value) return v;
+  else if constexpr (std::is_same<S, FFloat>::value) {
+    const FF f(v);
+    return FFloat{f.hi, f.lo};
+  }
   else if constexpr (std::is_same<S, float>::value) return (float)v;
   else if constexpr (std::is_same<S, __half>::value) return __double2half(v);
   else return __double2bfloat16(v);
@@ -224,6 +234,7 @@ size_t link_bytes(const Geom& g, tm_prec_t p, int recon) {
   const bool r12 = recon == 12;
   switch (p) {
     case TM_PREC_F64: return link_bytes_t<double, 18>(g);
+    case TM_PREC_FF: return link_bytes_t<FFloat, 18>(g);
     case TM_PREC_F32: return r12 ? link_bytes_t<float, 12>(g) : link_bytes_t<float, 18>(g);
     case TM_PREC_F16: return r12 ? link_bytes_t<__half, 12>(g) : link_bytes_t<__half, 18>(g);
     default: return r12 ? link_bytes_t<__nv_bfloat16, 12>(g) : link_bytes_t<__nv_bfloat16, 18>(g);
@@ -236,6 +247,7 @@ tm_status_t pack_links(const Geom& g, tm_prec_t p, int recon, void* out, const d
   const unsigned nb = blocks_for(n, 256);
   const bool r12 = recon == 12;
   if (p == TM_PREC_F64) pack_links_kernel<double, 18><<<nb, 256, 0, s>>>(g, out, U);
+  else if (p == TM_PREC_FF) pack_links_kernel<FFloat, 18><<<nb, 256, 0, s>>>(g, out, U);
   else if (p == TM_PREC_F32 && r12) pack_links_kernel<float, 12><<<nb, 256, 0, s>>>(g, out, U);
   else if (p == TM_PREC_F32) pack_links_kernel<float, 18><<<nb, 256, 0, s>>>(g, out, U);
   else if (p == TM_PREC_F16 && r12) pack_links_kernel<__half, 12><<<nb, 256, 0, s>>>(g, out, U);

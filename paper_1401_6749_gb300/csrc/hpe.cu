@@ -62,7 +62,7 @@ extern "C" tm_status_t tm_hpe_apply(tm_op_t* op, void* out, const void* in, int 
                                     tm_prec_t prec, tm_stream_t strm) {
   if (!op || !out || !in || nrhs < 0 || order < 0) { set_error("tm_hpe_apply: bad argument"); return TM_ERR_ARG; }
   if (out == in) { set_error("tm_hpe_apply: out and in must not overlap"); return TM_ERR_ARG; }
-  if ((int)prec < 0 || (int)prec > 3) { set_error("tm_hpe_apply: unknown precision"); return TM_ERR_ARG; }
+  if ((int)prec < 0 || (int)prec >= kNumPrec) { set_error("tm_hpe_apply: unknown precision"); return TM_ERR_ARG; }
   if (nrhs == 0) return TM_OK;
   const cudaStream_t s = (cudaStream_t)strm;
   const tm_geom_t gg = {{op->g.L[0], op->g.L[1], op->g.L[2], op->g.L[3]}};

@@ -60,6 +60,71 @@ __device__ __forceinline__ Cx<R> iphase_rt(int k, Cx<R> a) {
   }
 }
 
+// ------------------------------------------------------------ float-float
+// A real number as the unevaluated sum hi + lo of two FP32 values (|lo| at most
+// half an ulp of hi): about 48 significant bits with the FP32 exponent range,
+// computed on the FP32 pipes, which on GB300 run 64x the FP64 rate.  Built on
+// the error-free transformations of Knuth (two-sum: s + e = a + b exactly)
+// and Dekker (fast two-sum for |a| >= |b|; the exact product a b = p + e with
+// e = fma(a, b, -p)).  The low parts are added without compensation (the
+// "sloppy" addition of the double-double literature), so each operation errs
+// by a few 2^-47 of the size of its operands rather than of its result.  Every
+// step uses an explicit round-to-nearest intrinsic, so the compiler can
+// neither contract nor reorder it.
+struct FF {
+  float hi, lo;
+  FF() = default;
+  __host__ __device__ constexpr FF(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ constexpr FF(float v) : hi(v), lo(0.0f) {}
+  __host__ __device__ constexpr FF(float h, float l) : hi(h), lo(l) {}
+  // hi: d rounded to the nearest FP32; lo: the (exact) remainder, rounded
+  __host__ __device__ explicit FF(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+__device__ __forceinline__ FF operator-(FF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ FF operator+(FF a, FF b) {
+  const FF s = ff_two_sum(a.hi, b.hi);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF operator-(FF a, FF b) { return a + (-b); }
+__device__ __forceinline__ FF operator*(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+// a b + c with one renormalisation
+__device__ __forceinline__ FF ff_fma(FF a, FF b, FF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const FF s = ff_two_sum(p, c.hi);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+__device__ __forceinline__ FF& operator+=(FF& a, FF b) { return a = a + b; }
+__device__ __forceinline__ FF shfl_xor(FF v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+template <class T>
+__device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+// Storage of a float-float real: the pair (hi, lo), 8 bytes like FP64.
+struct FFloat {
+  float hi, lo;
+};
+
 // ------------------------------------------------------- storage precisions
 // Storage type S -> arithmetic type R and how many reals one 16-byte chunk holds.
 template <class S> struct Prec;
@@ -67,13 +132,22 @@ template <> struct Prec<double> { using R = double; static constexpr int kChunkR
 template <> struct Prec<float> { using R = float; static constexpr int kChunkReals = 4; static constexpr tm_prec_t id = TM_PREC_F32; };
 template <> struct Prec<__half> { using R = float; static constexpr int kChunkReals = 8; static constexpr tm_prec_t id = TM_PREC_F16; };
 template <> struct Prec<__nv_bfloat16> { using R = float; static constexpr int kChunkReals = 8; static constexpr tm_prec_t id = TM_PREC_BF16; };
+template <> struct Prec<FFloat> { using R = FF; static constexpr int kChunkReals = 2; static constexpr tm_prec_t id = TM_PREC_FF; };
+
+// arithmetic wider than FP32 (kernel constants are taken in FP64 for these)
+template <class R>
+constexpr bool kWide = std::is_same<R, double>::value || std::is_same<R, FF>::value;
 
 template <class S>
 __host__ __device__ constexpr int spinor_chunks() { return 24 / Prec<S>::kChunkReals; }
 
+// number of storage precisions (tm_prec_t values 0 .. kNumPrec - 1)
+constexpr int kNumPrec = 5;
+
 inline size_t prec_size(tm_prec_t p) {
   switch (p) {
     case TM_PREC_F64: return 8;
+    case TM_PREC_FF: return 8;
     case TM_PREC_F32: return 4;
     default: return 2;
   }
@@ -194,6 +268,12 @@ __device__ __forceinline__ void load_spinor(Cx<typename Prec<S>::R> (&v)[12], co
       const double2 d = reinterpret_cast<const double2*>(f)[b0 + j * cs];
       v[j] = {d.x, d.y};
     }
+  } else if constexpr (std::is_same<S, FFloat>::value) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const float4 d = reinterpret_cast<const float4*>(f)[b0 + j * cs];
+      v[j] = {FF{d.x, d.y}, FF{d.z, d.w}};
+    }
   } else if constexpr (std::is_same<S, float>::value) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -224,6 +304,10 @@ __device__ __forceinline__ void store_spinor(void* field, size_t b0, size_t cs,
 #pragma unroll
     for (int j = 0; j < 12; ++j)
       reinterpret_cast<double2*>(f)[b0 + j * cs] = make_double2(v[j].re, v[j].im);
+  } else if constexpr (std::is_same<S, FFloat>::value) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j)
+      reinterpret_cast<float4*>(f)[b0 + j * cs] = make_float4(v[j].re.hi, v[j].re.lo, v[j].im.hi, v[j].im.lo);
   } else if constexpr (std::is_same<S, float>::value) {
 #pragma unroll
     for (int j = 0; j < 6; ++j)
@@ -248,15 +332,17 @@ __device__ __forceinline__ void store_spinor(void* field, size_t b0, size_t cs,
 // third row is conj(row0 x row1)), packed row-major into units of
 // kCplxPerUnit complex numbers, the last unit zero-padded:
 //   F64: double2 units (1 complex): 9 or 6 units of 16 bytes.
+//   FF: (re.hi, re.lo, im.hi, im.lo) units (1 complex): 9 units of 16 bytes.
 //   F32: float4 units (2 complex): 5 (18) or 3 (12) units of 16 bytes.
 //   F16/BF16: RECON 18 -> 16-byte units of 4 complex (3 units),
 //             RECON 12 -> 8-byte units of 2 complex (3 units).
 template <class S, int RECON>
 struct LinkFmt {
   static constexpr bool kF64 = std::is_same<S, double>::value;
+  static constexpr bool kFF = std::is_same<S, FFloat>::value;
   static constexpr bool kF32 = std::is_same<S, float>::value;
   static constexpr int kCplx = RECON == 18 ? 9 : 6;
-  static constexpr int kCplxPerUnit = kF64 ? 1 : (kF32 ? 2 : (RECON == 18 ? 4 : 2));
+  static constexpr int kCplxPerUnit = (kF64 || kFF) ? 1 : (kF32 ? 2 : (RECON == 18 ? 4 : 2));
   static constexpr int NU = (kCplx + kCplxPerUnit - 1) / kCplxPerUnit;
   static constexpr int kUnitBytes = kCplxPerUnit * 2 * (int)sizeof(S);
 };
@@ -281,6 +367,13 @@ __device__ __forceinline__ Mat3<typename Prec<S>::R> load_link(const void* links
     for (int u = 0; u < F::NU; ++u) {
       const double2 d = p[b0 + u * cs];
       e[u] = {d.x, d.y};
+    }
+  } else if constexpr (F::kFF) {
+    const float4* p = reinterpret_cast<const float4*>(links);
+#pragma unroll
+    for (int u = 0; u < F::NU; ++u) {
+      const float4 d = p[b0 + u * cs];
+      e[u] = {FF{d.x, d.y}, FF{d.z, d.w}};
     }
   } else if constexpr (F::kF32) {
     const float4* p = reinterpret_cast<const float4*>(links);

@@ -11,8 +11,8 @@ struct tm_op {
   tml::Geom g;
   double kappa;
   double mu;
-  int recon_p[4];     // link format (12 or 18 reals) of the copy of each precision
-  void* links[4];     // indexed by tm_prec_t; F64 always 18-real
+  int recon_p[tml::kNumPrec];  // link format (12 or 18 reals) of the copy of each precision
+  void* links[tml::kNumPrec];  // indexed by tm_prec_t; F64 and FF always 18-real
   // solver work space, grown on demand, owned by the operator
   void* work;
   size_t work_bytes;

@@ -19,14 +19,14 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 # precisions, modes, status codes (tmloops.h)
-F64, F32, F16, BF16 = 0, 1, 2, 3
-PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+F64, F32, F16, BF16, FF = 0, 1, 2, 3, 4
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "ff": FF}
 CG_PLAIN, CG_MIXED = 0, 1
 LOOP_STD, LOOP_VV, LOOP_GEN = 0, 1, 2
 LOOP_MODE = {"std": LOOP_STD, "vv": LOOP_VV, "gen": LOOP_GEN}
 STATUS = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_CUDA", 3: "TM_ERR_NOCONV", 4: "TM_ERR_NAN",
           5: "TM_ERR_TIMEOUT", 6: "TM_ERR_UNSUPPORTED"}
-ELEM_SIZE = {F64: 8, F32: 4, F16: 2, BF16: 2}
+ELEM_SIZE = {F64: 8, F32: 4, F16: 2, BF16: 2, FF: 8}
 
 
 class TmError(RuntimeError):
@@ -134,7 +134,7 @@ def empty_field(L, prec, nrhs, device="cuda"):
 def link_reals(recon, prec):
     """Reals stored per link in the operator's copy of precision prec
     (recon 0 = per precision: 12 for F32, 18 for F16/BF16; F64 always 18)."""
-    if prec == F64:
+    if prec in (F64, FF):
         return 18
     if recon == 0:
         return 12 if prec == F32 else 18

@@ -10,7 +10,10 @@ For sources r = first .. first + N_HP + N_LP - 1 (Z4, Sec. 2):
     reliable updates) to tol_hp;
   * for every solution s: local and one-derivative loops with the one-end
     trick (L = R = s, P = g5, Eq. 5) and its generalisation (L = s,
-    R = g5 D_W s, P = g5, Eq. 6);
+    R = g5 D_W s, P = g5, Eq. 6); for the HP solutions D_W s and the
+    contractions run in hp_loop_prec: F64, or FF (float-float, about 48 bits
+    on the FP32 pipes, after one conversion of the FP64 solution), whose
+    loops agree with the FP64 ones to ~1e-13 relative;
   * TSM combination with prefactor -2 i nu (one-end) and 2 (generalised).
 The LP solve of a source is the same function of the source in every batch
 (per-system arithmetic, fixed-order reductions), so the correction term of
@@ -28,7 +31,7 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
-                 delta=0.1, kinds=KINDS, schur=True, overlap=False):
+                 delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64):
         """overlap: run the high-precision solves and contractions on a second
         stream from a host thread, concurrently with the low-precision batches
         (FP64 work uses other units than the FP32 arithmetic of the LP solves);
@@ -46,6 +49,9 @@ class TsmPipeline:
         self.seed, self.first = int(seed), int(first_src)
         self.max_iter, self.check_every, self.delta = max_iter, check_every, delta
         self.schur = bool(schur)
+        if hp_loop_prec not in (tl.F64, tl.FF):
+            raise ValueError("hp_loop_prec must be F64 or FF")
+        self.hp_loop_prec = hp_loop_prec
         self.kinds = tuple(kinds)
         self.nu = 2.0 * op.kappa * op.mu
         n_all = self.n_hp + self.n_lp
@@ -59,27 +65,38 @@ class TsmPipeline:
         b = min(self.batch, n_all)
         self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(4)]  # eta, x, D_W x, g5 D_W x
         nh = max(min(self.batch, self.n_hp), 1)
-        self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(4)] if self.n_hp else None
+        # eta, x, D_W x, g5 D_W x (the last two in hp_loop_prec, same byte size), and the
+        # copies of eta and x in hp_loop_prec when that is not F64
+        nf = 4 if hp_loop_prec == tl.F64 else 6
+        self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(nf)] if self.n_hp else None
         self.stats_lp, self.stats_hp = [], []
 
-    def _contract(self, op, x, w, g5w, prec, n, dst, row0, stream):
+    def _contract(self, op, x, w, g5w, prec, n, dst, row0, stream, eta=None):
         for k in self.kinds:
             kind, mode = k.split("_")
-            left, right = (x, x) if mode == "vv" else (x, g5w)
+            left, right = {"vv": (x, x), "gen": (x, g5w), "std": (eta, x)}[mode]
             out = dst[k][row0:row0 + n]
             if kind == "local":
                 tl.loop_contract_local(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
             else:
                 tl.loop_contract_oneD(op, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
 
-    def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None):
-        eta, x, w, g5w = fields
+    def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None,
+                            loop_prec=None):
+        eta, x, w, g5w = fields[:4]
         tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
         st, stats = tl.tm_cg_solve(op, x, eta, n, params, stream, raise_on_noconv=False)
+        if loop_prec is not None and loop_prec != prec:
+            # one conversion of the solution (and source) to the loop precision
+            eta_l, x_l = fields[4], fields[5]
+            tl.tm_spinor_convert(self.L, x_l, loop_prec, x, prec, n, stream)
+            if any(k.endswith("std") for k in self.kinds):
+                tl.tm_spinor_convert(self.L, eta_l, loop_prec, eta, prec, n, stream)
+            eta, x, prec = eta_l, x_l, loop_prec
         if any("gen" in k for k in self.kinds):
             tl.tm_dslash(op, w, x, n, mu_zero=True, prec=prec, stream=stream)
             tl.tm_gamma5(self.L, g5w, w, prec, n, stream)
-        self._contract(op, x, w, g5w, prec, n, dst, row0, stream)
+        self._contract(op, x, w, g5w, prec, n, dst, row0, stream, eta)
         return stats
 
     def _run_hp(self, stream):
@@ -89,7 +106,8 @@ class TsmPipeline:
         for b0 in range(0, self.n_hp, self.batch):
             n = min(self.batch, self.n_hp - b0)
             stats += self._solve_and_contract(self.op_hp, self._hp, tl.F64, self.first + b0, n,
-                                              hp_params, self.hp_loops, b0, stream)
+                                              hp_params, self.hp_loops, b0, stream,
+                                              loop_prec=self.hp_loop_prec)
         self.stats_hp = stats
 
     def run(self, dist=None):
