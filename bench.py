@@ -161,6 +161,22 @@ def _traffic_per_launch(alg_bytes):
     return int(round(float(kv["traffic_per_algorithmic_byte"]) * alg_bytes))
 
 
+def _tuned_shapes(tl, L):
+    """The autotuner's launch shapes for this lattice's half volume:
+    "<prec>.<out|resid>.<parity>.<n systems>" -> "<systems per thread>x<threads per block>"."""
+    vh = L[0] * L[1] * L[2] * L[3] // 2
+    pn = {0: "f64", 1: "f32", 2: "f16", 3: "bf16", 4: "ff"}
+    out = {}
+    for key, nr, bx in tl.tm_tune_entries():
+        if key["half_volume"] != vh:
+            continue
+        name = "%s%s.%s.%s.n%d" % (pn[key["prec"]], ".dag" if key["dagger"] else "",
+                                   "resid" if key["epilogue"] == 2 else "out",
+                                   {-1: "both", 0: "even", 1: "odd"}[key["parity"]], key["nrhs"])
+        out[name] = "%dx%d" % (nr, bx)
+    return out
+
+
 def _observables(pipe, c):
     """Per-source values of three volume-summed loops (sigma-term, g_A and
     Fig. 1 operator analogues) for the HP and LP sets, on the host."""
@@ -383,6 +399,7 @@ def run_ours(args):
                        "all_converged": ok},
             "fp64_cg_plain_s_per_source": round(t_plain, 4) if t_plain else None,
             "equal_error_speedup_vs_fp64_cg": speedup,
+            "dslash_shapes": _tuned_shapes(tl, L),
         }
         print(json.dumps(line), flush=True)
     op.close()

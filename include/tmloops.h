@@ -294,13 +294,34 @@ tm_status_t tsm_combine(const double *l_hp, const double *l_lp_on_hp, int n_hp,
  * launch the links of all sites); the kernel itself records how many systems
  * were active.  tm_trace_read returns, since the last reset, the launches,
  * summed device milliseconds and summed algorithmic bytes of a kernel class
- * "dslash.<f64|f32|f16|bf16>.<out|cgupd|resid>" (exact name, or a prefix
+ * "dslash.<f64|f32|f16|bf16|ff>.<out|cgupd|resid>", "local.<prec>",
+ * "oneD.<prec>", "blas.xpay", "z4_noise", "cg.graph" (exact name, or a prefix
  * ending in '*', e.g. "dslash.f16.*"); it synchronises the device.        */
 const char *tm_last_error(void);
 uint64_t tm_launch_count(void);
 void tm_trace_enable(int on);
 void tm_trace_reset(void);
 tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms, double *total_bytes);
+
+/* Autotuning of the FP32/FP16/BF16 Dslash launch shape (this library's own;
+ * the paper has no counterpart): systems per thread (1, 2, 4) and threads
+ * per block (32, 64, 128).  The first launch of each kind - precision, link
+ * format, dagger, epilogue, parity set, centre and inverse-twist terms, half
+ * volume and number of systems - times every shape on its own arguments
+ * (blocking the calling thread once) and the fastest is kept for the process;
+ * CG-update launches use the shape of the matching plain launch.  Results
+ * never depend on the shape.  Tuning is on unless the environment sets
+ * TM_TUNE=0; it is skipped while a CUDA graph is captured and when
+ * TM_DSLASH_NR fixes the systems per thread.
+ * tm_tune_enable(0/1) switches it at run time, tm_tune_reset forgets every
+ * choice, tm_tune_count gives the number of kinds tuned, and tm_tune_get(i,
+ * key[9], &nr, &block) reads entry i: key = {prec, reals per link, dagger,
+ * epilogue, parity (-1 both), centre (0 none, 1 copy, 2 twisted), inverse
+ * twist, half volume, systems}.                                           */
+void tm_tune_enable(int on);
+void tm_tune_reset(void);
+int tm_tune_count(void);
+tm_status_t tm_tune_get(int i, int *key, int *nr, int *block);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "tm_host.h"
@@ -83,9 +86,11 @@ static int* g_trace_counts = nullptr;  // device: active systems per traced laun
 static int g_trace_next = 0;
 constexpr int kTraceSlots = 1 << 20;
 
+static thread_local int t_tuning = 0;  // launches timed by the autotuner are not traced
+
 int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
   *ev0 = nullptr;
-  if (t_capturing || !g_trace_on.load(std::memory_order_relaxed)) return nullptr;
+  if (t_capturing || t_tuning || !g_trace_on.load(std::memory_order_relaxed)) return nullptr;
   std::lock_guard<std::mutex> lk(g_trace_mu);
   if (!g_trace_counts || g_trace_next >= kTraceSlots) return nullptr;
   if (cudaEventCreate(ev0) != cudaSuccess) { *ev0 = nullptr; return nullptr; }
@@ -115,6 +120,46 @@ int dslash_nr_override() {
   return v;
 }
 
+// ------------------------------------------------------------ autotuning
+// Process-wide cache of the chosen Dslash launch shapes.  TM_TUNE=0 disables
+// tuning (the built-in shape is used); tm_tune_enable overrides at run time.
+bool TuneKey::operator<(const TuneKey& o) const {
+  return std::tie(prec, recon, dag, epi, parity, centre, out_inv, vh, nrhs) <
+         std::tie(o.prec, o.recon, o.dag, o.epi, o.parity, o.centre, o.out_inv, o.vh, o.nrhs);
+}
+
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneCfg> g_tune;
+static std::atomic<int> g_tune_on{-1};
+
+static bool tune_on() {
+  int v = g_tune_on.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("TM_TUNE");
+    v = (e && atoi(e) == 0) ? 0 : 1;
+    g_tune_on.store(v, std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+bool tune_active() { return !t_capturing && tune_on(); }
+
+bool tune_lookup(const TuneKey& k, TuneCfg* c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+void tune_store(const TuneKey& k, const TuneCfg& c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[k] = c;
+}
+
+void tuning_begin() { ++t_tuning; }
+void tuning_end() { --t_tuning; }
+
 // ------------------------------------------------------------ dispatch
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
   const bool r12 = (int)prec >= 0 && (int)prec < kNumPrec && op->recon_p[prec] == 12;
@@ -139,6 +184,32 @@ using namespace tml;
 
 extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
 extern "C" uint64_t tm_launch_count(void) { return g_launches.load(); }
+
+extern "C" void tm_tune_enable(int on) { g_tune_on.store(on ? 1 : 0, std::memory_order_relaxed); }
+
+extern "C" void tm_tune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+extern "C" int tm_tune_count(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
+
+extern "C" tm_status_t tm_tune_get(int i, int* key, int* nr, int* block) {
+  if (!key || !nr || !block) { set_error("tm_tune_get: null argument"); return TM_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (i < 0 || i >= (int)g_tune.size()) { set_error("tm_tune_get: index %d out of range", i); return TM_ERR_ARG; }
+  auto it = g_tune.begin();
+  std::advance(it, i);
+  const TuneKey& k = it->first;
+  const int v[9] = {k.prec, k.recon, k.dag, k.epi, k.parity, k.centre, k.out_inv, k.vh, k.nrhs};
+  for (int j = 0; j < 9; ++j) key[j] = v[j];
+  *nr = it->second.nr;
+  *block = it->second.bx;
+  return TM_OK;
+}
 
 extern "C" void tm_trace_enable(int on) {
   std::lock_guard<std::mutex> lk(g_trace_mu);

@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
 }
 
 template <class S, int RECON, bool DAG, int EPI, int NR>
-tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
+tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, int bx = 128) {
   DslashArgs a;
   a.g = op->g;
   a.links = op->links[Prec<S>::id];
@@ -432,7 +432,6 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   a.hop_scale_f = (float)a.hop_scale;
   a.inv_f = (float)a.inv;
   a.nwarp = nwarp_of(op->g);
-  const int bx = 128;
   a.rhs_groups = (c.nrhs + NR - 1) / NR;
   const int per_par = (op->g.Vh + bx - 1) / bx;
   const int site_blocks = c.parity < 0 ? 2 * per_par : per_par;
@@ -463,23 +462,80 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   return check_launch("dslash");
 }
 
-// systems per thread: FP64 and float-float are arithmetic-bound and
-// register-heavy (1); the narrower formats share the site work over up to 4
-// systems
-int dslash_nr_override();
+// ------------------------------------------------------------- autotuning
+// Launch shape of the narrow-format Dslash: systems per thread (NR = 1, 2, 4:
+// the site's index arithmetic, link loads and reconstruction shared by NR
+// systems, against registers and occupancy) and threads per block (32, 64,
+// 128: small lattices fill more SMs with smaller blocks).  Results do not
+// depend on either (explicit round-to-nearest arithmetic per system, partial
+// sums per warp of 32 sites), so the first launch of each kind times every
+// shape on its own arguments and keeps the fastest for the process.  Only
+// launches that can be repeated without changing their result are timed
+// (EPI_OUT, EPI_RESID: out is a function of inputs it does not overwrite);
+// the CG-update launch takes the shape chosen for the plain launch of the same
+// operator form.  No tuning while a CUDA graph is being captured, nor while
+// TM_DSLASH_NR fixes NR.
+
+template <class S, int RECON, bool DAG, int EPI>
+tm_status_t launch_cfg(const tm_op* op, const DslashCall& c, cudaStream_t st, const TuneCfg& cfg) {
+  if (cfg.nr >= 4 && c.nrhs >= 4) return launch_one<S, RECON, DAG, EPI, 4>(op, c, st, cfg.bx);
+  if (cfg.nr >= 2 && c.nrhs >= 2) return launch_one<S, RECON, DAG, EPI, 2>(op, c, st, cfg.bx);
+  return launch_one<S, RECON, DAG, EPI, 1>(op, c, st, cfg.bx);
+}
+
+// time one launch shape: one warm-up launch, then the mean of three
+template <class S, int RECON, bool DAG, int EPI>
+float time_cfg(const tm_op* op, const DslashCall& c, cudaStream_t st, const TuneCfg& cfg) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.0f;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0f; }
+  float ms = -1.0f;
+  if (launch_cfg<S, RECON, DAG, EPI>(op, c, st, cfg) == TM_OK && cudaEventRecord(e0, st) == cudaSuccess) {
+    bool ok = true;
+    for (int i = 0; i < 3 && ok; ++i) ok = launch_cfg<S, RECON, DAG, EPI>(op, c, st, cfg) == TM_OK;
+    if (ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+      ms /= 3.0f;
+    else
+      ms = -1.0f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
 
 template <class S, int RECON, bool DAG, int EPI>
 tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
   if constexpr (std::is_same<S, double>::value || std::is_same<S, FFloat>::value) {
+    // FP64 and float-float: arithmetic-bound and register-heavy, one system per thread
     return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
   } else {
-    // measured at 32^3 x 64 with 16 systems: one system per thread is fastest
-    // (more per thread lowers occupancy more than it saves in shared site work)
+    TuneCfg cfg{1, 128};  // measured at 32^3 x 64 with 16 systems: NR = 1, 128 threads
     const int want = dslash_nr_override();
-    const int nr = want > 0 ? want : 1;
-    if (nr >= 4 && c.nrhs >= 4) return launch_one<S, RECON, DAG, EPI, 4>(op, c, st);
-    if (nr >= 2 && c.nrhs >= 2) return launch_one<S, RECON, DAG, EPI, 2>(op, c, st);
-    return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
+    if (want > 0) {
+      cfg.nr = want;
+      return launch_cfg<S, RECON, DAG, EPI>(op, c, st, cfg);
+    }
+    const TuneKey key{(int)Prec<S>::id, RECON, DAG ? 1 : 0, EPI == EPI_CGUPD ? (int)EPI_OUT : EPI,
+                      c.parity, c.centre, c.out_inv ? 1 : 0, op->g.Vh, c.nrhs};
+    if (tune_lookup(key, &cfg) || EPI == EPI_CGUPD || !tune_active())
+      return launch_cfg<S, RECON, DAG, EPI>(op, c, st, cfg);
+    float best = -1.0f;
+    TuneCfg pick = cfg;
+    tuning_begin();
+    for (int nr : {1, 2, 4}) {
+      if (nr > c.nrhs) continue;
+      for (int bx : {128, 64, 32}) {
+        const float t = time_cfg<S, RECON, DAG, EPI>(op, c, st, TuneCfg{nr, bx});
+        if (t > 0.0f && (best < 0.0f || t < best)) {
+          best = t;
+          pick = TuneCfg{nr, bx};
+        }
+      }
+    }
+    tuning_end();
+    tune_store(key, pick);
+    return launch_cfg<S, RECON, DAG, EPI>(op, c, st, pick);
   }
 }
 

@@ -24,6 +24,21 @@ struct tm_op {
 
 namespace tml {
 
+// Dslash launch-shape autotuning (cache in api.cu; selection in dslash.cuh)
+int dslash_nr_override();
+struct TuneKey {
+  int prec, recon, dag, epi, parity, centre, out_inv, vh, nrhs;
+  bool operator<(const TuneKey& o) const;
+};
+struct TuneCfg {
+  int nr, bx;
+};
+bool tune_lookup(const TuneKey& k, TuneCfg* c);
+void tune_store(const TuneKey& k, const TuneCfg& c);
+bool tune_active();   // tuning enabled and this thread not capturing a graph
+void tuning_begin();  // launches between these are timing runs (not traced)
+void tuning_end();
+
 enum Epi { EPI_OUT = 0, EPI_CGUPD = 1, EPI_RESID = 2 };
 
 // One Dslash application over nrhs fields, with an optional fused epilogue.

@@ -86,6 +86,10 @@ _SIGS = {
     "tm_trace_enable": [_i],
     "tm_trace_reset": [],
     "tm_trace_read": [ctypes.c_char_p, _P(_i), _P(_d), _P(_d)],
+    "tm_tune_enable": [_i],
+    "tm_tune_reset": [],
+    "tm_tune_count": [],
+    "tm_tune_get": [_i, _P(_i), _P(_i), _P(_i)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -96,6 +100,8 @@ _lib.tm_last_error.restype = ctypes.c_char_p
 _lib.tm_launch_count.restype = _u64
 _lib.tm_trace_enable.restype = None
 _lib.tm_trace_reset.restype = None
+_lib.tm_tune_enable.restype = None
+_lib.tm_tune_reset.restype = None
 
 EXPORTED = tuple(_SIGS)
 
@@ -320,3 +326,23 @@ def tm_trace_read(name="dslash.*"):
     nb = ctypes.c_double()
     _check(_lib.tm_trace_read(name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nb)))
     return n.value, ms.value, nb.value
+
+
+def tm_tune_enable(on):
+    _lib.tm_tune_enable(int(bool(on)))
+
+
+def tm_tune_reset():
+    _lib.tm_tune_reset()
+
+
+def tm_tune_entries():
+    """The autotuner's choices: list of (key dict, systems per thread, block size)."""
+    out = []
+    names = ("prec", "link_reals", "dagger", "epilogue", "parity", "centre", "out_inv", "half_volume", "nrhs")
+    for i in range(_lib.tm_tune_count()):
+        key = (_i * 9)()
+        nr, bx = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.tm_tune_get(i, key, ctypes.byref(nr), ctypes.byref(bx)))
+        out.append((dict(zip(names, list(key))), nr.value, bx.value))
+    return out
