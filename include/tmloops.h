@@ -124,6 +124,11 @@ tm_status_t tm_gamma5(const tm_geom_t *g, void *out, const void *in, tm_prec_t p
  * out and in must not overlap.                                             */
 tm_status_t tm_dslash(tm_op_t *op, void *out, const void *in, int nrhs, int dagger,
                       int mu_zero, tm_prec_t prec, tm_stream_t s);
+/* out = gamma_5 M in (or gamma_5 M^dag in, gamma_5 D_W in) in one pass: the
+ * right field R = gamma_5 D_W s of the generalised one-end trick (Eq. 6),
+ * without the separate gamma_5 pass.  Arguments as for tm_dslash.          */
+tm_status_t tm_dslash_g5(tm_op_t *op, void *out, const void *in, int nrhs, int dagger,
+                         int mu_zero, tm_prec_t prec, tm_stream_t s);
 
 /* Z4 noise (Sec. 2, Eqs. 1-2): eta_r(x)_{alpha c} = i^k with k = bits
  * [2(3 alpha + c), 2(3 alpha + c) + 1] of word 0 of Philox4x32-10 applied to

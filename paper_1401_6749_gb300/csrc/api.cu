@@ -351,3 +351,19 @@ extern "C" tm_status_t tm_dslash(tm_op_t* op, void* out, const void* in, int nrh
   c.epi = EPI_OUT;
   return dslash_dispatch(op, prec, c, (cudaStream_t)s);
 }
+
+extern "C" tm_status_t tm_dslash_g5(tm_op_t* op, void* out, const void* in, int nrhs, int dagger,
+                                    int mu_zero, tm_prec_t prec, tm_stream_t s) {
+  if (!op || !out || !in || nrhs < 0) { set_error("tm_dslash_g5: null argument"); return TM_ERR_ARG; }
+  if (out == in) { set_error("tm_dslash_g5: out and in must not overlap"); return TM_ERR_ARG; }
+  if (nrhs == 0) return TM_OK;
+  DslashCall c;
+  c.in = in;
+  c.out = out;
+  c.nrhs = nrhs;
+  c.dagger = dagger != 0;
+  c.mu_zero = mu_zero != 0;
+  c.g5_out = true;
+  c.epi = EPI_OUT;
+  return dslash_dispatch(op, prec, c, (cudaStream_t)s);
+}

@@ -85,6 +85,12 @@ __device__ __forceinline__ void project(Cx<R> (&h0)[3], Cx<R> (&h1)[3], const Cx
 // first, with 12 conversions fewer per hop.
 template <class S> struct Mixed;
 template <> struct Mixed<__half> {
+  // a b + c with a, b 16-bit: the product is exact in FP32, one rounding
+  static __device__ __forceinline__ float fma(unsigned short a, unsigned short b, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+  }
   static __device__ __forceinline__ float add(unsigned short a, float c) {
     float d;
     asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
@@ -97,6 +103,11 @@ template <> struct Mixed<__half> {
   }
 };
 template <> struct Mixed<__nv_bfloat16> {
+  static __device__ __forceinline__ float fma(unsigned short a, unsigned short b, float c) {
+    float d;
+    asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+  }
   static __device__ __forceinline__ float add(unsigned short a, float c) {
     float d;
     asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
@@ -374,6 +385,10 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
         }
       }
       if constexpr (EPI == EPI_OUT) {
+        if (a.c.g5_out) {  // gamma_5 = diag(1, 1, -1, -1)
+#pragma unroll
+          for (int k = 6; k < 12; ++k) out[k] = {-out[k].re, -out[k].im};
+        }
         store_spinor<S>(a.c.out, b0, cs, out);
         if (a.c.partial) part[j] = (double)norm2_12(out);
       } else if constexpr (EPI == EPI_CGUPD) {

@@ -157,29 +157,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// dt > 0: time dilution, noise only on slices t = t0 (mod dt), zero elsewhere
+// dt > 0: time dilution, noise only on slices t = t0 (mod dt), zero elsewhere.
+// One thread per (site, source): blockIdx.x covers the sites of both parities
+// (parity = blockIdx.x & 1), blockIdx.y the source.  The entries i^k are
+// built in the storage's own arithmetic (exact in every format), so no FP64
+// conversion runs per entry.
 template <class S>
-__global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int nsrc, int t0, int dt) {
-  const long V = 2L * g.Vh;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V * nsrc) return;
-  const int j = (int)(i / V);
-  const int lex = (int)(i % V);
-  const int x = lex % g.L[0], y = (lex / g.stride[1]) % g.L[1];
-  const int z = (lex / g.stride[2]) % g.L[2], t = lex / g.stride[3];
+__global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int t0, int dt) {
+  using R = typename Prec<S>::R;
+  const int par = blockIdx.x & 1;
+  const int cb = (int)(blockIdx.x >> 1) * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  const int j = blockIdx.y;
+  const Site st = site_of(g, par, cb);
+  const int t = st.c[3];
   const bool on = dt <= 0 || ((t - t0) % dt + dt) % dt == 0;
-  const uint4 w = on ? philox4x32_10(make_uint4((uint32_t)lex, first + (uint32_t)j, 0u, 0u), key)
+  const uint4 w = on ? philox4x32_10(make_uint4((uint32_t)st.lex, first + (uint32_t)j, 0u, 0u), key)
                      : make_uint4(0u, 0u, 0u, 0u);
-  Cx<double> v[12];
+  const R one = (R)1, zero = (R)0;
+  Cx<R> v[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int q = (int)((w.x >> (2 * k)) & 3u);  // component k = 3*alpha + colour
-    v[k] = !on ? Cx<double>{0, 0}
-         : q == 0 ? Cx<double>{1, 0} : q == 1 ? Cx<double>{0, 1} : q == 2 ? Cx<double>{-1, 0}
-                                                                          : Cx<double>{0, -1};
+    v[k] = !on ? Cx<R>{zero, zero}
+         : q == 0 ? Cx<R>{one, zero} : q == 1 ? Cx<R>{zero, one} : q == 2 ? Cx<R>{-one, zero}
+                                                                       : Cx<R>{zero, -one};
   }
-  const int par = (x + y + z + t) & 1;
-  store_spinor_f64<S>(eta, SpinorRef<S>::base(g, j, par, lex >> 1), (size_t)g.Vh, v);
+  store_spinor<S>(eta, SpinorRef<S>::base(g, j, par, cb), (size_t)g.Vh, v);
 }
 
 // ------------------------------------------------------------ gauge packing
@@ -534,13 +538,21 @@ static tm_status_t z4_launch(const tm_geom_t* gg, void* eta, tm_prec_t prec, uin
   if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
   if (nsrc == 0) return TM_OK;
   const Geom g = make_geom(gg->L, 1);
-  const unsigned nb = blocks_for(2L * g.Vh * nsrc, 256);
+  const unsigned nbx = 2 * blocks_for((long)g.Vh, 256);
   const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  const size_t per_src = tm_spinor_bytes(gg, prec, 1);
   TraceScope tr((cudaStream_t)s, "z4_noise", 24.0 * prec_size(prec) * 2.0 * g.Vh, 0.0, nsrc);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    z4_kernel<S><<<nb, 256, 0, (cudaStream_t)s>>>(g, eta, key, first_src, nsrc, t0, dt);
-    count_launch();
-    return check_launch("z4_noise");
+    // at most 65535 sources per launch (grid y)
+    for (int j0 = 0; j0 < nsrc; j0 += 65535) {
+      const int n = nsrc - j0 < 65535 ? nsrc - j0 : 65535;
+      z4_kernel<S><<<dim3(nbx, n), 256, 0, (cudaStream_t)s>>>(g, (char*)eta + per_src * (size_t)j0, key,
+                                                              first_src + (uint32_t)j0, t0, dt);
+      count_launch();
+      const tm_status_t st = check_launch("z4_noise");
+      if (st != TM_OK) return st;
+    }
+    return TM_OK;
   });
 }

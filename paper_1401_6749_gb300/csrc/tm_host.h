@@ -63,6 +63,7 @@ struct DslashCall {
   int centre = 2;
   const void* cfield = nullptr;
   bool out_inv = false;
+  bool g5_out = false;  // EPI_OUT: store gamma_5 times the result
   int parity = -1;  // output parity (0 even, 1 odd) or -1 for both
   int epi = EPI_OUT;
   double* partial = nullptr;

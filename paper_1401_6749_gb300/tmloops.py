@@ -69,6 +69,7 @@ _SIGS = {
     "tm_spinor_convert": [_P(tm_geom_t), _vp, _i, _vp, _i, _i, _vp],
     "tm_gamma5": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
     "tm_dslash": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
+    "tm_dslash_g5": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
     "z4_noise": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _vp],
     "tm_cg_solve": [_vp, _vp, _vp, _i, _P(tm_cg_params_t), _P(tm_cg_stats_t), _vp],
     "tm_cg_solve_group": [_i, _P(_vp), _P(_vp), _P(_vp), _P(_i), _P(tm_cg_params_t), _P(_P(tm_cg_stats_t)),
@@ -207,6 +208,12 @@ def tm_gamma5(L, out, inp, prec, nrhs, stream=None):
 def tm_dslash(op, out, inp, nrhs, dagger=False, mu_zero=False, prec=F32, stream=None):
     _check(_lib.tm_dslash(op.handle, _ptr(out), _ptr(inp), int(nrhs), int(bool(dagger)),
                           int(bool(mu_zero)), int(prec), _stream(stream)))
+
+
+def tm_dslash_g5(op, out, inp, nrhs, dagger=False, mu_zero=False, prec=F32, stream=None):
+    """out = gamma_5 (M, M^dag or D_W) inp in one pass."""
+    _check(_lib.tm_dslash_g5(op.handle, _ptr(out), _ptr(inp), int(nrhs), int(bool(dagger)),
+                             int(bool(mu_zero)), int(prec), _stream(stream)))
 
 
 def z4_noise(L, eta, prec, seed, first_src, nsrc, stream=None):

@@ -63,15 +63,15 @@ class TsmPipeline:
         self.hp_loops = {k: torch.empty((max(self.n_hp, 1), self.len[k.split("_")[0]] * 2),
                                         dtype=torch.float64, device=dev) for k in self.kinds}
         b = min(self.batch, n_all)
-        self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(4)]  # eta, x, D_W x, g5 D_W x
+        self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(3)]  # eta, x, g5 D_W x
         nh = max(min(self.batch, self.n_hp), 1)
-        # eta, x, D_W x, g5 D_W x (the last two in hp_loop_prec, same byte size), and the
-        # copies of eta and x in hp_loop_prec when that is not F64
-        nf = 4 if hp_loop_prec == tl.F64 else 6
+        # eta, x, g5 D_W x (the last in hp_loop_prec, same byte size), and the copies of
+        # eta and x in hp_loop_prec when that is not F64
+        nf = 3 if hp_loop_prec == tl.F64 else 5
         self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(nf)] if self.n_hp else None
         self.stats_lp, self.stats_hp = [], []
 
-    def _contract(self, op, x, w, g5w, prec, n, dst, row0, stream, eta=None):
+    def _contract(self, op, x, g5w, prec, n, dst, row0, stream, eta=None):
         for k in self.kinds:
             kind, mode = k.split("_")
             left, right = {"vv": (x, x), "gen": (x, g5w), "std": (eta, x)}[mode]
@@ -83,20 +83,19 @@ class TsmPipeline:
 
     def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None,
                             loop_prec=None):
-        eta, x, w, g5w = fields[:4]
+        eta, x, g5w = fields[:3]
         tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
         st, stats = tl.tm_cg_solve(op, x, eta, n, params, stream, raise_on_noconv=False)
         if loop_prec is not None and loop_prec != prec:
             # one conversion of the solution (and source) to the loop precision
-            eta_l, x_l = fields[4], fields[5]
+            eta_l, x_l = fields[3], fields[4]
             tl.tm_spinor_convert(self.L, x_l, loop_prec, x, prec, n, stream)
             if any(k.endswith("std") for k in self.kinds):
                 tl.tm_spinor_convert(self.L, eta_l, loop_prec, eta, prec, n, stream)
             eta, x, prec = eta_l, x_l, loop_prec
         if any("gen" in k for k in self.kinds):
-            tl.tm_dslash(op, w, x, n, mu_zero=True, prec=prec, stream=stream)
-            tl.tm_gamma5(self.L, g5w, w, prec, n, stream)
-        self._contract(op, x, w, g5w, prec, n, dst, row0, stream, eta)
+            tl.tm_dslash_g5(op, g5w, x, n, mu_zero=True, prec=prec, stream=stream)   # g5 D_W s
+        self._contract(op, x, g5w, prec, n, dst, row0, stream, eta)
         return stats
 
     def _run_hp(self, stream):

@@ -136,3 +136,20 @@ def test_per_precision_link_format(prec, same_as):
     assert tl.link_reals(0, prec) == same_as
     op0.close()
     opx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 4])
+@pytest.mark.parametrize("dagger,mu_zero", [(False, True), (True, False)])
+def test_dslash_g5_is_gamma5_of_dslash(prec, dagger, mu_zero):
+    """tm_dslash_g5 stores gamma_5 of the Dslash result (a sign flip of the
+    lower spins: exact in every format)."""
+    tl = require_gpu()
+    L = (6, 4, 4, 8)
+    op = tl.Operator(L, 0.16, 0.02, to_dev(synth.gauge_field(L, seed=23)), recon=0)
+    fin = pack(tl, L, synth.random_spinor(L, 2, seed=24), prec)
+    a, b = tl.empty_field(L, prec, 2), tl.empty_field(L, prec, 2)
+    tl.tm_dslash(op, a, fin, 2, dagger=dagger, mu_zero=mu_zero, prec=prec)
+    tl.tm_gamma5(L, a, a, prec, 2)
+    tl.tm_dslash_g5(op, b, fin, 2, dagger=dagger, mu_zero=mu_zero, prec=prec)
+    assert bool((a == b).all())
+    op.close()

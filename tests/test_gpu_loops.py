@@ -130,3 +130,30 @@ def test_pipeline_4x4_plain_fp64():
         got = _loops_gpu(tl, op, L, lf, rf, 0, n, mode, "oneD")
         assert rel_l2(got, oloops.oneD_loops(U, lo, ro, mode)) < 1e-8
     op.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("prec,recon", [(2, 18), (2, 12), (3, 18)])
+def test_contractions_16bit_match_oracle(mode, prec, recon):
+    """FP16/BF16 fields (FP32 arithmetic; with 18-real links the link
+    products multiply the 16-bit values in memory with the exact mixed FMA).
+    FP16 with 18-real links: the oracle takes the links rounded to FP16, so
+    only FP32 rounding separates the results (1e-5).  Otherwise the link
+    rounding (2^-11, 2^-8) bounds the difference."""
+    tl = require_gpu()
+    L = (6, 4, 4, 8)
+    U = synth.gauge_field(L, seed=30)
+    op = tl.Operator(L, 0.16, 0.01, to_dev(U), recon=recon)
+    n = 2
+    fa = pack(tl, L, synth.random_spinor(L, n, seed=31), prec)
+    fb = pack(tl, L, synth.random_spinor(L, n, seed=32), prec)
+    A, B = unpack(tl, L, fa, prec, n), unpack(tl, L, fb, prec, n)
+    got = _loops_gpu(tl, op, L, fa, fb, prec, n, mode, "local")
+    assert rel_l2(got, oloops.local_loops(A, B, mode)) < 1e-5
+    got = _loops_gpu(tl, op, L, fa, fb, prec, n, mode, "oneD")
+    if prec == 2 and recon == 18:
+        U16 = U.real.astype(np.float16).astype(np.float64) + 1j * U.imag.astype(np.float16).astype(np.float64)
+        assert rel_l2(got, oloops.oneD_loops(U16, A, B, mode)) < 1e-5
+    else:
+        assert rel_l2(got, oloops.oneD_loops(U, A, B, mode)) < (5e-3 if prec == 2 else 3e-2)
+    op.close()
