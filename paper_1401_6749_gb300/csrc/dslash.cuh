@@ -225,6 +225,85 @@ __device__ __forceinline__ void hop_site(Cx<typename Prec<S>::R> (&acc)[12], con
   hop_acc<MU, SGN, ADJ>(acc, h0, h1, U, bsign);
 }
 
+// Link product of a projected 2-spinor: w = W (h0, h1), W = U (ADJ = false) or
+// U^dag; with START = false it accumulates onto w (w += W h).  w[0..2] is the
+// product of h0, w[3..5] that of h1.
+template <bool ADJ, bool START, class R>
+__device__ __forceinline__ void link_mv2(Cx<R> (&w)[6], const Mat3<R>& U, const Cx<R> (&h0)[3],
+                                         const Cx<R> (&h1)[3]) {
+  using O = Ar<R>;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R r0, i0, r1, i1;
+    if (!START) { r0 = w[a].re; i0 = w[a].im; r1 = w[3 + a].re; i1 = w[3 + a].im; }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const Cx<R> u = ADJ ? conjx(U.m[b][a]) : U.m[a][b];
+      if (START && b == 0) {
+        r0 = O::mul(u.re, h0[b].re); i0 = O::mul(u.re, h0[b].im);
+        r1 = O::mul(u.re, h1[b].re); i1 = O::mul(u.re, h1[b].im);
+      } else {
+        r0 = O::fma(u.re, h0[b].re, r0); i0 = O::fma(u.re, h0[b].im, i0);
+        r1 = O::fma(u.re, h1[b].re, r1); i1 = O::fma(u.re, h1[b].im, i1);
+      }
+      r0 = O::fma(-u.im, h0[b].im, r0); i0 = O::fma(u.im, h0[b].re, i0);
+      r1 = O::fma(-u.im, h1[b].im, r1); i1 = O::fma(u.im, h1[b].re, i1);
+    }
+    w[a] = {r0, i0};
+    w[3 + a] = {r1, i1};
+  }
+}
+
+// Load the site at b0 and project it: (h0, h1) = rows 0, 1 of (1 + SGN g_MU) psi,
+// negated when neg (the antiperiodic sign of a hop across the time boundary).
+template <class S, int MU, int SGN>
+__device__ __forceinline__ void load_project(Cx<typename Prec<S>::R> (&h0)[3], Cx<typename Prec<S>::R> (&h1)[3],
+                                             const void* field, size_t b0, size_t cs, bool neg) {
+  using R = typename Prec<S>::R;
+  if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+    const uint4* f = reinterpret_cast<const uint4*>(field);
+    uint4 q[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) q[j] = f[b0 + j * cs];
+    project_raw<MU, SGN, S>(h0, h1, q);
+  } else {
+    Cx<R> psi[12];
+    load_spinor<S>(psi, field, b0, cs);
+    project<MU, SGN>(h0, h1, psi);
+  }
+  if (MU == 3 && neg) {  // warp-uniform: only on the first and last time slice
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = {-h0[c].re, -h0[c].im};
+      h1[c] = {-h1[c].re, -h1[c].im};
+    }
+  }
+}
+
+// Both hops of direction MU together: with w_f the forward and w_b the backward
+// link product (projection signs SF and SB = -SF), the upper spins receive
+// w_f + w_b and the lower ones SF B_mu (w_f - w_b).  sum = w_f + w_b is
+// accumulated onto w_f; w_f - w_b = 2 w_f - sum.
+template <int MU, int SF, class R>
+__device__ __forceinline__ void combine_dir(Cx<R> (&acc)[12], const Cx<R> (&wf)[6], const Cx<R> (&sum)[6]) {
+  using G = GBlock<MU>;
+  using O = Ar<R>;
+  constexpr int s2 = SF > 0 ? 0 : 2;
+  const R two = (R)2;
+  Cx<R> d[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) d[k] = {O::fma(two, wf[k].re, -sum[k].re), O::fma(two, wf[k].im, -sum[k].im)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = add_ph<0>(acc[c], sum[c]);
+    acc[3 + c] = add_ph<0>(acc[3 + c], sum[3 + c]);
+    const Cx<R> db0 = G::bc0 == 0 ? d[c] : d[3 + c];
+    const Cx<R> db1 = G::bc1 == 0 ? d[c] : d[3 + c];
+    acc[6 + c] = add_ph<G::bk0 + s2>(acc[6 + c], db0);
+    acc[9 + c] = add_ph<G::bk1 + s2>(acc[9 + c], db1);
+  }
+}
+
 struct DslashArgs {
   Geom g;
   const void* links;
@@ -258,23 +337,28 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Minimum resident blocks per SM requested from the compiler (caps the
 // registers per thread).  The narrow formats are latency/issue bound and gain
-// from occupancy: measured at 32^3 x 64, 16 systems, 7 blocks (72 registers)
-// is fastest for FP16/BF16 (8 blocks = 64 registers spills), 6 for FP32;
-// FP64 is arithmetic bound and keeps its registers.  TM_DSLASH_MINBLOCKS
-// overrides at build time.
-template <class S>
+// from occupancy: measured at 32^3 x 64, 16 systems, one system per thread, 7
+// blocks (72 registers) is fastest for FP16/BF16 (8 blocks = 64 registers
+// spills), 6 for FP32.  Several systems per thread need registers in
+// proportion (4 blocks for 2, 2 for 4), so that the autotuner compares them
+// without forced spills.  FP64 and float-float are arithmetic bound and keep
+// their registers.  TM_DSLASH_MINBLOCKS overrides the one-system value at
+// build time.
+template <class S, int NR = 1>
 constexpr int dslash_min_blocks() {
+  if constexpr (std::is_same<S, double>::value) return 1;
+  else if constexpr (std::is_same<S, FFloat>::value) return 2;
+  else if constexpr (NR >= 4) return 2;
+  else if constexpr (NR == 2) return 4;
 #ifdef TM_DSLASH_MINBLOCKS
-  return TM_DSLASH_MINBLOCKS;
+  else return TM_DSLASH_MINBLOCKS;
 #else
-  return std::is_same<S, double>::value ? 1
-       : std::is_same<S, FFloat>::value ? 2
-       : (std::is_same<S, float>::value ? 6 : 7);
+  else return std::is_same<S, float>::value ? 6 : 7;
 #endif
 }
 
 template <class S, int RECON, bool DAG, int EPI, int NR>
-__global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(const DslashArgs a) {
+__global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kernel(const DslashArgs a) {
   using R = typename Prec<S>::R;
   using O = Ar<R>;
   const Geom& g = a.g;
@@ -315,29 +399,66 @@ __global__ void __launch_bounds__(128, dslash_min_blocks<S>()) dslash_kernel(con
     // forward hops use (1 - g) for M and (1 + g) for M^dag; backward the opposite
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
+// FP32/FP64/float-float: both hops of a direction combined (combine_dir), the
+// time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time
+// with the sign multiplied in, which holds fewer registers and keeps the code
+// straight-line in this register-capped, issue-bound kernel (measured faster).
+// FP32/FP64/float-float: both hops of a direction combined (combine_dir), the
+// time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time
+// (hop_site), which holds fewer registers and spills less in this
+// register-capped, issue-bound kernel (measured faster).
 #define TM_HOPS(MU)                                                                              \
     {                                                                                            \
       const int lf = lex_fwd(g, s, MU);                                                          \
       const int lb = lex_bwd(g, s, MU);                                                          \
-      R sf = 1, sbk = 1;                                                                         \
-      if (MU == 3 && g.antiperiodic) {                                                           \
-        if (s.c[3] == g.L[3] - 1) sf = -1;                                                       \
-        if (s.c[3] == 0) sbk = -1;                                                               \
-      }                                                                                          \
-      {                                                                                          \
-        const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                         \
-        _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
-          if (!act[j]) continue;                                                                 \
-          hop_site<S, MU, SF, false>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), \
-                                     cs, Uf, sf);                                                \
+      if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {   \
+        R sf = 1, sbk = 1;                                                                       \
+        if (MU == 3 && g.antiperiodic) {                                                         \
+          if (s.c[3] == g.L[3] - 1) sf = -1;                                                     \
+          if (s.c[3] == 0) sbk = -1;                                                             \
         }                                                                                        \
-      }                                                                                          \
-      {                                                                                          \
-        const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);                   \
-        _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                         \
-          if (!act[j]) continue;                                                                 \
-          hop_site<S, MU, SB, true>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), \
-                                    cs, Ub, sbk);                                                \
+        {                                                                                        \
+          const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                       \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            hop_site<S, MU, SF, false>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), \
+                                       cs, Uf, sf);                                              \
+          }                                                                                      \
+        }                                                                                        \
+        {                                                                                        \
+          const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);                 \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            hop_site<S, MU, SB, true>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), \
+                                      cs, Ub, sbk);                                              \
+          }                                                                                      \
+        }                                                                                        \
+      } else {                                                                                   \
+        const bool negf = MU == 3 && g.antiperiodic && s.c[3] == g.L[3] - 1;                     \
+        const bool negb = MU == 3 && g.antiperiodic && s.c[3] == 0;                              \
+        Cx<R> wf[NR][6];                                                                         \
+        {                                                                                        \
+          const Mat3<R> Uf = load_link<S, RECON>(a.links, g, MU, par, cb);                       \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            Cx<R> h0[3], h1[3];                                                                  \
+            load_project<S, MU, SF>(h0, h1, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), \
+                                    cs, negf);                                                   \
+            link_mv2<false, true>(wf[j], Uf, h0, h1);                                            \
+          }                                                                                      \
+        }                                                                                        \
+        {                                                                                        \
+          const Mat3<R> Ub = load_link<S, RECON>(a.links, g, MU, opar, lb >> 1);                 \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            Cx<R> h0[3], h1[3];                                                                  \
+            load_project<S, MU, SB>(h0, h1, a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), \
+                                    cs, negb);                                                   \
+            Cx<R> sum[6];                                                                        \
+            _Pragma("unroll") for (int k = 0; k < 6; ++k) sum[k] = wf[j][k];                     \
+            link_mv2<true, false>(sum, Ub, h0, h1);                                              \
+            combine_dir<MU, SF>(acc[j], wf[j], sum);                                             \
+          }                                                                                      \
         }                                                                                        \
       }                                                                                          \
     }
