@@ -163,17 +163,18 @@ def _traffic_per_launch(alg_bytes):
 
 def _tuned_shapes(tl, L):
     """The autotuner's launch shapes for this lattice's half volume:
-    "<prec>.<out|resid>.<parity>.<n systems>" -> "<systems per thread>x<threads per block>"."""
+    "<prec>.<out|resid>.<parity>.<n systems>" -> "<systems per thread>[p]x<threads per block>"
+    (p: packed FP32x2 arithmetic)."""
     vh = L[0] * L[1] * L[2] * L[3] // 2
     pn = {0: "f64", 1: "f32", 2: "f16", 3: "bf16", 4: "ff"}
     out = {}
-    for key, nr, bx in tl.tm_tune_entries():
+    for key, nr, bx, pk in tl.tm_tune_entries():
         if key["half_volume"] != vh:
             continue
         name = "%s%s.%s.%s.n%d" % (pn[key["prec"]], ".dag" if key["dagger"] else "",
                                    "resid" if key["epilogue"] == 2 else "out",
                                    {-1: "both", 0: "even", 1: "odd"}[key["parity"]], key["nrhs"])
-        out[name] = "%dx%d" % (nr, bx)
+        out[name] = "%d%sx%d" % (nr, "p" if pk else "", bx)
     return out
 
 

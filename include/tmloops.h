@@ -309,8 +309,8 @@ void tm_trace_reset(void);
 tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms, double *total_bytes);
 
 /* Autotuning of the FP32/FP16/BF16 Dslash launch shape (this library's own;
- * the paper has no counterpart): systems per thread (1, 2, 4) and threads
- * per block (32, 64, 128).  The first launch of each kind - precision, link
+ * the paper has no counterpart): systems per thread (1, 2, 4; for FP16/BF16
+ * also 2 in packed FP32x2 arithmetic) and threads per block (32, 64, 128).  The first launch of each kind - precision, link
  * format, dagger, epilogue, parity set, centre and inverse-twist terms, half
  * volume and number of systems - times every shape on its own arguments
  * (blocking the calling thread once) and the fastest is kept for the process;
@@ -320,13 +320,13 @@ tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms, dou
  * TM_DSLASH_NR fixes the systems per thread.
  * tm_tune_enable(0/1) switches it at run time, tm_tune_reset forgets every
  * choice, tm_tune_count gives the number of kinds tuned, and tm_tune_get(i,
- * key[9], &nr, &block) reads entry i: key = {prec, reals per link, dagger,
- * epilogue, parity (-1 both), centre (0 none, 1 copy, 2 twisted), inverse
- * twist, half volume, systems}.                                           */
+ * key[9], &nr, &block, &packed) reads entry i: key = {prec, reals per link,
+ * dagger, epilogue, parity (-1 both), centre (0 none, 1 copy, 2 twisted),
+ * inverse twist, half volume, systems}; packed = 1 for the FP32x2 form.    */
 void tm_tune_enable(int on);
 void tm_tune_reset(void);
 int tm_tune_count(void);
-tm_status_t tm_tune_get(int i, int *key, int *nr, int *block);
+tm_status_t tm_tune_get(int i, int *key, int *nr, int *block, int *packed);
 
 #ifdef __cplusplus
 }

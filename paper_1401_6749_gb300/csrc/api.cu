@@ -109,12 +109,16 @@ void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, dou
   g_trace.push_back({name, ev0, ev1, sl, bytes_per_rhs, fixed_bytes, nrhs_if_uncounted});
 }
 
-// Systems per thread of the FP32/FP16/BF16 Dslash: TM_DSLASH_NR = 1, 2 or 4
-// overrides the built-in choice (a tuning knob; results do not depend on it).
+// Systems per thread of the FP32/FP16/BF16 Dslash (a tuning knob; results do
+// not depend on it): TM_DSLASH_NR = 1, 2, 4 fixes them, "2p" two systems in
+// packed FP32x2 arithmetic (returned as -2); unset leaves the choice to the
+// autotuner.
 int dslash_nr_override() {
   static const int v = [] {
     const char* e = getenv("TM_DSLASH_NR");
-    const int n = e ? atoi(e) : 0;
+    if (!e) return 0;
+    if (strcmp(e, "2p") == 0) return -2;
+    const int n = atoi(e);
     return (n == 1 || n == 2 || n == 4) ? n : 0;
   }();
   return v;
@@ -197,8 +201,8 @@ extern "C" int tm_tune_count(void) {
   return (int)g_tune.size();
 }
 
-extern "C" tm_status_t tm_tune_get(int i, int* key, int* nr, int* block) {
-  if (!key || !nr || !block) { set_error("tm_tune_get: null argument"); return TM_ERR_ARG; }
+extern "C" tm_status_t tm_tune_get(int i, int* key, int* nr, int* block, int* packed) {
+  if (!key || !nr || !block || !packed) { set_error("tm_tune_get: null argument"); return TM_ERR_ARG; }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (i < 0 || i >= (int)g_tune.size()) { set_error("tm_tune_get: index %d out of range", i); return TM_ERR_ARG; }
   auto it = g_tune.begin();
@@ -208,6 +212,7 @@ extern "C" tm_status_t tm_tune_get(int i, int* key, int* nr, int* block) {
   for (int j = 0; j < 9; ++j) key[j] = v[j];
   *nr = it->second.nr;
   *block = it->second.bx;
+  *packed = it->second.packed;
   return TM_OK;
 }
 

@@ -236,7 +236,7 @@ __device__ __forceinline__ void link_times2(Cx<R> (&w)[6], const Mat3<R>& U, con
         zi = O::fma(u.re, x.im, zi);
         zi = O::fma(u.im, x.re, zi);
       }
-      w[3 * a + c] = {zr, zi};
+      w[3 * a + c] = {O::norm(zr), O::norm(zi)};
     }
 }
 
@@ -462,6 +462,11 @@ __global__ void __launch_bounds__(256, oned_min_blocks<S>()) oneD_partial_kernel
         outer_acc2<S>(acc, Lf, bf, cs, w, -sf);
       }
     }
+  }
+  {
+    using O = Ar<R>;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = O::norm(acc[j]);
   }
   const R v = warp_transpose_reduce16(acc);
   const int lane = threadIdx.x & 31;

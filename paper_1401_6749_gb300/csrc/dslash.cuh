@@ -37,19 +37,24 @@ template <> struct GBlock<3> { static constexpr int ac0 = 0, ak0 = 0, ac1 = 1, a
 
 // explicit round-to-nearest arithmetic
 template <class R> struct Ar;
+// norm: renormalise a float-float value at the end of a multiply-add chain
+// (identity for the IEEE types)
 template <> struct Ar<float> {
+  static __device__ __forceinline__ float norm(float a) { return a; }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 template <> struct Ar<FF> {
+  static __device__ __forceinline__ FF norm(FF a) { return ff_norm(a); }
   static __device__ __forceinline__ FF add(FF a, FF b) { return a + b; }
   static __device__ __forceinline__ FF sub(FF a, FF b) { return a - b; }
   static __device__ __forceinline__ FF mul(FF a, FF b) { return a * b; }
   static __device__ __forceinline__ FF fma(FF a, FF b, FF c) { return ff_fma(a, b, c); }
 };
 template <> struct Ar<double> {
+  static __device__ __forceinline__ double norm(double a) { return a; }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -249,8 +254,8 @@ __device__ __forceinline__ void link_mv2(Cx<R> (&w)[6], const Mat3<R>& U, const 
       r0 = O::fma(-u.im, h0[b].im, r0); i0 = O::fma(u.im, h0[b].re, i0);
       r1 = O::fma(-u.im, h1[b].im, r1); i1 = O::fma(u.im, h1[b].re, i1);
     }
-    w[a] = {r0, i0};
-    w[3 + a] = {r1, i1};
+    w[a] = {O::norm(r0), O::norm(i0)};
+    w[3 + a] = {O::norm(r1), O::norm(i1)};
   }
 }
 
@@ -292,7 +297,8 @@ __device__ __forceinline__ void combine_dir(Cx<R> (&acc)[12], const Cx<R> (&wf)[
   const R two = (R)2;
   Cx<R> d[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) d[k] = {O::fma(two, wf[k].re, -sum[k].re), O::fma(two, wf[k].im, -sum[k].im)};
+  for (int k = 0; k < 6; ++k)
+    d[k] = {O::norm(O::fma(two, wf[k].re, -sum[k].re)), O::norm(O::fma(two, wf[k].im, -sum[k].im))};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     acc[c] = add_ph<0>(acc[c], sum[c]);
@@ -497,12 +503,16 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
 #pragma unroll
         for (int k = 0; k < 12; ++k) out[k] = {O::mul(shop, acc[j][k].re), O::mul(shop, acc[j][k].im)};
       }
+      if constexpr (std::is_same<R, FF>::value) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = {O::norm(out[k].re), O::norm(out[k].im)};
+      }
       if (a.c.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const R tw = k < 6 ? nu : -nu;
           const Cx<R> v = out[k];
-          out[k] = {O::mul(inv, O::fma(tw, v.im, v.re)), O::mul(inv, O::fma(-tw, v.re, v.im))};
+          out[k] = {O::mul(inv, O::norm(O::fma(tw, v.im, v.re))), O::mul(inv, O::norm(O::fma(-tw, v.re, v.im)))};
         }
       }
       if constexpr (EPI == EPI_OUT) {
@@ -547,7 +557,14 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
   }
 }
 
-template <class S, int RECON, bool DAG, int EPI, int NR>
+}  // namespace tml
+
+#include "dslash_x2.cuh"
+
+namespace tml {
+
+// X2: two systems per thread in packed FP32x2 arithmetic (FP16/BF16, NR = 2)
+template <class S, int RECON, bool DAG, int EPI, int NR, bool X2 = false>
 tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, int bx = 128) {
   DslashArgs a;
   a.g = op->g;
@@ -592,7 +609,8 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
   const double fixed = 4.0 * 2.0 * op->g.Vh * link_reals * e;
   cudaEvent_t ev = nullptr;
   a.trace_count = trace_begin(st, &ev);
-  dslash_kernel<S, RECON, DAG, EPI, NR><<<grid, bx, 0, st>>>(a);
+  if constexpr (X2) dslash_kernel_x2<S, RECON, DAG, EPI><<<grid, bx, 0, st>>>(a);
+  else dslash_kernel<S, RECON, DAG, EPI, NR><<<grid, bx, 0, st>>>(a);
   count_launch();
   trace_end(st, name, ev, a.trace_count, per_rhs, fixed);
   return check_launch("dslash");
@@ -601,7 +619,8 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
 // ------------------------------------------------------------- autotuning
 // Launch shape of the narrow-format Dslash: systems per thread (NR = 1, 2, 4:
 // the site's index arithmetic, link loads and reconstruction shared by NR
-// systems, against registers and occupancy) and threads per block (32, 64,
+// systems, against registers and occupancy; for FP16/BF16 also 2 systems in
+// packed FP32x2 arithmetic, dslash_kernel_x2) and threads per block (32, 64,
 // 128: small lattices fill more SMs with smaller blocks).  Results do not
 // depend on either (explicit round-to-nearest arithmetic per system, partial
 // sums per warp of 32 sites), so the first launch of each kind times every
@@ -612,8 +631,14 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
 // operator form.  No tuning while a CUDA graph is being captured, nor while
 // TM_DSLASH_NR fixes NR.
 
+template <class S, int RECON>
+constexpr bool kPackable = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+
 template <class S, int RECON, bool DAG, int EPI>
 tm_status_t launch_cfg(const tm_op* op, const DslashCall& c, cudaStream_t st, const TuneCfg& cfg) {
+  if constexpr (kPackable<S, RECON>) {
+    if (cfg.packed && c.nrhs >= 2) return launch_one<S, RECON, DAG, EPI, 2, true>(op, c, st, cfg.bx);
+  }
   if (cfg.nr >= 4 && c.nrhs >= 4) return launch_one<S, RECON, DAG, EPI, 4>(op, c, st, cfg.bx);
   if (cfg.nr >= 2 && c.nrhs >= 2) return launch_one<S, RECON, DAG, EPI, 2>(op, c, st, cfg.bx);
   return launch_one<S, RECON, DAG, EPI, 1>(op, c, st, cfg.bx);
@@ -646,10 +671,11 @@ tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
     // FP64 and float-float: arithmetic-bound and register-heavy, one system per thread
     return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
   } else {
-    TuneCfg cfg{1, 128};  // measured at 32^3 x 64 with 16 systems: NR = 1, 128 threads
+    TuneCfg cfg{1, 128, 0};  // measured at 32^3 x 64 with 16 systems: NR = 1, 128 threads
     const int want = dslash_nr_override();
-    if (want > 0) {
-      cfg.nr = want;
+    if (want != 0) {
+      cfg.nr = want > 0 ? want : 2;
+      cfg.packed = want < 0 ? 1 : 0;
       return launch_cfg<S, RECON, DAG, EPI>(op, c, st, cfg);
     }
     const TuneKey key{(int)Prec<S>::id, RECON, DAG ? 1 : 0, EPI == EPI_CGUPD ? (int)EPI_OUT : EPI,
@@ -659,13 +685,17 @@ tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
     float best = -1.0f;
     TuneCfg pick = cfg;
     tuning_begin();
-    for (int nr : {1, 2, 4}) {
-      if (nr > c.nrhs) continue;
+    // shapes: 1, 2 or 4 systems per thread, or 2 in packed FP32x2 (16-bit only)
+    for (int v = 0; v < 4; ++v) {
+      const int nr = v == 3 ? 2 : (1 << v);
+      const int pk = v == 3 ? 1 : 0;
+      if (nr > c.nrhs || (pk && !kPackable<S, RECON>)) continue;
       for (int bx : {128, 64, 32}) {
-        const float t = time_cfg<S, RECON, DAG, EPI>(op, c, st, TuneCfg{nr, bx});
+        const TuneCfg tc{nr, bx, pk};
+        const float t = time_cfg<S, RECON, DAG, EPI>(op, c, st, tc);
         if (t > 0.0f && (best < 0.0f || t < best)) {
           best = t;
-          pick = TuneCfg{nr, bx};
+          pick = tc;
         }
       }
     }

@@ -104,15 +104,23 @@ __device__ __forceinline__ FF operator*(FF a, FF b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return ff_fast_two_sum(p, e);
 }
-// a b + c with one renormalisation
+// a b + c as one step of a compensated dot product (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005: Dot2): the
+// exact product of the high parts plus its cross terms, the high part of the
+// sum by an exact two-sum, and every error term added into the low part in
+// FP32.  The result is left unnormalised (its low part may exceed half an
+// ulp of the high part), so a chain of these depends on the previous step
+// through one addition per part; ff_norm renormalises at the end of a chain,
+// before the value is used as a factor or stored.
 __device__ __forceinline__ FF ff_fma(FF a, FF b, FF c) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  const FF s = ff_two_sum(p, c.hi);
-  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+  const FF s = ff_two_sum(c.hi, p);
+  return {s.hi, __fadd_rn(c.lo, __fadd_rn(s.lo, e))};
 }
+__device__ __forceinline__ FF ff_norm(FF a) { return ff_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ FF& operator+=(FF& a, FF b) { return a = a + b; }
 __device__ __forceinline__ FF shfl_xor(FF v, int m) {
   return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
@@ -306,8 +314,10 @@ __device__ __forceinline__ void store_spinor(void* field, size_t b0, size_t cs,
       reinterpret_cast<double2*>(f)[b0 + j * cs] = make_double2(v[j].re, v[j].im);
   } else if constexpr (std::is_same<S, FFloat>::value) {
 #pragma unroll
-    for (int j = 0; j < 12; ++j)
-      reinterpret_cast<float4*>(f)[b0 + j * cs] = make_float4(v[j].re.hi, v[j].re.lo, v[j].im.hi, v[j].im.lo);
+    for (int j = 0; j < 12; ++j) {
+      const FF re = ff_norm(v[j].re), im = ff_norm(v[j].im);
+      reinterpret_cast<float4*>(f)[b0 + j * cs] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
   } else if constexpr (std::is_same<S, float>::value) {
 #pragma unroll
     for (int j = 0; j < 6; ++j)

@@ -32,6 +32,7 @@ struct TuneKey {
 };
 struct TuneCfg {
   int nr, bx;
+  int packed;  // 1: two systems per thread in packed FP32x2 arithmetic
 };
 bool tune_lookup(const TuneKey& k, TuneCfg* c);
 void tune_store(const TuneKey& k, const TuneCfg& c);

@@ -90,7 +90,7 @@ _SIGS = {
     "tm_tune_enable": [_i],
     "tm_tune_reset": [],
     "tm_tune_count": [],
-    "tm_tune_get": [_i, _P(_i), _P(_i), _P(_i)],
+    "tm_tune_get": [_i, _P(_i), _P(_i), _P(_i), _P(_i)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -344,12 +344,13 @@ def tm_tune_reset():
 
 
 def tm_tune_entries():
-    """The autotuner's choices: list of (key dict, systems per thread, block size)."""
+    """The autotuner's choices: list of (key dict, systems per thread, block size,
+    packed FP32x2 flag)."""
     out = []
     names = ("prec", "link_reals", "dagger", "epilogue", "parity", "centre", "out_inv", "half_volume", "nrhs")
     for i in range(_lib.tm_tune_count()):
         key = (_i * 9)()
-        nr, bx = ctypes.c_int(), ctypes.c_int()
-        _check(_lib.tm_tune_get(i, key, ctypes.byref(nr), ctypes.byref(bx)))
-        out.append((dict(zip(names, list(key))), nr.value, bx.value))
+        nr, bx, pk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.tm_tune_get(i, key, ctypes.byref(nr), ctypes.byref(bx), ctypes.byref(pk)))
+        out.append((dict(zip(names, list(key))), nr.value, bx.value, pk.value))
     return out

@@ -44,8 +44,9 @@ def test_tuned_shapes_give_identical_results(prec):
     got = _run(tl, op, L, prec)
     entries = tl.tm_tune_entries()
     assert len(entries) > 0
-    for key, nr, bx in entries:
+    for key, nr, bx, pk in entries:
         assert nr in (1, 2, 4) and nr <= key["nrhs"] and bx in (32, 64, 128)
+        assert pk in (0, 1) and (pk == 0 or (nr == 2 and key["prec"] in (2, 3)))
         assert key["epilogue"] in (0, 2)                 # CG updates are never timed
     again = _run(tl, op, L, prec)                        # cached shapes
     for a, b, c in zip(ref, got, again):
