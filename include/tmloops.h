@@ -307,6 +307,10 @@ uint64_t tm_launch_count(void);
 void tm_trace_enable(int on);
 void tm_trace_reset(void);
 tm_status_t tm_trace_read(const char *name, int *launches, double *total_ms, double *total_bytes);
+/* The algorithmic flops of the same launches (recorded by the Dslash: per
+ * output site and active system 1320 for the hops, plus the centre, twist and
+ * epilogue terms; 0 for other classes).                                    */
+tm_status_t tm_trace_read_flops(const char *name, double *total_flops);
 
 /* Autotuning of the FP32/FP16/BF16 Dslash launch shape (this library's own;
  * the paper has no counterpart): systems per thread (1, 2, 4; for FP16/BF16

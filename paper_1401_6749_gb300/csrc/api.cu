@@ -78,6 +78,7 @@ struct TraceRec {
   int slot;        // device counter of active systems, or -1
   double bytes_per_rhs, fixed_bytes;
   int nrhs;        // systems counted as active when slot < 0
+  double flops_per_rhs;
 };
 static std::mutex g_trace_mu;
 static std::atomic<int> g_trace_on{0};
@@ -99,14 +100,14 @@ int* trace_begin(cudaStream_t s, cudaEvent_t* ev0) {
 }
 
 void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
-               double fixed_bytes, int nrhs_if_uncounted) {
+               double fixed_bytes, int nrhs_if_uncounted, double flops_per_rhs) {
   if (!ev0) return;
   cudaEvent_t ev1;
   if (cudaEventCreate(&ev1) != cudaSuccess) { cudaEventDestroy(ev0); return; }
   cudaEventRecord(ev1, s);
   std::lock_guard<std::mutex> lk(g_trace_mu);
   const int sl = slot ? (int)(slot - g_trace_counts) : -1;
-  g_trace.push_back({name, ev0, ev1, sl, bytes_per_rhs, fixed_bytes, nrhs_if_uncounted});
+  g_trace.push_back({name, ev0, ev1, sl, bytes_per_rhs, fixed_bytes, nrhs_if_uncounted, flops_per_rhs});
 }
 
 // Systems per thread of the FP32/FP16/BF16 Dslash (a tuning knob; results do
@@ -239,9 +240,8 @@ extern "C" void tm_trace_reset(void) {
   g_trace_next = 0;
 }
 
-extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* total_ms,
-                                     double* total_bytes) {
-  if (!name || !launches || !total_ms || !total_bytes) { set_error("tm_trace_read: null argument"); return TM_ERR_ARG; }
+static tm_status_t trace_sum(const char* name, int* launches, double* total_ms, double* total_bytes,
+                             double* total_flops) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   std::vector<int> counts((size_t)g_trace_next);
   if (g_trace_next > 0) {
@@ -252,7 +252,7 @@ extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* to
     }
   }
   int n = 0;
-  double ms = 0.0, bytes = 0.0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
   // exact class name, or a prefix followed by '*'
   const std::string want(name);
   const bool prefix = !want.empty() && want.back() == '*';
@@ -265,12 +265,27 @@ extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* to
     ms += t;
     const int act = r.slot < 0 ? r.nrhs : (r.slot < (int)counts.size() ? counts[r.slot] : 0);
     bytes += act > 0 ? act * r.bytes_per_rhs + r.fixed_bytes : 0.0;
+    flops += act * r.flops_per_rhs;
     ++n;
   }
   *launches = n;
   *total_ms = ms;
   *total_bytes = bytes;
+  if (total_flops) *total_flops = flops;
   return TM_OK;
+}
+
+extern "C" tm_status_t tm_trace_read(const char* name, int* launches, double* total_ms,
+                                     double* total_bytes) {
+  if (!name || !launches || !total_ms || !total_bytes) { set_error("tm_trace_read: null argument"); return TM_ERR_ARG; }
+  return trace_sum(name, launches, total_ms, total_bytes, nullptr);
+}
+
+extern "C" tm_status_t tm_trace_read_flops(const char* name, double* total_flops) {
+  if (!name || !total_flops) { set_error("tm_trace_read_flops: null argument"); return TM_ERR_ARG; }
+  int n = 0;
+  double ms = 0.0, bytes = 0.0;
+  return trace_sum(name, &n, &ms, &bytes, total_flops);
 }
 
 extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const double* U_lex,

@@ -170,6 +170,7 @@ constexpr int kOneDK = 8;           // sites per thread
 constexpr int kOneDLanes = 32;      // sites side by side in a block (x 8 warps)
 constexpr int kOneDChunk = kOneDLanes * kOneDK;
 
+
 __device__ __forceinline__ int sel4(const int (&a)[4], int mu) {
   return mu == 0 ? a[0] : mu == 1 ? a[1] : mu == 2 ? a[2] : a[3];
 }
@@ -394,9 +395,11 @@ template <class S, int RECON>
 __global__ void __launch_bounds__(256, oned_min_blocks<S>()) oneD_partial_kernel(
     Geom g, const void* links, const void* Lf, const void* Rf, int nchunk, double* partial) {
   using R = typename Prec<S>::R;
-  const int chunk = blockIdx.x;
-  const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
-  const int rhs = blockIdx.z;
+  // the system index is the fastest block index: the blocks of all systems
+  // for one set of sites run together and share its links through L2
+  const int rhs = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const int t = blockIdx.z >> 1, par = blockIdx.z & 1;
   const int mu = threadIdx.y >> 1, h = threadIdx.y & 1;
   const int opar = par ^ 1;
   const size_t cs = (size_t)g.Vh;
@@ -701,14 +704,14 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   if (!valid_mode(mode)) { set_error("loop_contract_oneD: unknown mode %d", (int)mode); return TM_ERR_ARG; }
   if ((int)prec < 0 || (int)prec >= kNumPrec) { set_error("loop_contract_oneD: unknown precision %d", (int)prec); return TM_ERR_ARG; }
   if (nrhs == 0) return TM_OK;
-  if (nrhs > 65535) { set_error("loop_contract_oneD: nrhs must be <= 65535"); return TM_ERR_ARG; }
   const cudaStream_t s = (cudaStream_t)strm;
   const Geom& g = op->g;
   const int nchunk = (g.V3h + kOneDChunk - 1) / kOneDChunk;
+  if (nchunk > 65535 || 2 * g.L[3] > 65535) { set_error("loop_contract_oneD: lattice too large for the grid"); return TM_ERR_ARG; }
   double* scratch = nullptr;
   tm_status_t st = scratch_alloc((void**)&scratch, sizeof(double) * 128 * (size_t)nrhs * g.L[3] * 2 * nchunk, s);
   if (st != TM_OK) return st;
-  const dim3 grid(nchunk, 2 * g.L[3], nrhs);
+  const dim3 grid(nrhs, nchunk, 2 * g.L[3]);
   const dim3 block(kOneDLanes, 8);
   const bool r12 = op->recon_p[prec] == 12;
   const void* links = op->links[prec];

@@ -612,7 +612,13 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
   if constexpr (X2) dslash_kernel_x2<S, RECON, DAG, EPI><<<grid, bx, 0, st>>>(a);
   else dslash_kernel<S, RECON, DAG, EPI, NR><<<grid, bx, 0, st>>>(a);
   count_launch();
-  trace_end(st, name, ev, a.trace_count, per_rhs, fixed);
+  // algorithmic flops per output site and system: the spin-projected hops
+  // (8 x (12 projection + 132 link product + 24 accumulation) + 24 boundary
+  // sign, counted as 1320 as usual), the hop scale and centre (48), the twist
+  // A (48), A^-1 (72), the epilogue (CG update 144, residual 72, norm 48)
+  const double site_flops = 1320.0 + 48.0 + (a.c.centre == 2 ? 48.0 : 0.0) + (a.c.out_inv ? 72.0 : 0.0) +
+                            (EPI == EPI_CGUPD ? 144.0 : EPI == EPI_RESID ? 72.0 : (a.c.partial ? 48.0 : 0.0));
+  trace_end(st, name, ev, a.trace_count, per_rhs, fixed, 0, out_sites * site_flops);
   return check_launch("dslash");
 }
 

@@ -447,10 +447,11 @@ tm_status_t check_launch(const char* what);
 // Tracing of Dslash launches (tm_trace_enable): trace_begin records a start
 // event and returns a device slot in which the kernel stores how many of its
 // systems were active (nullptr when tracing is off); trace_end records the end
-// event with the launch's algorithmic bytes per active system and per launch.
+// event with the launch's algorithmic bytes per active system and per launch,
+// and its algorithmic flops per active system.
 int* trace_begin(cudaStream_t s, cudaEvent_t* ev0);
 void trace_end(cudaStream_t s, const char* name, cudaEvent_t ev0, int* slot, double bytes_per_rhs,
-               double fixed_bytes, int nrhs_if_uncounted = 0);
+               double fixed_bytes, int nrhs_if_uncounted = 0, double flops_per_rhs = 0.0);
 
 // RAII form for kernels that do not count their active systems: all nrhs
 // systems are taken as active.

@@ -87,6 +87,7 @@ _SIGS = {
     "tm_trace_enable": [_i],
     "tm_trace_reset": [],
     "tm_trace_read": [ctypes.c_char_p, _P(_i), _P(_d), _P(_d)],
+    "tm_trace_read_flops": [ctypes.c_char_p, _P(_d)],
     "tm_tune_enable": [_i],
     "tm_tune_reset": [],
     "tm_tune_count": [],
@@ -333,6 +334,13 @@ def tm_trace_read(name="dslash.*"):
     nb = ctypes.c_double()
     _check(_lib.tm_trace_read(name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(nb)))
     return n.value, ms.value, nb.value
+
+
+def tm_trace_read_flops(name="dslash.*"):
+    """Algorithmic flops of a traced Dslash class (same launches as tm_trace_read)."""
+    f = ctypes.c_double()
+    _check(_lib.tm_trace_read_flops(name.encode(), ctypes.byref(f)))
+    return f.value
 
 
 def tm_tune_enable(on):
