@@ -241,70 +241,6 @@ __device__ __forceinline__ void link_times2(Cx<R> (&w)[6], const Mat3<R>& U, con
     }
 }
 
-// 16-bit storage with 18-real links: every factor of a link product is a
-// 16-bit number in memory, and the mixed-precision FMA (fma.rn.f32.f16|bf16)
-// multiplies two of them exactly and adds in FP32 with one rounding.  The
-// products therefore skip the conversions of the link and of the spinor and
-// give the bits of link_times2 on converted operands: same operations in the
-// same order, with each sign moved onto the spinor factor (exact).
-template <class S, int RECON>
-constexpr bool kRawLinks =
-    (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) && RECON == 18;
-
-// the 9 complex entries of a link (row-major), one 32-bit word each (re low)
-template <class S>
-__device__ __forceinline__ void load_link_raw(unsigned (&u)[9], const void* links, const Geom& g, int mu,
-                                              int par, int cb) {
-  using F = LinkFmt<S, 18>;
-  const uint4* p = reinterpret_cast<const uint4*>(links);
-  const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
-  const size_t cs = (size_t)g.Vh;
-  const uint4 a = p[b0], b = p[b0 + cs];
-  u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
-  u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
-  u[8] = reinterpret_cast<const unsigned*>(p + b0 + 2 * cs)[0];
-}
-
-// components 6h .. 6h + 5 of a 16-bit spinor, one word per complex number
-template <class S>
-__device__ __forceinline__ void load_spins2_raw(unsigned (&x)[6], const void* field, size_t b0, size_t cs,
-                                                int h) {
-  const uint4* f = reinterpret_cast<const uint4*>(field);
-  const uint4 a = f[b0 + h * cs], b = f[b0 + (h + 1) * cs];
-  const unsigned e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-  for (int j = 0; j < 6; ++j) x[j] = h ? e[2 + j] : e[j];
-}
-
-template <bool ADJ, bool SUB, class S>
-__device__ __forceinline__ void link_times2_raw(Cx<float> (&w)[6], const unsigned (&u)[9], const unsigned (&x)[6]) {
-  using M = Mixed<S>;
-  // signs of Re u and Im u in (ADJ ? conj(U) : U), negated for SUB
-  constexpr bool pre = !SUB, pim = ADJ == SUB;
-  unsigned xn[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) xn[j] = x[j] ^ 0x80008000u;  // -x
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float zr = SUB ? w[3 * a + c].re : 0.0f, zi = SUB ? w[3 * a + c].im : 0.0f;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const unsigned uw = ADJ ? u[3 * d + c] : u[3 * c + d];
-        const unsigned short ur = (unsigned short)(uw & 0xffffu), ui = (unsigned short)(uw >> 16);
-        const unsigned xp = x[3 * a + d], xm = xn[3 * a + d];
-        const unsigned short xpr = (unsigned short)(xp & 0xffffu), xpi = (unsigned short)(xp >> 16);
-        const unsigned short xmr = (unsigned short)(xm & 0xffffu), xmi = (unsigned short)(xm >> 16);
-        zr = M::fma(ur, pre ? xpr : xmr, zr);    // Re u Re x
-        zr = M::fma(ui, pim ? xmi : xpi, zr);    // -Im u Im x
-        zi = M::fma(ur, pre ? xpi : xmi, zi);    // Re u Im x
-        zi = M::fma(ui, pim ? xpr : xmr, zi);    // Im u Re x
-      }
-      w[3 * a + c] = {zr, zi};
-    }
-}
-
 // acc_{a, bb} += sgn * sum_c conj(l_{a c}) w_{bb c}, a = 0..3, bb = 0..1; FP64 reads
 // one row of L at a time
 template <class S, class R>

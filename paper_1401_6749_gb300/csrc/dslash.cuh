@@ -165,6 +165,125 @@ __device__ __forceinline__ void project_raw(Cx<float> (&h0)[3], Cx<float> (&h1)[
   }
 }
 
+// 16-bit storage with 18-real links: every factor of a link product is a
+// 16-bit number in memory, and the mixed-precision FMA (fma.rn.f32.f16|bf16)
+// multiplies two of them exactly and adds in FP32 with one rounding.  The
+// products therefore skip the conversions of the link and of the spinor and
+// give the bits of link_times2 on converted operands: same operations in the
+// same order, with each sign moved onto the spinor factor (exact).
+template <class S, int RECON>
+constexpr bool kRawLinks =
+    (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) && RECON == 18;
+
+// the 9 complex entries of a link (row-major), one 32-bit word each (re low)
+template <class S>
+__device__ __forceinline__ void load_link_raw(unsigned (&u)[9], const void* links, const Geom& g, int mu,
+                                              int par, int cb) {
+  using F = LinkFmt<S, 18>;
+  const uint4* p = reinterpret_cast<const uint4*>(links);
+  const size_t b0 = ((size_t)(mu * 2 + par) * F::NU) * (size_t)g.Vh + (size_t)cb;
+  const size_t cs = (size_t)g.Vh;
+  const uint4 a = p[b0], b = p[b0 + cs];
+  u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+  u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+  u[8] = reinterpret_cast<const unsigned*>(p + b0 + 2 * cs)[0];
+}
+
+// components 6h .. 6h + 5 of a 16-bit spinor, one word per complex number
+template <class S>
+__device__ __forceinline__ void load_spins2_raw(unsigned (&x)[6], const void* field, size_t b0, size_t cs,
+                                                int h) {
+  const uint4* f = reinterpret_cast<const uint4*>(field);
+  const uint4 a = f[b0 + h * cs], b = f[b0 + (h + 1) * cs];
+  const unsigned e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int j = 0; j < 6; ++j) x[j] = h ? e[2 + j] : e[j];
+}
+
+template <bool ADJ, bool SUB, class S>
+__device__ __forceinline__ void link_times2_raw(Cx<float> (&w)[6], const unsigned (&u)[9], const unsigned (&x)[6]) {
+  using M = Mixed<S>;
+  // signs of Re u and Im u in (ADJ ? conj(U) : U), negated for SUB
+  constexpr bool pre = !SUB, pim = ADJ == SUB;
+  unsigned xn[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) xn[j] = x[j] ^ 0x80008000u;  // -x
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float zr = SUB ? w[3 * a + c].re : 0.0f, zi = SUB ? w[3 * a + c].im : 0.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const unsigned uw = ADJ ? u[3 * d + c] : u[3 * c + d];
+        const unsigned short ur = (unsigned short)(uw & 0xffffu), ui = (unsigned short)(uw >> 16);
+        const unsigned xp = x[3 * a + d], xm = xn[3 * a + d];
+        const unsigned short xpr = (unsigned short)(xp & 0xffffu), xpi = (unsigned short)(xp >> 16);
+        const unsigned short xmr = (unsigned short)(xm & 0xffffu), xmi = (unsigned short)(xm >> 16);
+        zr = M::fma(ur, pre ? xpr : xmr, zr);    // Re u Re x
+        zr = M::fma(ui, pim ? xmi : xpi, zr);    // -Im u Im x
+        zi = M::fma(ur, pre ? xpi : xmi, zi);    // Re u Im x
+        zi = M::fma(ui, pim ? xpr : xmr, zi);    // Im u Re x
+      }
+      w[3 * a + c] = {zr, zi};
+    }
+}
+
+// Packed 16-bit pairs held as 32-bit words (low half = real part):
+// f16x2 / bf16x2 add with round-to-nearest.
+template <class S>
+__device__ __forceinline__ unsigned hadd2_w(unsigned a, unsigned b) {
+  unsigned d;
+  if constexpr (std::is_same<S, __half>::value) asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  else asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// a + i^K b on 16-bit complex words, rounded once to the storage format: the
+// i^K rotation only swaps halves and flips signs (exact), then one packed add
+template <int K, class S>
+__device__ __forceinline__ unsigned add_ph_w(unsigned a, unsigned b) {
+  constexpr int k = ((K % 4) + 4) % 4;
+  if constexpr (k == 0) return hadd2_w<S>(a, b);
+  else if constexpr (k == 2) return hadd2_w<S>(a, b ^ 0x80008000u);
+  else if constexpr (k == 1) return hadd2_w<S>(a, __byte_perm(b, 0u, 0x1032) ^ 0x00008000u);  // (-b.im, b.re)
+  else return hadd2_w<S>(a, __byte_perm(b, 0u, 0x1032) ^ 0x80000000u);                        // (b.im, -b.re)
+}
+
+// FP16/BF16 with 18-real links: one hop straight from the 16-bit words.  The
+// projection h = psi_up + SGN A_mu psi_dn is one packed add per complex entry
+// (one rounding to the storage format, like storing h), the link product
+// multiplies the 16-bit link and h words exactly with the mixed FMA and
+// accumulates in FP32, and the time-boundary sign flips h's sign bits.  No
+// FP16 -> FP32 conversion at all.
+template <class S, int MU, int SGN, bool ADJ>
+__device__ __forceinline__ void hop_site_w(Cx<float> (&acc)[12], const void* field, size_t b0, size_t cs,
+                                           const unsigned (&u)[9], unsigned negmask) {
+  using G = GBlock<MU>;
+  constexpr int s2 = SGN > 0 ? 0 : 2;
+  const uint4* f = reinterpret_cast<const uint4*>(field);
+  uint4 q[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) q[j] = f[b0 + j * cs];
+  unsigned h[6];  // (h0[0..2], h1[0..2])
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h[c] = add_ph_w<G::ak0 + s2, S>(raw_word(q, c), raw_word(q, 3 * (2 + G::ac0) + c)) ^ negmask;
+    h[3 + c] = add_ph_w<G::ak1 + s2, S>(raw_word(q, 3 + c), raw_word(q, 3 * (2 + G::ac1) + c)) ^ negmask;
+  }
+  Cx<float> w[6];
+  link_times2_raw<ADJ, false, S>(w, u, h);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = add_ph<0>(acc[c], w[c]);
+    acc[3 + c] = add_ph<0>(acc[3 + c], w[3 + c]);
+    const Cx<float> wb0 = G::bc0 == 0 ? w[c] : w[3 + c];
+    const Cx<float> wb1 = G::bc1 == 0 ? w[c] : w[3 + c];
+    acc[6 + c] = add_ph<G::bk0 + s2>(acc[6 + c], wb0);
+    acc[9 + c] = add_ph<G::bk1 + s2>(acc[9 + c], wb1);
+  }
+}
+
 // acc += bsign * (1 + SGN g_MU) W psi given the projection (h0, h1) of psi,
 // where W = U (ADJ = false) or U^dag.
 template <int MU, int SGN, bool ADJ, class R>
@@ -410,14 +529,36 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
 // with the sign multiplied in, which holds fewer registers and keeps the code
 // straight-line in this register-capped, issue-bound kernel (measured faster).
 // FP32/FP64/float-float: both hops of a direction combined (combine_dir), the
-// time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time
-// (hop_site), which holds fewer registers and spills less in this
-// register-capped, issue-bound kernel (measured faster).
+// time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time,
+// which holds fewer registers and spills less in this register-capped,
+// issue-bound kernel (measured faster); with 18-real links entirely on the
+// 16-bit words (hop_site_w), with 12-real links on converted values (hop_site).
 #define TM_HOPS(MU)                                                                              \
     {                                                                                            \
       const int lf = lex_fwd(g, s, MU);                                                          \
       const int lb = lex_bwd(g, s, MU);                                                          \
-      if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {   \
+      if constexpr (kRawLinks<S, RECON>) {                                                       \
+        const unsigned negf = (MU == 3 && g.antiperiodic && s.c[3] == g.L[3] - 1) ? 0x80008000u : 0u; \
+        const unsigned negb = (MU == 3 && g.antiperiodic && s.c[3] == 0) ? 0x80008000u : 0u;      \
+        {                                                                                        \
+          unsigned u[9];                                                                         \
+          load_link_raw<S>(u, a.links, g, MU, par, cb);                                          \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            hop_site_w<S, MU, SF, false>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lf >> 1), \
+                                         cs, u, negf);                                           \
+          }                                                                                      \
+        }                                                                                        \
+        {                                                                                        \
+          unsigned u[9];                                                                         \
+          load_link_raw<S>(u, a.links, g, MU, opar, lb >> 1);                                    \
+          _Pragma("unroll") for (int j = 0; j < NR; ++j) {                                       \
+            if (!act[j]) continue;                                                               \
+            hop_site_w<S, MU, SB, true>(acc[j], a.c.in, ((size_t)(rhs[j] * 2 + opar) * NCH) * cs + (lb >> 1), \
+                                        cs, u, negb);                                            \
+          }                                                                                      \
+        }                                                                                        \
+      } else if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) { \
         R sf = 1, sbk = 1;                                                                       \
         if (MU == 3 && g.antiperiodic) {                                                         \
           if (s.c[3] == g.L[3] - 1) sf = -1;                                                     \
@@ -637,8 +778,9 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
 // operator form.  No tuning while a CUDA graph is being captured, nor while
 // TM_DSLASH_NR fixes NR.
 
+// the packed kernel mirrors the 12-real-link 16-bit path (kRawLinks is the other)
 template <class S, int RECON>
-constexpr bool kPackable = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+constexpr bool kPackable = (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) && RECON == 12;
 
 template <class S, int RECON, bool DAG, int EPI>
 tm_status_t launch_cfg(const tm_op* op, const DslashCall& c, cudaStream_t st, const TuneCfg& cfg) {

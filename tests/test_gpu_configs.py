@@ -57,14 +57,15 @@ L1, K1, M1 = (16, 16, 16, 32), 0.16, 0.005
 def w16():
     tl = require_gpu()
     U = synth.gauge_field(L1, 1235)
-    ops = {r: tl.Operator(L1, K1, M1, to_dev(U), recon=r) for r in (12, 18)}
+    ops = {r: tl.Operator(L1, K1, M1, to_dev(U), recon=r) for r in (12, 18)}  # FP64 always 18
     yield tl, U, ops
     for op in ops.values():
         op.close()
 
 
 @pytest.mark.parametrize("prec,recon,tol", [(0, 18, 1e-13), (1, 12, 1e-6), (1, 18, 1e-6),
-                                            (2, 12, 16 * UNIT_ROUNDOFF[2])])
+                                            (2, 12, 16 * UNIT_ROUNDOFF[2]), (2, 18, 16 * UNIT_ROUNDOFF[2]),
+                                            (3, 18, 16 * UNIT_ROUNDOFF[3])])
 def test_16x32_dslash_whole_lattice(w16, prec, recon, tol):
     tl, U, ops = w16
     fin = tl.empty_field(L1, prec, 1)
