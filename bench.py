@@ -180,6 +180,33 @@ def _tuned_shapes(tl, L):
     return out
 
 
+def _dslash_alone(tl, op, L, prec, n, recon, warmup=5, reps=20):
+    """tm_dslash (M on both parities) of n Z4 fields on the workload's operator,
+    timed with CUDA events after warm-up; algorithmic bytes per launch are
+    n x (in + out) spinors plus the links once."""
+    import torch
+    V = L[0] * L[1] * L[2] * L[3]
+    fin = tl.empty_field(L, prec, n)
+    fout = tl.empty_field(L, prec, n)
+    tl.z4_noise(L, fin, prec, 7, 0, n)
+    for _ in range(warmup):
+        tl.tm_dslash(op, fout, fin, n, prec=prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        tl.tm_dslash(op, fout, fin, n, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    esz = tl.ELEM_SIZE[prec]
+    nbytes = n * 2 * 24 * esz * V + 4 * tl.link_reals(recon, prec) * esz * V
+    peak, src = _peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"nrhs": n, "ms_per_launch": round(ms, 4), "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+            "link_reals": tl.link_reals(recon, prec), "peak_source": src}
+
+
 def _observables(pipe, c):
     """Per-source values of three volume-summed loops (sigma-term, g_A and
     Fig. 1 operator analogues) for the HP and LP sets, on the host."""
@@ -315,6 +342,11 @@ def run_ours(args):
         roofline = dict(bound="hbm", **{k: v for k, v in hbm_view.items()}, traffic=traffic, kernel=dom,
                         algorithmic_bytes_per_launch=round(b_dom / n_dom))
 
+    # ---- the Dslash alone on the workload's lattice: FP32 with one system
+    # (bandwidth bound, the HBM roofline target) and FP16 with a batch of 16
+    dslash_alone = {"f32": _dslash_alone(tl, op, L, tl.F32, 1, c["recon"]),
+                    "f16": _dslash_alone(tl, op, L, tl.F16, c["batch"], c["recon"])}
+
     # ---- correctness/quality summary of the last step
     it_lp = [s["iters"] for s in pipe.stats_lp]
     it_hp = [s["iters"] for s in pipe.stats_hp]
@@ -421,6 +453,7 @@ def run_ours(args):
             "fp64_cg_plain_s_per_source": round(t_plain, 4) if t_plain else None,
             "equal_error_speedup_vs_fp64_cg": speedup,
             "dslash_shapes": _tuned_shapes(tl, L),
+            "dslash_alone": dslash_alone,
         }
         print(json.dumps(line), flush=True)
     op.close()

@@ -467,14 +467,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 // spills), 6 for FP32.  Several systems per thread need registers in
 // proportion (4 blocks for 2, 2 for 4), so that the autotuner compares them
 // without forced spills.  FP64 and float-float are arithmetic bound and keep
-// their registers.  TM_DSLASH_MINBLOCKS overrides the one-system value at
-// build time.
+// their registers.  TM_DSLASH_MINBLOCKS (TM_DSLASH_MINBLOCKS_F32 for FP32
+// only) overrides the one-system value at build time.
 template <class S, int NR = 1>
 constexpr int dslash_min_blocks() {
   if constexpr (std::is_same<S, double>::value) return 1;
   else if constexpr (std::is_same<S, FFloat>::value) return 2;
   else if constexpr (NR >= 4) return 2;
   else if constexpr (NR == 2) return 4;
+#ifdef TM_DSLASH_MINBLOCKS_F32
+  else if constexpr (std::is_same<S, float>::value) return TM_DSLASH_MINBLOCKS_F32;
+#endif
 #ifdef TM_DSLASH_MINBLOCKS
   else return TM_DSLASH_MINBLOCKS;
 #else
