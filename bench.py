@@ -387,12 +387,13 @@ def run_ours(args):
     if not args.no_e2e:
         res_bytes = sum(2 * m.numel() * 8 for m, _ in res.values())
         host_out = [torch.empty(m.numel() * 2, dtype=torch.float64).pin_memory() for m, _ in res.values()]
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        _barrier(dist)
-        e0.record()
-        for _ in range(args.steps):
-            Ud = U_host.to("cuda", non_blocking=True)
+        # device staging buffer for the gauge field, filled from pinned host
+        # memory every step (allocating it anew would time the caching
+        # allocator's cudaMalloc, not the copy)
+        Ud = torch.empty_like(U_host, device="cuda")
+
+        def e2e_step():
+            Ud.copy_(U_host, non_blocking=True)
             op2 = tl.Operator(L, c["kappa"], c["mu"], Ud, recon=c["recon"])
             p2 = mk(op2)
             r2 = p2.run(dist)
@@ -402,7 +403,16 @@ def run_ours(args):
             torch.cuda.synchronize()
             del p2
             op2.close()
-            del Ud
+
+        # one untimed step: the library's memory pool grows to hold a second
+        # operator beside the resident one; later steps reuse that memory
+        e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(dist)
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step()
         e1.record()
         torch.cuda.synchronize()
         ems = _max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)

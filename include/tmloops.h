@@ -104,6 +104,18 @@ tm_status_t tm_op_destroy(tm_op_t *op);
  * source.  Calls on one handle must not overlap.                          */
 tm_status_t tm_op_clone(tm_op_t **out, const tm_op_t *src);
 
+/* Device memory.  Link copies, solver work spaces and contraction scratch come
+ * from a stream-ordered pool owned by the library, one per device, that keeps
+ * freed memory for its next allocations: creating an operator after
+ * destroying one of the same lattice maps no new pages.  tm_op_destroy waits
+ * for the device (like cudaFree) before returning its memory to the pool.
+ * tm_mem_trim(keep_bytes) waits for the device and releases unused pool
+ * memory beyond keep_bytes to the system (and the cached pinned host blocks
+ * of the solver's flags); tm_mem_reserved gives the bytes the pool of the
+ * current device holds, in use or not.                                     */
+tm_status_t tm_mem_trim(size_t keep_bytes);
+tm_status_t tm_mem_reserved(size_t *bytes);
+
 /* Bytes of nrhs internal spinor fields of precision prec on geometry g. */
 size_t tm_spinor_bytes(const tm_geom_t *g, tm_prec_t prec, int nrhs);
 

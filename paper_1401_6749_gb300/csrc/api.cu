@@ -165,6 +165,100 @@ void tune_store(const TuneKey& k, const TuneCfg& c) {
 void tuning_begin() { ++t_tuning; }
 void tuning_end() { --t_tuning; }
 
+// ------------------------------------------------------------ memory
+// One stream-ordered pool per device for everything the library allocates on
+// it.  Its release threshold is unbounded, so memory freed by one operator or
+// call stays mapped and the next allocation of similar size is served without
+// the driver mapping fresh pages (cudaMalloc/cudaFree of the gigabytes an
+// operator and its solver hold cost tens of milliseconds and synchronise the
+// device).  tm_mem_trim hands the unused part back.
+static std::mutex g_mem_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+static std::multimap<int, int*> g_pinned;  // free pinned blocks by size (ints)
+
+static tm_status_t pool_of_current_device(cudaMemPool_t* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return TM_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  auto it = g_pools.find(dev);
+  if (it == g_pools.end()) {
+    cudaMemPoolProps pr;
+    memset(&pr, 0, sizeof pr);
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.handleTypes = cudaMemHandleTypeNone;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t pool;
+    if (cudaMemPoolCreate(&pool, &pr) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMemPoolCreate failed on device %d", dev);
+      return TM_ERR_CUDA;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    it = g_pools.emplace(dev, pool).first;
+  }
+  *out = it->second;
+  return TM_OK;
+}
+
+tm_status_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
+  *p = nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cudaError_t e;
+  if (cs != cudaStreamCaptureStatusNone) {
+    // inside a caller's graph capture: a graph memory node of the default pool
+    e = cudaMallocAsync(p, bytes, s);
+  } else {
+    cudaMemPool_t pool;
+    TM_TRY(pool_of_current_device(&pool));
+    e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("%s: allocation of %zu bytes of device memory failed", what, bytes);
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int* pinned_take(int n, int* got) {
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    auto it = g_pinned.lower_bound(n);
+    if (it != g_pinned.end()) {
+      int* p = it->second;
+      *got = it->first;
+      g_pinned.erase(it);
+      return p;
+    }
+  }
+  int* p = nullptr;
+  if (cudaMallocHost(&p, sizeof(int) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    *got = 0;
+    return nullptr;
+  }
+  *got = n;
+  return p;
+}
+
+void pinned_give(int* p, int n) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  g_pinned.emplace(n, p);
+}
+
 // ------------------------------------------------------------ dispatch
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
   const bool r12 = (int)prec >= 0 && (int)prec < kNumPrec && op->recon_p[prec] == 12;
@@ -317,11 +411,8 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   for (int i = 0; i < kNumPrec; ++i) {
     const tm_prec_t pr = (tm_prec_t)i;
     const size_t nb = link_bytes(op->g, pr, op->recon_p[i]);
-    if (cudaMalloc(&op->links[i], nb) != cudaSuccess) {
-      set_error("tm_op_create: cudaMalloc of %zu bytes failed", nb);
-      tm_op_destroy(op);
-      return TM_ERR_CUDA;
-    }
+    const tm_status_t sa = dev_alloc(&op->links[i], nb, st, "tm_op_create");
+    if (sa != TM_OK) { tm_op_destroy(op); return sa; }
     const tm_status_t st2 = pack_links(op->g, pr, op->recon_p[i], op->links[i], U_lex, st);
     if (st2 != TM_OK) { tm_op_destroy(op); return st2; }
   }
@@ -349,11 +440,42 @@ extern "C" tm_status_t tm_op_clone(tm_op_t** out, const tm_op_t* src) {
 
 extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
   if (!op) return TM_OK;
+  // no work of the operator may still run: wait for the device (as cudaFree
+  // would), then return the memory to the pool and wait for that too, so
+  // that the next allocation on any stream can reuse it at once
+  cudaDeviceSynchronize();
   for (int i = 0; i < kNumPrec; ++i)
-    if (op->links[i] && op->owns_links) cudaFree(op->links[i]);
-  if (op->work) cudaFree(op->work);
-  if (op->host_flags) cudaFreeHost(op->host_flags);
+    if (op->owns_links) dev_free(op->links[i], nullptr);
+  dev_free(op->work, nullptr);
+  cudaStreamSynchronize(nullptr);
+  pinned_give(op->host_flags, op->host_flags_n);
   delete op;
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_mem_trim(size_t keep_bytes) {
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("tm_mem_trim: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  for (auto& kv : g_pools) cudaMemPoolTrimTo(kv.second, keep_bytes);
+  for (auto& kv : g_pinned) cudaFreeHost(kv.second);
+  g_pinned.clear();
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_mem_reserved(size_t* bytes) {
+  if (!bytes) { set_error("tm_mem_reserved: null argument"); return TM_ERR_ARG; }
+  *bytes = 0;
+  cudaMemPool_t pool;
+  TM_TRY(pool_of_current_device(&pool));
+  uint64_t v = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) != cudaSuccess) {
+    set_error("tm_mem_reserved: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  *bytes = (size_t)v;
   return TM_OK;
 }
 

@@ -258,40 +258,32 @@ struct Carver {
   }
 };
 
-static tm_status_t ensure_work(tm_op* op, size_t bytes, int nflags) {
+static tm_status_t ensure_work(tm_op* op, size_t bytes, int nflags, cudaStream_t s) {
   if (op->work_bytes < bytes) {
     if (op->work) {
       cudaDeviceSynchronize();
-      cudaFree(op->work);
+      dev_free(op->work, s);
       op->work = nullptr;
       op->work_bytes = 0;
     }
-    if (cudaMalloc(&op->work, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("tm_cg_solve: cudaMalloc of %zu bytes of work space failed", bytes);
+    TM_TRY(dev_alloc(&op->work, bytes, s, "tm_cg_solve work space"));
+    // the work space is used on other streams of the solve as well
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
       return TM_ERR_CUDA;
     }
     op->work_bytes = bytes;
   }
   if (op->host_flags_n < nflags) {
-    if (op->host_flags) cudaFreeHost(op->host_flags);
-    op->host_flags = nullptr;
-    if (cudaMallocHost(&op->host_flags, sizeof(int) * (size_t)nflags) != cudaSuccess) {
-      cudaGetLastError();
-      op->host_flags_n = 0;
+    pinned_give(op->host_flags, op->host_flags_n);
+    op->host_flags = pinned_take(nflags, &op->host_flags_n);
+    if (!op->host_flags) {
       set_error("tm_cg_solve: pinned host allocation failed");
       return TM_ERR_CUDA;
     }
-    op->host_flags_n = nflags;
   }
   return TM_OK;
 }
-
-#define TM_TRY(x)                          \
-  do {                                     \
-    const tm_status_t _s = (x);            \
-    if (_s != TM_OK) return _s;            \
-  } while (0)
 
 static tm_status_t scalar_launch(void (*k)(CgState, CgScalars), const CgState& st,
                                  const CgScalars& sc, cudaStream_t s) {
@@ -406,7 +398,7 @@ tm_status_t CgRun::setup() {
     st.iters = (int*)c.take(sizeof(int) * nrhs);
     st.nru = (int*)c.take(sizeof(int) * nrhs);
     st.status = (int*)c.take(sizeof(int) * nrhs);
-    if (pass == 0) TM_TRY(ensure_work(op, c.off, 5 * nrhs));
+    if (pass == 0) TM_TRY(ensure_work(op, c.off, 5 * nrhs, s));
   }
   sc.tol2 = prm.tol * prm.tol;
   sc.delta2 = mixed ? prm.delta * prm.delta : 0.0;

@@ -531,12 +531,7 @@ static const char* prec_name(const char* const (&names)[kNumPrec], tm_prec_t p) 
 }
 
 static tm_status_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
-  if (cudaMallocAsync(p, bytes, s) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("contraction scratch: cudaMallocAsync of %zu bytes failed", bytes);
-    return TM_ERR_CUDA;
-  }
-  return TM_OK;
+  return dev_alloc(p, bytes, s, "contraction scratch");
 }
 
 // local contraction with caller-chosen scratch (>= local_scratch_bytes)
@@ -583,7 +578,7 @@ extern "C" tm_status_t loop_contract_local(const tm_geom_t* gg, const void* left
   tm_status_t st = scratch_alloc((void**)&scratch, local_scratch_bytes(g, nrhs), s);
   if (st != TM_OK) return st;
   st = local_contract_into(g, left, right, prec, nrhs, mode != TM_LOOP_STD, out, scratch, s);
-  cudaFreeAsync(scratch, s);
+  dev_free(scratch, s);
   return st;
 }
 
@@ -629,7 +624,7 @@ extern "C" tm_status_t loop_contract_local_mom(const tm_geom_t* gg, const void* 
     count_launch();
     st = check_launch("loop_contract_local_mom final");
   }
-  cudaFreeAsync(scratch, s);
+  dev_free(scratch, s);
   return st;
 }
 
@@ -673,7 +668,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
       else oneD_partial_kernel<__nv_bfloat16, 18><<<grid, block, 0, s>>>(g, links, left, right, nchunk, scratch);
       break;
     default:
-      cudaFreeAsync(scratch, s);
+      dev_free(scratch, s);
       set_error("loop_contract_oneD: unknown precision %d", (int)prec);
       return TM_ERR_ARG;
   }
@@ -685,7 +680,7 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
     count_launch();
     st = check_launch("loop_contract_oneD final");
   }
-  cudaFreeAsync(scratch, s);
+  dev_free(scratch, s);
   return st;
 }
 

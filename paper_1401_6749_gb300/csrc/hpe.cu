@@ -76,10 +76,9 @@ extern "C" tm_status_t tm_hpe_apply(tm_op_t* op, void* out, const void* in, int 
   }
   // ping-pong so that the last application lands in out
   void* tmp = nullptr;
-  if (order > 1 && cudaMallocAsync(&tmp, F, s) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("tm_hpe_apply: cudaMallocAsync of %zu bytes failed", F);
-    return TM_ERR_CUDA;
+  if (order > 1) {
+    const tm_status_t sa = dev_alloc(&tmp, F, s, "tm_hpe_apply");
+    if (sa != TM_OK) return sa;
   }
   const void* src = in;
   tm_status_t st = TM_OK;
@@ -97,7 +96,7 @@ extern "C" tm_status_t tm_hpe_apply(tm_op_t* op, void* out, const void* in, int 
     st = dslash_dispatch(op, prec, c, s);
     src = dst;
   }
-  if (tmp) cudaFreeAsync(tmp, s);
+  dev_free(tmp, s);
   return st;
 }
 

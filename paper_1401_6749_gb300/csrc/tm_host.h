@@ -40,6 +40,23 @@ bool tune_active();   // tuning enabled and this thread not capturing a graph
 void tuning_begin();  // launches between these are timing runs (not traced)
 void tuning_end();
 
+#define TM_TRY(x)               \
+  do {                          \
+    const tm_status_t _s = (x); \
+    if (_s != TM_OK) return _s; \
+  } while (0)
+
+// Device memory of the library (gauge-link copies, solver work spaces,
+// contraction and HPE scratch): a stream-ordered pool of its own per device
+// that keeps freed memory mapped for the next allocation (api.cu).
+// dev_alloc reports failures through set_error with `what` in the message.
+tm_status_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+void dev_free(void* p, cudaStream_t s);
+// Pinned host blocks of at least n ints for the solver's flag mirrors, kept
+// for reuse when given back.
+int* pinned_take(int n, int* got);
+void pinned_give(int* p, int n);
+
 enum Epi { EPI_OUT = 0, EPI_CGUPD = 1, EPI_RESID = 2 };
 
 // One Dslash application over nrhs fields, with an optional fused epilogue.

@@ -63,6 +63,8 @@ _SIGS = {
     "tm_op_create": [_P(_vp), _P(tm_params_t), _vp, _vp],
     "tm_op_destroy": [_vp],
     "tm_op_clone": [_P(_vp), _vp],
+    "tm_mem_trim": [_sz],
+    "tm_mem_reserved": [_P(_sz)],
     "tm_spinor_bytes": [_P(tm_geom_t), _i, _i],
     "tm_spinor_pack": [_P(tm_geom_t), _vp, _i, _vp, _i, _vp],
     "tm_spinor_unpack": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
@@ -184,6 +186,18 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def tm_mem_trim(keep_bytes=0):
+    """Release unused memory of the library's device pool beyond keep_bytes."""
+    _check(_lib.tm_mem_trim(int(keep_bytes)))
+
+
+def tm_mem_reserved():
+    """Bytes held by the library's device pool on the current device."""
+    v = ctypes.c_size_t()
+    _check(_lib.tm_mem_reserved(ctypes.byref(v)))
+    return v.value
 
 
 def tm_spinor_pack(L, out, prec, in_lex, nrhs, stream=None):

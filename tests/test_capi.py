@@ -71,6 +71,7 @@ int main(void) {
   tm_op_t *op = NULL;
   if (tm_op_create(&op, &p, (const double *)out, NULL) != TM_ERR_ARG) return 5;
   if (tm_last_error()[0] == 0) return 6;
+  if (tm_mem_reserved(NULL) != TM_ERR_ARG) return 7;
   printf("ok\n");
   return 0;
 }
