@@ -340,6 +340,14 @@ tm_status_t tm_trace_read_flops(const char *name, double *total_flops);
  * dagger, epilogue, parity (-1 both), centre (0 none, 1 copy, 2 twisted),
  * inverse twist, half volume, systems}; packed = 1 for the FP32x2 form.    */
 void tm_tune_enable(int on);
+/* The FP16/BF16 Dslash with 18-real links on the tensor cores (warp-level
+ * MMA: 16 systems per MMA row block, the forward and backward hops of a
+ * direction in one m16n8k16 product per output spin, FP32 accumulation)
+ * instead of the CUDA-core kernel.  Off unless the environment sets
+ * TM_DSLASH_MMA=1; tm_dslash_mma_enable(0/1) switches it for the process
+ * (between launches).  Both kernels agree with the FP64 operator to the
+ * 16-bit tolerance; their bits differ (another summation order).          */
+tm_status_t tm_dslash_mma_enable(int on);
 void tm_tune_reset(void);
 int tm_tune_count(void);
 tm_status_t tm_tune_get(int i, int *key, int *nr, int *block, int *packed);

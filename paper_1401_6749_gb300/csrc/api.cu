@@ -125,6 +125,29 @@ int dslash_nr_override() {
   return v;
 }
 
+// The FP16/BF16 Dslash with 18-real links on the tensor cores: off unless the
+// environment sets TM_DSLASH_MMA=1; tm_dslash_mma_enable switches it at run
+// time (it is slower than the CUDA-core kernel at the sizes measured).
+static std::atomic<int> g_mma{-1};  // -1: not read from the environment yet
+
+bool dslash_mma_on() {
+  int v = g_mma.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("TM_DSLASH_MMA");
+    v = (e && strcmp(e, "1") == 0) ? 1 : 0;
+    int expect = -1;
+    g_mma.compare_exchange_strong(expect, v);
+    v = g_mma.load(std::memory_order_relaxed);
+  }
+  return v == 1;
+}
+
+static tm_status_t prepare_mma() {
+  static const tm_status_t prep =
+      dslash_mma_prepare<__half>() == TM_OK ? dslash_mma_prepare<__nv_bfloat16>() : TM_ERR_CUDA;
+  return prep;
+}
+
 // ------------------------------------------------------------ autotuning
 // Process-wide cache of the chosen Dslash launch shapes.  TM_TUNE=0 disables
 // tuning (the built-in shape is used); tm_tune_enable overrides at run time.
@@ -284,6 +307,12 @@ using namespace tml;
 extern "C" const char* tm_last_error(void) { return g_last_error.c_str(); }
 extern "C" uint64_t tm_launch_count(void) { return g_launches.load(); }
 
+extern "C" tm_status_t tm_dslash_mma_enable(int on) {
+  if (on) TM_TRY(prepare_mma());
+  g_mma.store(on ? 1 : 0, std::memory_order_relaxed);
+  return TM_OK;
+}
+
 extern "C" void tm_tune_enable(int on) { g_tune_on.store(on ? 1 : 0, std::memory_order_relaxed); }
 
 extern "C" void tm_tune_reset(void) {
@@ -390,6 +419,10 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   if (p->recon != 0 && p->recon != 12 && p->recon != 18) {
     set_error("recon must be 0, 12 or 18, got %d", p->recon);
     return TM_ERR_ARG;
+  }
+  if (dslash_mma_on()) {
+    const tm_status_t prep = prepare_mma();
+    if (prep != TM_OK) return prep;
   }
   tm_op* op = new tm_op();
   op->g = make_geom(p->L, p->antiperiodic_t ? 1 : 0);

@@ -485,6 +485,99 @@ constexpr int dslash_min_blocks() {
 #endif
 }
 
+// Scalars of the epilogue in the arithmetic type (FP32 copies for the narrow
+// formats: no FP64 arithmetic in their kernels)
+template <class R>
+struct EpiConsts {
+  R shop, nu, inv;
+  const void* cfield;
+};
+template <class R>
+__device__ __forceinline__ EpiConsts<R> epi_consts(const DslashArgs& a) {
+  EpiConsts<R> k;
+  if constexpr (kWide<R>) {
+    k.shop = (R)a.hop_scale; k.nu = (R)a.nu; k.inv = (R)a.inv;
+  } else {
+    k.shop = a.hop_scale_f; k.nu = a.nu_f; k.inv = a.inv_f;
+  }
+  k.cfield = a.c.cfield ? a.c.cfield : a.c.in;
+  return k;
+}
+
+// Everything after the hopping sum acc = H in at output site cb of parity par
+// for system r: out = T_out(T_c(c) + s_hop acc), then the epilogue of EPI.
+// Returns the system's |.|^2 contribution to the partial sums (0 if none).
+template <class S, int EPI, class R>
+__device__ __forceinline__ double dslash_epilogue(const DslashArgs& a, const EpiConsts<R>& k, int r, int par,
+                                                  int cb, const Cx<R> (&acc)[12]) {
+  using O = Ar<R>;
+  constexpr int NCH = spinor_chunks<S>();
+  const size_t cs = (size_t)a.g.Vh;
+  const R shop = k.shop, nu = k.nu, inv = k.inv;
+  const size_t b0 = ((size_t)(r * 2 + par) * NCH) * cs + cb;
+  Cx<R> out[12];
+  if (a.c.centre != 0) {
+    load_spinor<S>(out, k.cfield, b0, cs);
+    if (a.c.centre == 2) {  // A c = c + i nu g5 c
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        const R tw = q < 6 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
+        const Cx<R> c = out[q];
+        out[q] = {O::fma(-tw, c.im, c.re), O::fma(tw, c.re, c.im)};
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+      out[q] = {O::fma(shop, acc[q].re, out[q].re), O::fma(shop, acc[q].im, out[q].im)};
+  } else {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) out[q] = {O::mul(shop, acc[q].re), O::mul(shop, acc[q].im)};
+  }
+  if constexpr (std::is_same<R, FF>::value) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) out[q] = {O::norm(out[q].re), O::norm(out[q].im)};
+  }
+  if (a.c.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const R tw = q < 6 ? nu : -nu;
+      const Cx<R> v = out[q];
+      out[q] = {O::mul(inv, O::norm(O::fma(tw, v.im, v.re))), O::mul(inv, O::norm(O::fma(-tw, v.re, v.im)))};
+    }
+  }
+  double part = 0.0;
+  if constexpr (EPI == EPI_OUT) {
+    if (a.c.g5_out) {  // gamma_5 = diag(1, 1, -1, -1)
+#pragma unroll
+      for (int q = 6; q < 12; ++q) out[q] = {-out[q].re, -out[q].im};
+    }
+    store_spinor<S>(a.c.out, b0, cs, out);
+    if (a.c.partial) part = (double)norm2_12(out);
+  } else if constexpr (EPI == EPI_CGUPD) {
+    const R al = (R)a.c.alpha[r];
+    Cx<R> v[12];
+    load_spinor<S>(v, a.c.r, b0, cs);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = {O::fma(-al, out[q].re, v[q].re), O::fma(-al, out[q].im, v[q].im)};
+    store_spinor<S>(a.c.r, b0, cs, v);
+    part = (double)norm2_12(v);
+    Cx<R> w[12];
+    load_spinor<S>(v, a.c.x, b0, cs);
+    load_spinor<S>(w, a.c.p, b0, cs);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = {O::fma(al, w[q].re, v[q].re), O::fma(al, w[q].im, v[q].im)};
+    store_spinor<S>(a.c.x, b0, cs, v);
+  } else {  // EPI_RESID
+    Cx<R> v[12];
+    load_spinor<S>(v, a.c.b, b0, cs);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = {O::sub(v[q].re, out[q].re), O::sub(v[q].im, out[q].im)};
+    store_spinor<S>(a.c.out, b0, cs, v);
+    part = (double)norm2_12(v);
+  }
+  return part;
+}
+
 template <class S, int RECON, bool DAG, int EPI, int NR>
 __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kernel(const DslashArgs a) {
   using R = typename Prec<S>::R;
@@ -617,77 +710,11 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
     TM_HOPS(2)
     TM_HOPS(3)
 #undef TM_HOPS
-    // FP32 copies for the narrow formats: no FP64 arithmetic in their kernels
-    R shop, nu, inv;
-    if constexpr (kWide<R>) {
-      shop = (R)a.hop_scale; nu = (R)a.nu; inv = (R)a.inv;
-    } else {
-      shop = a.hop_scale_f; nu = a.nu_f; inv = a.inv_f;
-    }
-    const void* cfield = a.c.cfield ? a.c.cfield : a.c.in;
+    const EpiConsts<R> k = epi_consts<R>(a);
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       if (!act[j]) continue;
-      const size_t b0 = ((size_t)(rhs[j] * 2 + par) * NCH) * cs + cb;
-      Cx<R> out[12];
-      if (a.c.centre != 0) {
-        load_spinor<S>(out, cfield, b0, cs);
-        if (a.c.centre == 2) {  // A c = c + i nu g5 c
-#pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            const R tw = k < 6 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
-            const Cx<R> c = out[k];
-            out[k] = {O::fma(-tw, c.im, c.re), O::fma(tw, c.re, c.im)};
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-          out[k] = {O::fma(shop, acc[j][k].re, out[k].re), O::fma(shop, acc[j][k].im, out[k].im)};
-      } else {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) out[k] = {O::mul(shop, acc[j][k].re), O::mul(shop, acc[j][k].im)};
-      }
-      if constexpr (std::is_same<R, FF>::value) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) out[k] = {O::norm(out[k].re), O::norm(out[k].im)};
-      }
-      if (a.c.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          const R tw = k < 6 ? nu : -nu;
-          const Cx<R> v = out[k];
-          out[k] = {O::mul(inv, O::norm(O::fma(tw, v.im, v.re))), O::mul(inv, O::norm(O::fma(-tw, v.re, v.im)))};
-        }
-      }
-      if constexpr (EPI == EPI_OUT) {
-        if (a.c.g5_out) {  // gamma_5 = diag(1, 1, -1, -1)
-#pragma unroll
-          for (int k = 6; k < 12; ++k) out[k] = {-out[k].re, -out[k].im};
-        }
-        store_spinor<S>(a.c.out, b0, cs, out);
-        if (a.c.partial) part[j] = (double)norm2_12(out);
-      } else if constexpr (EPI == EPI_CGUPD) {
-        const R al = (R)a.c.alpha[rhs[j]];
-        Cx<R> v[12];
-        load_spinor<S>(v, a.c.r, b0, cs);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = {O::fma(-al, out[k].re, v[k].re), O::fma(-al, out[k].im, v[k].im)};
-        store_spinor<S>(a.c.r, b0, cs, v);
-        part[j] = (double)norm2_12(v);
-        Cx<R> w[12];
-        load_spinor<S>(v, a.c.x, b0, cs);
-        load_spinor<S>(w, a.c.p, b0, cs);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = {O::fma(al, w[k].re, v[k].re), O::fma(al, w[k].im, v[k].im)};
-        store_spinor<S>(a.c.x, b0, cs, v);
-      } else {  // EPI_RESID
-        Cx<R> v[12];
-        load_spinor<S>(v, a.c.b, b0, cs);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = {O::sub(v[k].re, out[k].re), O::sub(v[k].im, out[k].im)};
-        store_spinor<S>(a.c.out, b0, cs, v);
-        part[j] = (double)norm2_12(v);
-      }
+      part[j] = dslash_epilogue<S, EPI>(a, k, rhs[j], par, cb, acc[j]);
     }
   }
   if (EPI != EPI_OUT || a.c.partial != nullptr) {
@@ -704,11 +731,13 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
 }  // namespace tml
 
 #include "dslash_x2.cuh"
+#include "dslash_mma.cuh"
 
 namespace tml {
 
-// X2: two systems per thread in packed FP32x2 arithmetic (FP16/BF16, NR = 2)
-template <class S, int RECON, bool DAG, int EPI, int NR, bool X2 = false>
+// X2: two systems per thread in packed FP32x2 arithmetic (FP16/BF16, NR = 2);
+// MMA: the tensor-core kernel (FP16/BF16 with 18-real links, NR and bx unused)
+template <class S, int RECON, bool DAG, int EPI, int NR, bool X2 = false, bool MMA = false>
 tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, int bx = 128) {
   DslashArgs a;
   a.g = op->g;
@@ -733,6 +762,14 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
   const int per_par = (op->g.Vh + bx - 1) / bx;
   const int site_blocks = c.parity < 0 ? 2 * per_par : per_par;
   dim3 grid((unsigned)(site_blocks * a.rhs_groups));
+  if constexpr (MMA) {
+    const int tiles = (op->g.Vh + kMmaSites - 1) / kMmaSites;
+    grid = dim3((unsigned)(c.parity < 0 ? 2 * tiles : tiles), (unsigned)((c.nrhs + kMmaRows - 1) / kMmaRows));
+    if ((int)grid.y > 65535) {
+      set_error("dslash: %d systems exceed the launch grid", c.nrhs);
+      return TM_ERR_ARG;
+    }
+  }
   // trace class: dslash.<precision>.<epilogue>
   static const char* const kNames[5][3] = {
       {"dslash.f64.out", "dslash.f64.cgupd", "dslash.f64.resid"},
@@ -753,7 +790,8 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
   const double fixed = 4.0 * 2.0 * op->g.Vh * link_reals * e;
   cudaEvent_t ev = nullptr;
   a.trace_count = trace_begin(st, &ev);
-  if constexpr (X2) dslash_kernel_x2<S, RECON, DAG, EPI><<<grid, bx, 0, st>>>(a);
+  if constexpr (MMA) dslash_kernel_mma<S, DAG, EPI><<<grid, kMmaThreads, kMmaSmem, st>>>(a);
+  else if constexpr (X2) dslash_kernel_x2<S, RECON, DAG, EPI><<<grid, bx, 0, st>>>(a);
   else dslash_kernel<S, RECON, DAG, EPI, NR><<<grid, bx, 0, st>>>(a);
   count_launch();
   // algorithmic flops per output site and system: the spin-projected hops
@@ -822,6 +860,9 @@ tm_status_t launch_nr(const tm_op* op, const DslashCall& c, cudaStream_t st) {
     // FP64 and float-float: arithmetic-bound and register-heavy, one system per thread
     return launch_one<S, RECON, DAG, EPI, 1>(op, c, st);
   } else {
+    if constexpr (kRawLinks<S, RECON>) {
+      if (dslash_mma_on()) return launch_one<S, RECON, DAG, EPI, 1, false, true>(op, c, st);
+    }
     TuneCfg cfg{1, 128, 0};  // measured at 32^3 x 64 with 16 systems: NR = 1, 128 threads
     const int want = dslash_nr_override();
     if (want != 0) {
@@ -875,5 +916,7 @@ tm_status_t dslash_launch(const tm_op* op, const DslashCall& c, cudaStream_t st)
 #define TM_INSTANTIATE_DSLASH(S)                                                           \
   template tm_status_t dslash_launch<S, 18>(const tm_op*, const DslashCall&, cudaStream_t); \
   template tm_status_t dslash_launch<S, 12>(const tm_op*, const DslashCall&, cudaStream_t);
+
+#define TM_INSTANTIATE_DSLASH_MMA(S) template tm_status_t dslash_mma_prepare<S>();
 
 }  // namespace tml

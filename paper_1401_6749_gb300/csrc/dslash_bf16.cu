@@ -4,4 +4,5 @@
 
 namespace tml {
 TM_INSTANTIATE_DSLASH(__nv_bfloat16)
+TM_INSTANTIATE_DSLASH_MMA(__nv_bfloat16)
 }  // namespace tml

@@ -4,4 +4,5 @@
 
 namespace tml {
 TM_INSTANTIATE_DSLASH(__half)
+TM_INSTANTIATE_DSLASH_MMA(__half)
 }  // namespace tml

@@ -26,6 +26,7 @@ namespace tml {
 
 // Dslash launch-shape autotuning (cache in api.cu; selection in dslash.cuh)
 int dslash_nr_override();
+bool dslash_mma_on();  // FP16/BF16 with 18-real links on the tensor cores (api.cu)
 struct TuneKey {
   int prec, recon, dag, epi, parity, centre, out_inv, vh, nrhs;
   bool operator<(const TuneKey& o) const;
@@ -97,6 +98,10 @@ inline int nwarp_of(const Geom& g) { return (g.Vh + 31) / 32; }
 
 template <class S, int RECON>
 tm_status_t dslash_launch(const tm_op* op, const DslashCall& c, cudaStream_t s);
+// one-time set-up of the tensor-core Dslash kernels of a 16-bit format
+// (their shared-memory limit); tm_op_create calls it outside any capture
+template <class S>
+tm_status_t dslash_mma_prepare();
 
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s);
 

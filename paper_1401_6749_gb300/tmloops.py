@@ -64,6 +64,7 @@ _SIGS = {
     "tm_op_destroy": [_vp],
     "tm_op_clone": [_P(_vp), _vp],
     "tm_mem_trim": [_sz],
+    "tm_dslash_mma_enable": [_i],
     "tm_mem_reserved": [_P(_sz)],
     "tm_spinor_bytes": [_P(tm_geom_t), _i, _i],
     "tm_spinor_pack": [_P(tm_geom_t), _vp, _i, _vp, _i, _vp],
@@ -186,6 +187,11 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def tm_dslash_mma_enable(on=True):
+    """Run the FP16/BF16 18-real-link Dslash on the tensor cores (or not)."""
+    _check(_lib.tm_dslash_mma_enable(int(bool(on))))
 
 
 def tm_mem_trim(keep_bytes=0):
