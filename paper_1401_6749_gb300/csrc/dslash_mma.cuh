@@ -23,15 +23,16 @@
 // boundary sign goes onto W.
 //
 // A block of 256 threads takes 32 consecutive output sites of one parity and
-// 16 systems, in two rounds of four hops (two directions).  Each round first
-// stages the neighbour spinors of the 32 sites (16 systems x 3 chunks) and
-// their links in shared memory with 16-byte asynchronous copies, lane = site
-// as in the CUDA-core kernel (coalesced: consecutive sites share cache lines),
-// then each warp runs the MMAs of 4 sites from shared memory.  The staging
-// layout [hop][row][chunk][site ^ (row & 7)][4 words] keeps both the copies
-// (lane = site) and the fragment reads (8 rows per instruction) free of bank
-// conflicts.  The accumulators stay in registers across the rounds; the
-// sums go through shared memory, and each thread runs the common epilogue
+// 16 systems, one direction at a time through two shared-memory buffers: the
+// neighbour spinors of the 32 sites (16 systems x 3 chunks, both hops) and
+// their links are staged with 16-byte asynchronous copies, lane = site as in
+// the CUDA-core kernel (coalesced: consecutive sites share cache lines), and
+// direction mu + 1 is copied while the warps run the MMAs of direction mu,
+// 4 sites per warp.  The staging layout [hop][row][chunk][site ^ (row & 7)][4
+// words] keeps both the copies (lane = site) and the fragment reads (8 rows
+// per instruction) free of bank conflicts.  The time-boundary sign comes from
+// a per-site flag.  The accumulators stay in registers across the directions;
+// the sums go through shared memory, and each thread runs the common epilogue
 // (dslash_epilogue) for one (site, system), 32 consecutive sites per warp, so
 // the per-warp partial sums are the same as the CUDA-core kernel's.  A
 // system's result depends only on its own row.
