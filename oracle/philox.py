@@ -2,7 +2,7 @@
 
 Z4 noise (Sec. 2, Eqs. 1-2): every component of a source eta_r is drawn
 independently and uniformly from {1, i, -1, -i}.  The paper does not say how the
-random numbers are produced; this build uses the counter-based generator
+random numbers are produced; this library uses the counter-based generator
 Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
 as easy as 1, 2, 3", SC'11), so that a source depends only on (seed, source
 index, site) and can be regenerated anywhere.
