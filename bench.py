@@ -750,15 +750,23 @@ def run_reference(args):
     # CG, which takes the same number of iterations in exact arithmetic
     it_lp = [args.ref_lp_iters] * (c["n_hp"] + c["n_lp"])
     it_hp = [args.ref_hp_iters] * c["n_hp"]
-    vals = []
+    vals, walls = [], []
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(c, it_lp, it_hp, sample_L=(8, 8, 8, 16))
         if k >= args.warmup:
             vals.append(cb["value"])
+            walls.append(time.perf_counter() - t0)
     v = statistics.median(vals)
     cb["value"] = v
+    n_src = c["n_hp"] + c["n_lp"]
+    # ms_per_step: the oracle's time for one whole step of the workload (all
+    # sources), extrapolated from the sample; sample_ms_per_step: the wall time
+    # of one bounded sample as run
     line = {"metric": METRIC, "value": v, "unit": "s/source", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "warmup": args.warmup, "ms_per_step": round(v * n_src * 1e3, 1),
+            "sample_ms_per_step": round(statistics.median(walls) * 1e3, 1),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_name(c)}, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s/source", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
