@@ -72,6 +72,7 @@ int main(void) {
   if (tm_op_create(&op, &p, (const double *)out, NULL) != TM_ERR_ARG) return 5;
   if (tm_last_error()[0] == 0) return 6;
   if (tm_mem_reserved(NULL) != TM_ERR_ARG) return 7;
+  if (tm_dslash_mma_enable(0) != TM_OK) return 8;  /* switching off needs no device */
   printf("ok\n");
   return 0;
 }
