@@ -37,8 +37,7 @@ CONFIGS = {
                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
 }
 
-N_SM = 152                 # GB300: 2 dies x 76 SMs
-FP32_LANES = N_SM * 128    # FP32 FMA lanes
+FP32_LANES_PER_SM = 128    # FP32 FMA lanes per SM (4 partitions x 32)
 PREC_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "ff": 8}
 METRIC = "Dslash HBM GB/s and % roofline; TSM loop sec/source at fixed error vs FP64 CG"
 
@@ -72,13 +71,28 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
+    @staticmethod
+    def device_id():
+        """nvidia-smi's id of this process's GPU: its UUID (CUDA ordinals differ from
+        nvidia-smi's indices when CUDA_VISIBLE_DEVICES remaps them)."""
+        import torch
+        dev = torch.cuda.current_device()
+        try:
+            uid = str(torch.cuda.get_device_properties(dev).uuid)
+            if uid and uid != "None":
+                return uid if uid.startswith(("GPU-", "MIG-")) else "GPU-" + uid
+        except (AttributeError, RuntimeError):
+            pass
+        vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+        return vis[dev] if dev < len(vis) else str(dev)
+
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                 "-lms", "200", "-i", self.device_id()],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -330,12 +344,13 @@ def run_ours(args):
         # FMA pipe 60%, DRAM 27%): roofline against the FP32 peak derived from
         # the unit counts and the SM clock sampled during the timed region
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        alu_peak = FP32_LANES * 2.0 * sm_mhz * 1e6 / 1e12
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        alu_peak = n_sm * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
         tflops = flops_dom / (t_dom * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": round(tflops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                     "frac": round(tflops / alu_peak, 4), "traffic": traffic, "kernel": dom,
                     "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sampled)"
-                                   % (N_SM, sm_mhz),
+                                   % (n_sm, sm_mhz),
                     "algorithmic_flops_per_launch": round(flops_dom / n_dom),
                     "algorithmic_bytes_per_launch": round(b_dom / n_dom), "hbm": hbm_view}
     else:

@@ -4,10 +4,11 @@
  *
  * C ABI.  Every pointer to a field, a loop array or a gauge field is a DEVICE
  * pointer owned by the caller; the library never frees caller memory.  The
- * library allocates device memory only inside an opaque tm_op_t (link copies,
- * solver work vectors) and, for the two-stage reductions of the contraction
- * kernels, stream-ordered scratch (cudaMallocAsync/cudaFreeAsync on the
- * caller's stream).  All calls are asynchronous with respect to the host and
+ * library allocates device memory only from its own stream-ordered pool (one
+ * per device, see tm_mem_trim): inside an opaque tm_op_t (link copies, solver
+ * work vectors) and, for the two-stage reductions of the contraction kernels
+ * and the HPE ping-pong fields, scratch taken from and returned to that pool
+ * in the caller's stream order.  All calls are asynchronous with respect to the host and
  * ordered on the given stream, except tm_op_create (waits for the link packing)
  * and tm_cg_solve (returns when every right-hand side has converged or hit
  * its iteration limit).  Functions return a tm_status_t; on failure
@@ -252,8 +253,10 @@ tm_status_t tm_cg_solve_group(int nsets, tm_op_t *const *ops, void *const *x,
  * TM_LOOP_GEN (L = s, R = gamma_5 D_W s, Eq. 6, prefactor 2).  The caller
  * forms L and R; the prefactor is applied by tsm_combine.  left/right are
  * internal-layout fields of precision prec; out is a device array of doubles
- * (layout above).  Uses stream-ordered scratch of
- * 32 * nrhs * T * 2 * ceil(X*Y*Z/2/256) doubles (local) and 8x that (oneD).  */
+ * (layout above).  The two-stage reductions take their scratch from the
+ * library's pool: 64 * nrhs * T * ceil(X*Y*Z/2048) doubles (local), a few
+ * times that (oneD).  The launch grid limits T to 2 T <= 65535 and nrhs to
+ * 65535 (TM_ERR_ARG beyond).                                               */
 typedef enum { TM_LOOP_STD = 0, TM_LOOP_VV = 1, TM_LOOP_GEN = 2 } tm_loop_mode_t;
 
 tm_status_t loop_contract_local(const tm_geom_t *g, const void *left, const void *right,

@@ -572,6 +572,7 @@ extern "C" tm_status_t loop_contract_local(const tm_geom_t* gg, const void* left
   if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
   if (nrhs == 0) return TM_OK;
   if (nrhs > 65535) { set_error("loop_contract_local: nrhs must be <= 65535"); return TM_ERR_ARG; }
+  if (2 * gg->L[3] > 65535) { set_error("loop_contract_local: T = %d exceeds the launch grid (2 T <= 65535)", gg->L[3]); return TM_ERR_ARG; }
   const cudaStream_t s = (cudaStream_t)strm;
   const Geom g = make_geom(gg->L, 1);
   double* scratch = nullptr;
@@ -592,6 +593,7 @@ extern "C" tm_status_t loop_contract_local_mom(const tm_geom_t* gg, const void* 
   if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
   if (nrhs == 0) return TM_OK;
   if ((long)nrhs * n_mom > 65535) { set_error("loop_contract_local_mom: nrhs * n_mom must be <= 65535"); return TM_ERR_ARG; }
+  if (2 * gg->L[3] > 65535) { set_error("loop_contract_local_mom: T = %d exceeds the launch grid (2 T <= 65535)", gg->L[3]); return TM_ERR_ARG; }
   const cudaStream_t s = (cudaStream_t)strm;
   const Geom g = make_geom(gg->L, 1);
   MomList ml;

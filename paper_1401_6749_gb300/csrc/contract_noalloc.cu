@@ -70,7 +70,7 @@ extern "C" tm_status_t loop_contract_local_noalloc(const tm_geom_t* gg, const vo
     set_error("loop_contract_local_noalloc: unknown mode %d", (int)mode);
     return TM_ERR_ARG;
   }
-  if ((int)prec < 0 || (int)prec > 3) {
+  if ((unsigned)prec >= (unsigned)kNumPrec) {
     set_error("loop_contract_local_noalloc: unknown precision %d", (int)prec);
     return TM_ERR_ARG;
   }
@@ -78,6 +78,10 @@ extern "C" tm_status_t loop_contract_local_noalloc(const tm_geom_t* gg, const vo
   if (nrhs == 0) return TM_OK;
   if (nrhs > 65535) {
     set_error("loop_contract_local_noalloc: nrhs must be <= 65535");
+    return TM_ERR_ARG;
+  }
+  if (2 * gg->L[3] > 65535) {
+    set_error("loop_contract_local_noalloc: T = %d exceeds the launch grid (2 T <= 65535)", gg->L[3]);
     return TM_ERR_ARG;
   }
   const Geom g = make_geom(gg->L, 1);

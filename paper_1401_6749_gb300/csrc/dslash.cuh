@@ -621,10 +621,6 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<S, NR>())) dslash_kern
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
 // FP32/FP64/float-float: both hops of a direction combined (combine_dir), the
-// time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time
-// with the sign multiplied in, which holds fewer registers and keeps the code
-// straight-line in this register-capped, issue-bound kernel (measured faster).
-// FP32/FP64/float-float: both hops of a direction combined (combine_dir), the
 // time-boundary sign on the projected spinor.  FP16/BF16: one hop at a time,
 // which holds fewer registers and spills less in this register-capped,
 // issue-bound kernel (measured faster); with 18-real links entirely on the
@@ -783,7 +779,11 @@ tm_status_t launch_one(const tm_op* op, const DslashCall& c, cudaStream_t st, in
   // streams; per launch the links of all sites
   const double e = (double)sizeof(S);
   const double out_sites = (c.parity < 0 ? 2.0 : 1.0) * op->g.Vh;
-  const int centre = a.c.centre != 0 ? 1 : 0;
+  // the centre field counts unless it is the input array read on both parities
+  // (a full-lattice M: the centre reads are the neighbour reads of the other
+  // output parity, the same bytes)
+  const bool centre_is_in = a.c.cfield == nullptr || a.c.cfield == a.c.in;
+  const int centre = (a.c.centre != 0 && !(c.parity < 0 && centre_is_in)) ? 1 : 0;
   const int epi_streams = EPI == EPI_OUT ? 1 : (EPI == EPI_CGUPD ? 5 : 2);
   const double per_rhs = out_sites * 24.0 * e * (1 + centre + epi_streams);
   const int link_reals = RECON;

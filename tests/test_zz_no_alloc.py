@@ -3,17 +3,23 @@ allocate device memory (their application owns the GPU's memory, or their
 loop must not pay for an allocation per call).  It keeps its reduction scratch
 in a fixed array inside the library instead of allocating any.
 
-Checked through the C ABI against loop_contract_local, on two calls in a row
-with different inputs, sizes and precisions (the shared array keeps the last
-call's contents, which must not leak into the next result), within the
-contraction tolerances of the other tests (1e-12 for FP64 fields, 1e-5 for
-FP32).  This file is collected last so that a failure here leaves every other
-test already run.
+Checked through the C ABI, on consecutive calls with different inputs, sizes
+and precisions (the shared array keeps the last call's contents, which must
+not leak into the next result):
+  * bit-identical to loop_contract_local (the same kernels in the same order,
+    only the scratch address differs);
+  * against the FP64 oracle for the FP64 case, at 1e-12;
+  * a call allocates nothing: the library pool, torch's caching allocator and
+    its allocation counters are unchanged across it;
+  * sizes beyond the fixed array are rejected before any launch.
+This file is collected last so that a failure here leaves every other test
+already run.
 """
 import numpy as np
 import pytest
 import torch
 
+from oracle import loops as oloops
 from paper_1401_6749_gb300 import synth
 
 from .gpu_util import from_dev, pack, rel_l2, require_gpu
@@ -28,7 +34,13 @@ def _both(tl, L, fa, fb, prec, n, mode):
     tl.loop_contract_local(L, fa, fb, prec, n, mode, ref)
     tl.loop_contract_local_noalloc(L, fa, fb, prec, n, mode, got)
     torch.cuda.synchronize()
-    return from_dev(got, (n, 16, T)), from_dev(ref, (n, 16, T))
+    return got, ref
+
+
+def _alloc_state(tl):
+    st = torch.cuda.memory_stats()
+    return (tl.tm_mem_reserved(), torch.cuda.memory_reserved(), torch.cuda.memory_allocated(),
+            st.get("allocation.all.allocated", 0), st.get("segment.all.allocated", 0))
 
 
 def test_noalloc_matches_allocating_contraction_on_consecutive_calls():
@@ -38,15 +50,34 @@ def test_noalloc_matches_allocating_contraction_on_consecutive_calls():
     a = synth.random_spinor(L1, 3, seed=101)
     b = synth.random_spinor(L1, 3, seed=102)
     got, ref = _both(tl, L1, pack(tl, L1, a, tl.F64), pack(tl, L1, b, tl.F64), tl.F64, 3, tl.LOOP_VV)
-    assert np.all(np.isfinite(got))
-    assert rel_l2(got, ref) < 1e-12
-    # call 2: other lattice, FP32 fields, 2 right-hand sides, other estimator
-    L2 = (12, 10, 8, 6)
-    c = synth.random_spinor(L2, 2, seed=103)
-    d = synth.random_spinor(L2, 2, seed=104)
-    got, ref = _both(tl, L2, pack(tl, L2, c, tl.F32), pack(tl, L2, d, tl.F32), tl.F32, 2, tl.LOOP_GEN)
-    assert np.all(np.isfinite(got))
-    assert rel_l2(got, ref) < 1e-5
+    assert torch.equal(got, ref)
+    orc = oloops.local_loops(a, b, "vv")
+    assert rel_l2(from_dev(got, (3, 16, L1[3])), orc) < 1e-12
+    # calls 2-4: other lattices and precisions (FP32, FP16, float-float), other estimators
+    cases = [((12, 10, 8, 6), tl.F32, 2, tl.LOOP_GEN), ((8, 8, 8, 16), tl.F16, 5, tl.LOOP_STD),
+             ((10, 8, 6, 4), tl.FF, 2, tl.LOOP_VV)]
+    for k, (L, prec, n, mode) in enumerate(cases):
+        c = synth.random_spinor(L, n, seed=103 + 2 * k)
+        d = synth.random_spinor(L, n, seed=104 + 2 * k)
+        got, ref = _both(tl, L, pack(tl, L, c, prec), pack(tl, L, d, prec), prec, n, mode)
+        assert torch.isfinite(got).all()
+        assert torch.equal(got, ref), "precision %d" % prec
+
+
+def test_noalloc_allocates_nothing():
+    tl = require_gpu()
+    L = (8, 8, 8, 8)
+    n = 4
+    a = pack(tl, L, synth.random_spinor(L, n, seed=201), tl.F32)
+    b = pack(tl, L, synth.random_spinor(L, n, seed=202), tl.F32)
+    out = torch.empty(n * 16 * L[3] * 2, dtype=torch.float64, device="cuda")
+    tl.loop_contract_local_noalloc(L, a, b, tl.F32, n, tl.LOOP_VV, out)   # first call: set-up
+    torch.cuda.synchronize()
+    before = _alloc_state(tl)
+    for mode in (tl.LOOP_STD, tl.LOOP_VV, tl.LOOP_GEN):
+        tl.loop_contract_local_noalloc(L, a, b, tl.F32, n, mode, out)
+    torch.cuda.synchronize()
+    assert _alloc_state(tl) == before
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
@@ -55,3 +86,6 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
     with pytest.raises(tl.TmError) as e:
         tl.loop_contract_local_noalloc((32, 32, 32, 64), dummy, dummy, tl.F16, 17, tl.LOOP_STD, dummy)
     assert e.value.status == 1                                     # TM_ERR_ARG
+    with pytest.raises(tl.TmError) as e:
+        tl.loop_contract_local_noalloc((32, 32, 32, 64), dummy, dummy, 7, 1, tl.LOOP_STD, dummy)
+    assert e.value.status == 1
