@@ -194,22 +194,30 @@ def _tuned_shapes(tl, L):
     return out
 
 
-def _dslash_alone(tl, op, L, prec, n, recon, warmup=5, reps=20):
+def _dslash_alone(tl, op, L, prec, n, recon, warmup=5, reps=20, il=False):
     """tm_dslash (M on both parities) of n Z4 fields on the workload's operator,
     timed with CUDA events after warm-up; algorithmic bytes per launch are
-    n x (in + out) spinors plus the links once."""
+    n x (in + out) spinors plus the links once.  il: the same fields in the
+    system-interleaved layout through tm_dslash_il (tensor cores)."""
     import torch
     V = L[0] * L[1] * L[2] * L[3]
     fin = tl.empty_field(L, prec, n)
     fout = tl.empty_field(L, prec, n)
     tl.z4_noise(L, fin, prec, 7, 0, n)
+    apply = lambda: tl.tm_dslash(op, fout, fin, n, prec=prec)
+    if il:
+        fin_il = tl.empty_field_il(L, n)
+        fout_il = tl.empty_field_il(L, n)
+        tl.tm_spinor_to_il(L, fin_il, fin, prec, n)
+        del fin, fout
+        apply = lambda: tl.tm_dslash_il(op, fout_il, fin_il, n, prec=prec)
     for _ in range(warmup):
-        tl.tm_dslash(op, fout, fin, n, prec=prec)
+        apply()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        tl.tm_dslash(op, fout, fin, n, prec=prec)
+        apply()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -311,7 +319,7 @@ def run_ours(args):
     clk = clocks.stop()
     classes = {}
     precs = ("f64", "f32", "f16", "bf16", "ff")
-    names = ["dslash.%s.%s" % (p, e) for p in precs for e in ("out", "cgupd", "resid")]
+    names = ["dslash.%s.%s" % (p, e) for p in precs + ("f16il", "bf16il") for e in ("out", "cgupd", "resid")]
     names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in precs]
     names += ["blas.xpay", "z4_noise", "cg.graph"]
     flops = {}
@@ -339,7 +347,7 @@ def run_ours(args):
     hbm_view = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_source": peak_src}
     flops_dom = flops.get(dom, 0.0)
-    if dom.startswith(("dslash.f16", "dslash.bf16")) and flops_dom > 0:
+    if dom.startswith(("dslash.f16.", "dslash.bf16.")) and flops_dom > 0:
         # the 16-bit Dslash is bound by FP32 instruction issue (ncu: issue 78%,
         # FMA pipe 60%, DRAM 27%): roofline against the FP32 peak derived from
         # the unit counts and the SM clock sampled during the timed region
@@ -360,7 +368,8 @@ def run_ours(args):
     # ---- the Dslash alone on the workload's lattice: FP32 with one system
     # (bandwidth bound, the HBM roofline target) and FP16 with a batch of 16
     dslash_alone = {"f32": _dslash_alone(tl, op, L, tl.F32, 1, c["recon"]),
-                    "f16": _dslash_alone(tl, op, L, tl.F16, c["batch"], c["recon"])}
+                    "f16": _dslash_alone(tl, op, L, tl.F16, c["batch"], c["recon"]),
+                    "f16il": _dslash_alone(tl, op, L, tl.F16, c["batch"], c["recon"], il=True)}
 
     # ---- correctness/quality summary of the last step
     it_lp = [s["iters"] for s in pipe.stats_lp]
@@ -507,13 +516,21 @@ def run_dslash(args):
     fin = tl.empty_field(L, prec, n)
     fout = tl.empty_field(L, prec, n)
     tl.z4_noise(L, fin, prec, 7, 0, n)
+    apply = lambda: tl.tm_dslash(op, fout, fin, n, prec=prec)
+    if args.layout == "il":
+        # the same fields in the system-interleaved layout, tensor-core kernel
+        fin_il = tl.empty_field_il(L, n)
+        fout_il = tl.empty_field_il(L, n)
+        tl.tm_spinor_to_il(L, fin_il, fin, prec, n)
+        del fin, fout
+        apply = lambda: tl.tm_dslash_il(op, fout_il, fin_il, n, prec=prec)
     for _ in range(args.warmup):
-        tl.tm_dslash(op, fout, fin, n, prec=prec)
+        apply()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        tl.tm_dslash(op, fout, fin, n, prec=prec)
+        apply()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -522,7 +539,7 @@ def run_dslash(args):
     nbytes = n * 2 * 24 * esz * V + 4 * link_reals * esz * V
     peak, src = _peaks()
     gbs = nbytes / (ms * 1e-3) / 1e9
-    print(json.dumps({"mode": "dslash", "lattice": list(L), "nrhs": n, "prec": args.prec,
+    print(json.dumps({"mode": "dslash", "layout": args.layout, "lattice": list(L), "nrhs": n, "prec": args.prec,
                       "recon": link_reals, "ms_per_launch": round(ms, 4), "bytes_per_launch": nbytes,
                       "GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4), "peak_source": src,
                       "l2": "in+out fields %.0f MB" % (2 * n * 24 * esz * V / 1e6)}), flush=True)
@@ -818,6 +835,8 @@ def main():
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16", "ff"])
+    ap.add_argument("--layout", default="std", choices=["std", "il"],
+                    help="--dslash: standard layout (CUDA-core kernel) or system-interleaved (tensor cores)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
     if args.schur is not None:

@@ -143,6 +143,43 @@ tm_status_t tm_dslash(tm_op_t *op, void *out, const void *in, int nrhs, int dagg
 tm_status_t tm_dslash_g5(tm_op_t *op, void *out, const void *in, int nrhs, int dagger,
                          int mu_zero, tm_prec_t prec, tm_stream_t s);
 
+/* System-interleaved 16-bit layout (this library's own; the paper gives no
+ * layout).  nrhs F16 or BF16 fields stored as ceil(nrhs / 16) blocks of 16
+ * systems: [block][parity][k = 3 spin + colour][cb][slot 0..15], 4 bytes per
+ * slot (one complex number, re in the low half), 64 bytes per (k, site);
+ * system j < 8 of a block sits in slot 2j and system j + 8 in slot 2j + 1.
+ * The multi-system Dslash reads it with one 8-byte load per (spin, colour,
+ * two systems) and feeds the tensor cores straight from it.
+ * tm_spinor_bytes_il: bytes of nrhs systems (0 on a bad geometry).
+ * tm_spinor_to_il / tm_spinor_from_il: standard internal layout <-> this one
+ *   (a byte permutation: exact; slots of systems >= nrhs are written as
+ *   zero); out and in must not overlap.  prec F16 or BF16, else TM_ERR_ARG.
+ * tm_dslash_il: out = M in, M^dag in or D_W in (as tm_dslash) on fields in
+ *   this layout, each hop a warp-level MMA over 16 systems (FP16/BF16
+ *   products, FP32 accumulation), every site's neighbours staged in shared
+ *   memory by bulk asynchronous copies (the fields must be 16-byte aligned,
+ *   else TM_ERR_ARG).  Needs the 18-real 16-bit link copy (recon 18 or 0:
+ *   TM_ERR_UNSUPPORTED for 12).  Results agree with tm_dslash to the 16-bit
+ *   tolerance; the bits differ (summation order).  A staging wait that never
+ *   completes gives up after a bounded number of rounds and sets a flag of
+ *   the operator: tm_op_check(op) waits for the device and returns
+ *   TM_ERR_TIMEOUT (clearing the flag) if that happened, tm_cg_solve returns
+ *   TM_ERR_TIMEOUT at its next poll.
+ * tm_cg_il_enable(1) (default, unless the environment sets TM_CG_IL=0): plain
+ *   F16/BF16 solves of tm_cg_solve convert eta to this layout, iterate on it
+ *   with tm_dslash_il's kernel and convert x back; 0 keeps them on the
+ *   CUDA-core kernel of the standard layout.  Switch between solves only: the
+ *   two give different (equally valid) truncated solutions.                */
+size_t tm_spinor_bytes_il(const tm_geom_t *g, int nrhs);
+tm_status_t tm_spinor_to_il(const tm_geom_t *g, void *out_il, const void *in, tm_prec_t prec, int nrhs,
+                            tm_stream_t s);
+tm_status_t tm_spinor_from_il(const tm_geom_t *g, void *out, const void *in_il, tm_prec_t prec, int nrhs,
+                              tm_stream_t s);
+tm_status_t tm_dslash_il(tm_op_t *op, void *out_il, const void *in_il, int nrhs, int dagger, int mu_zero,
+                         tm_prec_t prec, tm_stream_t s);
+tm_status_t tm_cg_il_enable(int on);
+tm_status_t tm_op_check(tm_op_t *op);
+
 /* Z4 noise (Sec. 2, Eqs. 1-2): eta_r(x)_{alpha c} = i^k with k = bits
  * [2(3 alpha + c), 2(3 alpha + c) + 1] of word 0 of Philox4x32-10 applied to
  * counter (lex, r, 0, 0) with key (seed mod 2^32, seed >> 32), for

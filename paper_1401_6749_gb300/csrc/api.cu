@@ -284,6 +284,7 @@ void pinned_give(int* p, int n) {
 
 // ------------------------------------------------------------ dispatch
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
+  if (c.il) return dslash_il_dispatch(op, prec, c, s);
   const bool r12 = (int)prec >= 0 && (int)prec < kNumPrec && op->recon_p[prec] == 12;
   switch (prec) {
     case TM_PREC_F64: return dslash_launch<double, 18>(op, c, s);
@@ -439,7 +440,8 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   op->host_flags = nullptr;
   op->host_flags_n = 0;
   op->owns_links = true;
-  for (int i = 0; i < kNumPrec; ++i) op->links[i] = nullptr;
+  for (int i = 0; i < kNumPrec; ++i) op->links[i] = op->links_il[i] = nullptr;
+  op->il_err = nullptr;
   const cudaStream_t st = (cudaStream_t)s;
   for (int i = 0; i < kNumPrec; ++i) {
     const tm_prec_t pr = (tm_prec_t)i;
@@ -448,6 +450,24 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
     if (sa != TM_OK) { tm_op_destroy(op); return sa; }
     const tm_status_t st2 = pack_links(op->g, pr, op->recon_p[i], op->links[i], U_lex, st);
     if (st2 != TM_OK) { tm_op_destroy(op); return st2; }
+    // the interleaved (tensor-core) Dslash reads the 16-bit links site-major
+    if ((pr == TM_PREC_F16 || pr == TM_PREC_BF16) && op->recon_p[i] == 18) {
+      tm_status_t s3 = dev_alloc(&op->links_il[i], il_link_bytes(op->g), st, "tm_op_create");
+      if (s3 == TM_OK) s3 = il_pack_links(op->g, op->links_il[i], op->links[i], st);
+      if (s3 != TM_OK) { tm_op_destroy(op); return s3; }
+      if (!op->il_err) {
+        s3 = dev_alloc((void**)&op->il_err, sizeof(int), st, "tm_op_create");
+        if (s3 == TM_OK && cudaMemsetAsync(op->il_err, 0, sizeof(int), st) != cudaSuccess) {
+          set_error("tm_op_create: %s", cudaGetErrorString(cudaGetLastError()));
+          s3 = TM_ERR_CUDA;
+        }
+        if (s3 != TM_OK) { tm_op_destroy(op); return s3; }
+      }
+    }
+  }
+  if (op->il_err) {
+    const tm_status_t s4 = il_prepare();
+    if (s4 != TM_OK) { tm_op_destroy(op); return s4; }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("tm_op_create: %s", cudaGetErrorString(cudaGetLastError()));
@@ -478,7 +498,11 @@ extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
   // that the next allocation on any stream can reuse it at once
   cudaDeviceSynchronize();
   for (int i = 0; i < kNumPrec; ++i)
-    if (op->owns_links) dev_free(op->links[i], nullptr);
+    if (op->owns_links) {
+      dev_free(op->links[i], nullptr);
+      dev_free(op->links_il[i], nullptr);
+    }
+  if (op->owns_links) dev_free(op->il_err, nullptr);
   dev_free(op->work, nullptr);
   cudaStreamSynchronize(nullptr);
   pinned_give(op->host_flags, op->host_flags_n);

@@ -50,24 +50,25 @@ struct SolveOp {
   bool schur;
   int nrhs;
   cudaStream_t s;
+  bool il = false;  // vectors in the system-interleaved 16-bit layout
   double nu() const { return 2.0 * op->kappa * op->mu; }
 
   // t = Op v (+ |t|^2 partials); for the Schur operator v's even half is scratch
   tm_status_t apply(tm_prec_t prec, void* v, void* t, double* partial, const int* active) const {
     if (!schur) {
       DslashCall c;
-      c.in = v; c.out = t; c.nrhs = nrhs; c.partial = partial; c.active = active;
+      c.in = v; c.out = t; c.nrhs = nrhs; c.partial = partial; c.active = active; c.il = il;
       return dslash_dispatch(op, prec, c, s);
     }
     DslashCall c1;  // v_e = A^-1 H_eo v_o
     c1.custom = true; c1.in = v; c1.out = v; c1.nrhs = nrhs; c1.active = active;
-    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = nu();
+    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = nu(); c1.il = il;
     const tm_status_t st = dslash_dispatch(op, prec, c1, s);
     if (st != TM_OK) return st;
     DslashCall c2;  // t_o = A v_o - kappa^2 H_oe v_e
     c2.custom = true; c2.in = v; c2.cfield = v; c2.out = t; c2.nrhs = nrhs; c2.active = active;
     c2.parity = 1; c2.centre = 2; c2.hop_scale = -op->kappa * op->kappa; c2.nu = nu();
-    c2.partial = partial;
+    c2.partial = partial; c2.il = il;
     return dslash_dispatch(op, prec, c2, s);
   }
 
@@ -76,13 +77,14 @@ struct SolveOp {
   tm_status_t apply_dag(tm_prec_t prec, void* t, DslashCall e) const {
     e.nrhs = nrhs;
     e.dagger = true;
+    e.il = il;
     if (!schur) {
       e.in = t;
       return dslash_dispatch(op, prec, e, s);
     }
     DslashCall c1;  // t_e = A(-nu)^-1 (H^dag)_eo t_o
     c1.custom = true; c1.dagger = true; c1.in = t; c1.out = t; c1.nrhs = nrhs; c1.active = e.active;
-    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = -nu();
+    c1.parity = 0; c1.centre = 0; c1.hop_scale = 1.0; c1.out_inv = true; c1.nu = -nu(); c1.il = il;
     const tm_status_t st = dslash_dispatch(op, prec, c1, s);
     if (st != TM_OK) return st;
     e.custom = true; e.in = t; e.cfield = t; e.parity = 1; e.centre = 2;
@@ -92,11 +94,12 @@ struct SolveOp {
 
   // eta_hat_o = eta_o + kappa H_oe A^-1 eta_e into dst (odd half; even half scratch)
   tm_status_t prepare(tm_prec_t prec, const void* eta, void* dst) const {
-    tm_status_t st = twist(op->g, prec, dst, eta, nu(), 1, 0, nrhs, s);
+    tm_status_t st = il ? il_twist(op->g, prec, dst, eta, nu(), 1, 0, nrhs, s)
+                        : twist(op->g, prec, dst, eta, nu(), 1, 0, nrhs, s);
     if (st != TM_OK) return st;
     DslashCall c;
     c.custom = true; c.in = dst; c.cfield = eta; c.out = dst; c.nrhs = nrhs;
-    c.parity = 1; c.centre = 1; c.hop_scale = op->kappa; c.nu = nu();
+    c.parity = 1; c.centre = 1; c.hop_scale = op->kappa; c.nu = nu(); c.il = il;
     return dslash_dispatch(op, prec, c, s);
   }
 
@@ -104,7 +107,7 @@ struct SolveOp {
   tm_status_t reconstruct(tm_prec_t prec, const void* eta, void* x) const {
     DslashCall c;
     c.custom = true; c.in = x; c.cfield = eta; c.out = x; c.nrhs = nrhs;
-    c.parity = 0; c.centre = 1; c.hop_scale = op->kappa; c.out_inv = true; c.nu = nu();
+    c.parity = 0; c.centre = 1; c.hop_scale = op->kappa; c.out_inv = true; c.nu = nu(); c.il = il;
     return dslash_dispatch(op, prec, c, s);
   }
 };
@@ -323,6 +326,10 @@ struct CgRun {
   cudaStream_t s = nullptr;
 
   bool mixed = false, schur = false;
+  // plain F16/BF16 solves iterate on the system-interleaved layout (tensor-core
+  // Dslash): eta is converted into eta_il at set-up, x_il back into x at the end
+  bool il = false;
+  void *eta_il = nullptr, *x_il = nullptr;
   tm_prec_t lo = TM_PREC_F64, hi = TM_PREC_F64;
   int par0 = 0, npar = 2, nwarp = 0;
   void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
@@ -337,13 +344,14 @@ struct CgRun {
   int nper = 0;
   size_t pstride = 0;
 
-  SolveOp A() const { return SolveOp{op, schur, nrhs, s}; }
+  SolveOp A() const { return SolveOp{op, schur, nrhs, s, il}; }
   tm_status_t reduce() const { return reduce_partials(part0, nper, nrhs, st.red, s, pstride); }
 
   tm_status_t setup();
   tm_status_t iteration();
   tm_status_t poll() const;    // active flags -> the operator's pinned host flags
   bool any_active() const;
+  bool timed_out() const;
   tm_status_t finish(tm_status_t* worst);
 };
 
@@ -370,7 +378,8 @@ tm_status_t CgRun::setup() {
   par0 = schur ? 1 : 0;
   npar = schur ? 1 : 2;
   const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
-  const size_t F = tm_spinor_bytes(&gg, lo, nrhs);
+  il = !mixed && (lo == TM_PREC_F16 || lo == TM_PREC_BF16) && op->recon_p[lo] == 18 && cg_il_on();
+  const size_t F = il ? il_bytes(g, nrhs) : tm_spinor_bytes(&gg, lo, nrhs);
   const size_t F64 = tm_spinor_bytes(&gg, TM_PREC_F64, nrhs);
   nwarp = nwarp_of(g);
   const size_t P = sizeof(double) * (size_t)nrhs * 2 * (size_t)nwarp;
@@ -383,6 +392,7 @@ tm_status_t CgRun::setup() {
       y = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
     } else {
       b = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
+      if (il) { eta_il = c.take(F); x_il = c.take(F); }
     }
     partial = (double*)c.take(P);
     st.bb = (double*)c.take(sizeof(double) * nrhs);
@@ -410,16 +420,18 @@ tm_status_t CgRun::setup() {
   part0 = partial + (schur ? nwarp : 0);
   nper = npar * nwarp;
   pstride = 2 * (size_t)nwarp;
-  xs = mixed ? y : x;
+  xs = mixed ? y : (il ? x_il : x);
   bb_field = mixed ? b64 : b;
   scratch_hi = mixed ? tmp64 : t;
   const SolveOp Op = A();
 
+  if (il) TM_TRY(il_convert(g, eta_il, eta, nrhs, true, s));
+  const void* eta_in = il ? eta_il : eta;
   // b = Op^dag eta (Schur: Op^dag eta_hat), |b|^2
   {
-    const void* src = eta;
+    const void* src = eta_in;
     if (schur) {
-      TM_TRY(Op.prepare(hi, eta, scratch_hi));
+      TM_TRY(Op.prepare(hi, eta_in, scratch_hi));
       src = scratch_hi;
     }
     DslashCall e;
@@ -430,6 +442,7 @@ tm_status_t CgRun::setup() {
       e.in = src;
       e.nrhs = nrhs;
       e.dagger = true;
+      e.il = il;
       TM_TRY(dslash_dispatch(op, hi, e, s));
     }
     TM_TRY(reduce());
@@ -441,7 +454,7 @@ tm_status_t CgRun::setup() {
     TM_TRY(memset_d(y, F, s));
   } else {
     TM_TRY(memcpy_d2d(r, b, F, s));
-    TM_TRY(memset_d(x, F, s));
+    TM_TRY(memset_d(xs, F, s));
   }
   TM_TRY(memcpy_d2d(p, r, F, s));
   return TM_OK;
@@ -475,16 +488,22 @@ tm_status_t CgRun::iteration() {
     TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
     TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s));
   }
+  if (il) return il_xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s);
   return xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s);
 }
 
 tm_status_t CgRun::poll() const {
-  if (cudaMemcpyAsync(op->host_flags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+  if (cudaMemcpyAsync(op->host_flags, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (il && cudaMemcpyAsync(op->host_flags + nrhs, op->il_err, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                 cudaSuccess)) {
     set_error("tm_cg_solve: %s", cudaGetErrorString(cudaGetLastError()));
     return TM_ERR_CUDA;
   }
   return TM_OK;
 }
+
+// a bounded wait of the interleaved Dslash gave up (flag copied by poll())
+bool CgRun::timed_out() const { return il && op->host_flags[nrhs] != 0; }
 
 bool CgRun::any_active() const {
   for (int i = 0; i < nrhs; ++i)
@@ -524,7 +543,7 @@ tm_status_t CgRun::finish(tm_status_t* worst_out) {
   if (recompute) {
     void* tmp = mixed ? tmp64 : t;
     void* res = mixed ? r64 : r;
-    TM_TRY(Op.apply(hi, x, tmp, nullptr, nullptr));
+    TM_TRY(Op.apply(hi, mixed ? x : xs, tmp, nullptr, nullptr));
     DslashCall e4;
     e4.out = res; e4.b = bb_field; e4.epi = EPI_RESID; e4.partial = partial;
     TM_TRY(Op.apply_dag(hi, tmp, e4));
@@ -535,7 +554,8 @@ tm_status_t CgRun::finish(tm_status_t* worst_out) {
       return TM_ERR_CUDA;
     }
   }
-  if (schur) TM_TRY(Op.reconstruct(hi, eta, x));
+  if (schur) TM_TRY(Op.reconstruct(hi, il ? eta_il : eta, mixed ? x : xs));
+  if (il) TM_TRY(il_convert(g, x, x_il, nrhs, false, s));
   const bool want_true = mixed || prm.true_residual;
   tm_status_t worst = TM_OK;
   for (int i = 0; i < nrhs; ++i) {
@@ -705,7 +725,13 @@ static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* p
     }
     done += k;
     bool any = false;
-    for (const auto& run : runs) any = any || run.any_active();
+    for (const auto& run : runs) {
+      if (run.timed_out()) {
+        set_error("tm_cg_solve: a bounded wait of the interleaved Dslash gave up");
+        return TM_ERR_TIMEOUT;
+      }
+      any = any || run.any_active();
+    }
     if (!any) break;
   }
 

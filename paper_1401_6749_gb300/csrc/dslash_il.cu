@@ -1,0 +1,999 @@
+// FP16/BF16 Dslash on the tensor cores, on a system-interleaved field layout.
+//
+// Layout IL16 ("interleaved"): a set of nrhs 16-bit spinor fields stored as
+// ceil(nrhs / 16) blocks of 16 systems,
+//   [block][parity][cb][k = 3 spin + colour][slot 0..15] x 4 bytes,
+// one complex number (re in the low half) per slot, 64 bytes per (site, k)
+// and 768 contiguous bytes per site.  Systems j and j + 8 (j = 0..7), the two
+// a tensor-core lane needs, share one 8-byte pair of slots, at pair position
+// j in rows k = 0, 1 (mod 3) and j ^ 4 in rows k = 2 (mod 3): the XOR keeps
+// the three colour rows a warp reads at once in distinct shared-memory banks.
+// Slots of systems beyond nrhs are zero after tm_spinor_to_il.
+//
+// Every hop of a site is a small dense contraction over the 16 systems: with
+// the spin projection h_s = psi_s + SGN i^ak psi_{2+ac} (s = 0, 1; the upper
+// rows of (1 + SGN g_mu), DeGrand-Rossi basis) of the neighbour,
+//   upper spins  out_s     += W_f h_f,s + W_b h_b,s
+//   lower spins  out_{2+r} += SF i^bk_r W_f h_f,bc_r + SB i^bk_r W_b h_b,bc_r
+// (W_f = U_mu(x), W_b = U_mu(x - mu)^dag, SF / SB the forward / backward
+// projection signs, B_mu the lower-left block of g_mu).  One
+// mma.sync.m16n8k16 (FP32 accumulation) per output spin and direction takes
+//   A[system][(hop, colour, re/im)] = the projected words h (rows = systems),
+//   B[(hop, colour, re/im)][(colour', re/im)] = the real form of the phased
+//     links, forward hop in k = 0..7 and backward hop in k = 8..15,
+// so the forward and backward hops of a direction are one product and the
+// accumulators stay in registers across the four directions: 16 MMAs per
+// site for 16 systems.  Lane (g, t) of a warp holds A rows g and g + 8 at
+// colour t (one 8-byte load per spin and hop straight from the layout), B
+// column g (output colour g/2, part g&1) at colour t (one link word per hop,
+// rotated by a lane-dependent phase so that every B word is a fixed swap or
+// sign flip of it), and D rows g, g + 8 at output colour t: exactly the words
+// it loads and stores in the epilogue.  Nothing goes through shared memory.
+//
+// A block of four warps takes 32 consecutive sites of one parity and one
+// block of systems, warp q the sites q, q + 4, ..., q + 28; blocks are
+// dispatched in site order with the systems' blocks fastest and live briefly,
+// so the sites in flight at one time are few and adjacent and their
+// neighbours meet in L2 (as in the CUDA-core kernel).  Lane i computes the
+// neighbour indices of the block's site i once; the loop broadcasts them.
+// Every load of a site (eight neighbours, eight links, the centre field) is
+// issued before any of its products, so that a warp has the whole site in
+// flight at once.  The block writes one partial sum per system and 32 sites
+// (FP32 per warp, then FP64 over the lanes and the warps in a fixed order),
+// in the per-warp layout of the CUDA-core kernel.  A system's result depends only on
+// its own MMA row: rows do not mix in the products, and the per-lane sums run
+// in a fixed order, whatever the other systems of the block are.
+#include <atomic>
+#include <cstdlib>
+#include <mutex>
+
+#include "tm_host.h"
+
+namespace tml {
+
+constexpr int kIlRows = 16;   // systems per interleaved block (MMA rows)
+constexpr int kIlWarps = 4;   // warps per block
+
+static std::atomic<int> g_il_on{-1};
+
+bool cg_il_on() {
+  int v = g_il_on.load();
+  if (v < 0) {
+    const char* e = getenv("TM_CG_IL");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_il_on.store(v);
+  }
+  return v != 0;
+}
+
+size_t il_bytes(const Geom& g, int nrhs) {
+  const size_t nblk = (size_t)((nrhs + kIlRows - 1) / kIlRows);
+  return nblk * 2 * (size_t)g.Vh * 12 * kIlRows * 4;
+}
+
+// ----------------------------------------------------------- 16-bit words
+template <class S> struct H16;
+template <> struct H16<__half> {
+  static constexpr unsigned kMinusPlus = 0x3C00BC00u;  // (re -1, im +1)
+  static constexpr unsigned kPlusMinus = 0xBC003C00u;  // (re +1, im -1)
+  static __device__ __forceinline__ unsigned add(unsigned a, unsigned b) {
+    unsigned d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+  }
+  static __device__ __forceinline__ unsigned sub(unsigned a, unsigned b) {
+    unsigned d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+  }
+  static __device__ __forceinline__ unsigned fma(unsigned a, unsigned b, unsigned c) {
+    unsigned d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+  }
+  static __device__ __forceinline__ float2 to_f2(unsigned w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  }
+  static __device__ __forceinline__ unsigned pack(float re, float im) {
+    const __half2 h = __floats2half2_rn(re, im);
+    return *reinterpret_cast<const unsigned*>(&h);
+  }
+};
+template <> struct H16<__nv_bfloat16> {
+  static constexpr unsigned kMinusPlus = 0x3F80BF80u;
+  static constexpr unsigned kPlusMinus = 0xBF803F80u;
+  static __device__ __forceinline__ unsigned add(unsigned a, unsigned b) {
+    unsigned d;
+    asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+  }
+  static __device__ __forceinline__ unsigned sub(unsigned a, unsigned b) {
+    unsigned d;
+    asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+  }
+  static __device__ __forceinline__ unsigned fma(unsigned a, unsigned b, unsigned c) {
+    unsigned d;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+  }
+  static __device__ __forceinline__ float2 to_f2(unsigned w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  static __device__ __forceinline__ unsigned pack(float re, float im) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    return *reinterpret_cast<const unsigned*>(&h);
+  }
+};
+
+// a + i^K b, rounded once to the storage format (the phase is exact: a swap
+// of halves and a sign, as a product by (+-1, +-1) inside one packed FMA)
+template <int K, class S>
+__device__ __forceinline__ unsigned proj_w(unsigned a, unsigned b) {
+  constexpr int k = ((K % 4) + 4) % 4;
+  if constexpr (k == 0) return H16<S>::add(a, b);
+  else if constexpr (k == 2) return H16<S>::sub(a, b);
+  else if constexpr (k == 1) return H16<S>::fma(__byte_perm(b, 0u, 0x1032), H16<S>::kMinusPlus, a);
+  else return H16<S>::fma(__byte_perm(b, 0u, 0x1032), H16<S>::kPlusMinus, a);
+}
+
+// i^K times a 16-bit complex word: swap halves and flip signs, exact
+template <int K>
+__device__ __forceinline__ unsigned il_rot(unsigned h) {
+  constexpr int k = ((K % 4) + 4) % 4;
+  if constexpr (k == 0) return h;
+  else if constexpr (k == 2) return h ^ 0x80008000u;
+  else if constexpr (k == 1) return __byte_perm(h, 0u, 0x1032) ^ 0x00008000u;  // (-im, re)
+  else return __byte_perm(h, 0u, 0x1032) ^ 0x80000000u;                        // (im, -re)
+}
+
+template <class S>
+__device__ __forceinline__ void il_mma(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                       unsigned b0, unsigned b1) {
+  if constexpr (std::is_same<S, __half>::value)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  else
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// A-side phases: the DeGrand-Rossi gamma_mu = [[0, A_mu], [B_mu, 0]] as
+// (column, i^k) per row of A_mu and B_mu
+template <int MU> struct IlG;
+template <> struct IlG<0> { static constexpr int ac0 = 1, ak0 = 1, ac1 = 0, ak1 = 1, bc0 = 1, bk0 = 3, bc1 = 0, bk1 = 3; };
+template <> struct IlG<1> { static constexpr int ac0 = 1, ak0 = 2, ac1 = 0, ak1 = 0, bc0 = 1, bk0 = 0, bc1 = 0, bk1 = 2; };
+template <> struct IlG<2> { static constexpr int ac0 = 0, ak0 = 1, ac1 = 1, ak1 = 3, bc0 = 0, bk0 = 3, bc1 = 1, bk1 = 1; };
+template <> struct IlG<3> { static constexpr int ac0 = 0, ak0 = 0, ac1 = 1, ak1 = 0, bc0 = 0, bk0 = 0, bc1 = 1, bk1 = 0; };
+
+struct IlArgs {
+  Geom g;
+  const void* links_il;   // links in the site-major layout [par][cb][mu][12 words]
+  int* err;               // set to 1 when a staging wait gave up
+  const uint2* in;
+  uint2* out;
+  const uint2* cfield;    // centre field (null: in)
+  const uint2* p;
+  uint2* x;
+  uint2* r;
+  const uint2* b;
+  const int* active;
+  const double* alpha;
+  double* partial;
+  int* trace_count;
+  int nrhs, nblk, parity, nwarp;
+  int centre, out_inv, g5_out;
+  float nu, shop, inv;
+};
+
+// per-lane constants of a warp
+struct IlLane {
+  int gq, tq;
+  bool ld;         // lane loads spinor words (colour t < 3)
+  bool lw;         // lane holds a link entry (t < 3, output colour g/2 < 3)
+  unsigned psel;   // lane phase of the link words: swap halves on odd columns
+  unsigned pmf, pmb;
+};
+
+// Words of one site in uint2 units: site cb of parity par in block blk starts
+// at ((blk * 2 + par) * Vh + cb) * 96; lane (g, t) reads spin s at + (3 s + t) * 8 + g.
+constexpr int kIlSiteU2 = 96;
+
+// One direction: both hops of 16 systems into the four spin accumulators,
+// from the loaded neighbour words pf / pb (spins 0..3, systems g and g + 8)
+// and link words uf / ub; negf / negb the antiperiodic signs (0 or 0x80008000).
+template <class S, int MU, int SF>
+__device__ __forceinline__ void il_dir(float (&d)[4][4], const IlLane& l, const uint2 (&pf)[4],
+                                       const uint2 (&pb)[4], unsigned uf, unsigned ub, unsigned negf,
+                                       unsigned negb) {
+  using G = IlG<MU>;
+  constexpr int SB = -SF;
+  constexpr int pf2 = SF < 0 ? 2 : 0, pb2 = SB < 0 ? 2 : 0;
+  // lane phase (odd columns: forward words times -i, backward words times +i)
+  // and the time-boundary sign; every B word below is then a fixed rotation
+  uf = __byte_perm(uf, 0u, l.psel) ^ l.pmf ^ negf;
+  ub = __byte_perm(ub, 0u, l.psel) ^ l.pmb ^ negb;
+  // projected words (rows g, g + 8) of the two upper spins for both hops
+  const unsigned h0f0 = proj_w<G::ak0 + pf2, S>(pf[0].x, pf[2 + G::ac0].x);
+  const unsigned h0f1 = proj_w<G::ak0 + pf2, S>(pf[0].y, pf[2 + G::ac0].y);
+  const unsigned h0b0 = proj_w<G::ak0 + pb2, S>(pb[0].x, pb[2 + G::ac0].x);
+  const unsigned h0b1 = proj_w<G::ak0 + pb2, S>(pb[0].y, pb[2 + G::ac0].y);
+  const unsigned h1f0 = proj_w<G::ak1 + pf2, S>(pf[1].x, pf[2 + G::ac1].x);
+  const unsigned h1f1 = proj_w<G::ak1 + pf2, S>(pf[1].y, pf[2 + G::ac1].y);
+  const unsigned h1b0 = proj_w<G::ak1 + pb2, S>(pb[1].x, pb[2 + G::ac1].x);
+  const unsigned h1b1 = proj_w<G::ak1 + pb2, S>(pb[1].y, pb[2 + G::ac1].y);
+  // B words: forward conj(i^k u), backward i^-k u (k: phase of W)
+  const unsigned bf_up = uf ^ 0x80000000u, bb_up = ub;
+  const unsigned bf_l0 = il_rot<G::bk0 + pf2>(uf) ^ 0x80000000u, bb_l0 = il_rot<-(G::bk0 + pb2)>(ub);
+  const unsigned bf_l1 = il_rot<G::bk1 + pf2>(uf) ^ 0x80000000u, bb_l1 = il_rot<-(G::bk1 + pb2)>(ub);
+  il_mma<S>(d[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
+  il_mma<S>(d[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
+  if constexpr (G::bc0 == 0) il_mma<S>(d[2], h0f0, h0f1, h0b0, h0b1, bf_l0, bb_l0);
+  else il_mma<S>(d[2], h1f0, h1f1, h1b0, h1b1, bf_l0, bb_l0);
+  if constexpr (G::bc1 == 0) il_mma<S>(d[3], h0f0, h0f1, h0b0, h0b1, bf_l1, bb_l1);
+  else il_mma<S>(d[3], h1f0, h1f1, h1b0, h1b1, bf_l1, bb_l1);
+}
+
+// store one 8-byte pair of words, only the halves of active systems
+__device__ __forceinline__ void il_store(uint2* p, unsigned w0, unsigned w1, bool a0, bool a1) {
+  if (a0 && a1) *p = make_uint2(w0, w1);
+  else if (a0) reinterpret_cast<unsigned*>(p)[0] = w0;
+  else if (a1) reinterpret_cast<unsigned*>(p)[1] = w1;
+}
+
+// ------------------------------------------------- staging (TMA, mbarrier)
+// Each warp owns a ring of two stages in shared memory; a stage holds what
+// the hops of one output site need: its eight neighbour sites (768 bytes
+// each, copied whole), its forward links (4 directions x 48 bytes) and the
+// four backward links.  One bulk asynchronous copy (cp.async.bulk) per block,
+// each issued by its own lane in one instruction, completes on the stage's
+// mbarrier, whose expected byte count lane 0 posts; every lane waits on the
+// barrier's phase before reading its words.  The copies of site m + 1 are in
+// flight while site m is computed.  The words of the output site itself
+// (centre, residual, solution, search direction) are read straight into
+// registers, issued right after the previous site's epilogue.
+constexpr int kIlSiteBytes = 768;
+constexpr int kIlLinkBytes = 48;                 // one direction of one site: 9 words + 3 pad
+constexpr int kIlLinkSiteBytes = 4 * kIlLinkBytes;
+constexpr int kIlGroups = 4;                     // 32-site groups per block (128 sites)
+constexpr unsigned kIlWaitLimit = 1u << 22;      // try_wait rounds before a wait gives up
+
+template <int EPI>
+struct IlStage {
+  static constexpr int kLinkOff = 8 * kIlSiteBytes;               // after the eight neighbours
+  static constexpr int kBytes = kLinkOff + 2 * kIlLinkSiteBytes;  // forward site links + 4 backward
+  static constexpr int kStages = 2;
+  static constexpr int kWarpBytes = kStages * kBytes;
+  static constexpr int kSmem = kIlWarps * kWarpBytes;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar), "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// bounded wait for a stage; false (and the launch's error flag set) if it gave up
+__device__ __forceinline__ bool il_wait(unsigned bar, unsigned phase, int* err) {
+  for (unsigned it = 0; it < kIlWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+template <class S, bool DAG, int EPI>
+__global__ void __launch_bounds__(kIlWarps * 32, 4) dslash_il_kernel(const IlArgs a) {
+  using H = H16<S>;
+  using ST = IlStage<EPI>;
+  extern __shared__ __align__(128) unsigned char il_smem[];
+  __shared__ __align__(8) unsigned long long bars[kIlWarps][ST::kStages];
+  __shared__ float red[kIlWarps][kIlGroups][kIlRows];
+  const Geom& g = a.g;
+  const int lane = threadIdx.x & 31;
+  const int wq = threadIdx.x >> 5;
+  const int blk = blockIdx.x % a.nblk;
+  const int rest = blockIdx.x / a.nblk;
+  if (a.trace_count && blockIdx.x == 0 && threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < a.nrhs; ++r) n += (a.active == nullptr || a.active[r] != 0) ? 1 : 0;
+    *a.trace_count = n;
+  }
+  // both parities: alternate them block by block (the centre reads of one are
+  // the neighbour reads of the other)
+  const int par = a.parity < 0 ? (rest & 1) : a.parity;
+  const int cg = a.parity < 0 ? (rest >> 1) : rest;  // the block's 128-site chunk
+  const int opar = par ^ 1;
+  IlLane l;
+  l.gq = lane >> 2;
+  l.tq = lane & 3;
+  const int r0 = blk * kIlRows + l.gq, r1 = r0 + 8;
+  const bool act0 = r0 < a.nrhs && (a.active == nullptr || a.active[r0] != 0);
+  const bool act1 = r1 < a.nrhs && (a.active == nullptr || a.active[r1] != 0);
+  const bool want_norm = EPI != EPI_OUT || a.partial != nullptr;
+  if (lane == 0) {
+#pragma unroll
+    for (int st = 0; st < ST::kStages; ++st) mbar_init(smem_u32(&bars[wq][st]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < kIlWarps * kIlGroups * kIlRows; i += blockDim.x) (&red[0][0][0])[i] = 0.0f;
+  __syncthreads();
+  const size_t Vh = (size_t)g.Vh;
+  const int base = cg * (kIlGroups * 32);
+  // sites of this warp: base + wq + 4 m, m = 0 .. nsite - 1
+  const int left = g.Vh - base - wq;
+  const int nsite = left <= 0 ? 0 : min(32, (left + kIlWarps - 1) / kIlWarps);
+  if (__any_sync(0xffffffffu, act0 || act1) && nsite > 0) {
+    // lane m: the warp's site m (lex index, coordinates, time-boundary flags)
+    int lexl = 0;
+    unsigned c01 = 0u, c23 = 0u, bfl = 0u;
+    if (lane < nsite) {
+      const Site s = site_of(g, par, base + wq + kIlWarps * lane);
+      lexl = s.lex;
+      c01 = (unsigned)s.c[0] | ((unsigned)s.c[1] << 16);
+      c23 = (unsigned)s.c[2] | ((unsigned)s.c[3] << 16);
+      if (g.antiperiodic) bfl = (s.c[3] == g.L[3] - 1 ? 1u : 0u) | (s.c[3] == 0 ? 2u : 0u);
+    }
+    const size_t obase = ((size_t)blk * 2 + par) * Vh * kIlSiteBytes;
+    // copy role of this lane (one bulk copy per lane and site): lanes 0..7 the
+    // neighbours (direction lane / 2, forward for even lanes), 9 the forward
+    // links, 10..13 the backward link of direction lane - 10; src = rbase +
+    // index * rmul, index the neighbour's or the site's checkerboard index
+    const int rmu = lane < 8 ? (lane >> 1) : (lane >= 10 && lane < 14 ? lane - 10 : 0);
+    const bool rbwd = lane < 8 ? (lane & 1) != 0 : true;
+    const bool rnb = lane < 8 || (lane >= 10 && lane < 14);
+    const int rstride = g.stride[rmu], rL = g.L[rmu];
+    const int rsh = (rmu & 1) ? 16 : 0;
+    const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il);
+    const unsigned char* rbase = nullptr;
+    unsigned rmul = kIlSiteBytes, rdoff = 0, rbytes = 0;
+    if (lane < 8) {
+      rbase = reinterpret_cast<const unsigned char*>(a.in) + ((size_t)blk * 2 + opar) * Vh * kIlSiteBytes;
+      rdoff = lane * kIlSiteBytes;
+      rbytes = kIlSiteBytes;
+    } else if (lane == 9) {
+      rbase = lk + (size_t)par * Vh * kIlLinkSiteBytes;
+      rmul = kIlLinkSiteBytes;
+      rdoff = ST::kLinkOff;
+      rbytes = kIlLinkSiteBytes;
+    } else if (lane >= 10 && lane < 14) {
+      rbase = lk + (size_t)opar * Vh * kIlLinkSiteBytes + rmu * kIlLinkBytes;
+      rmul = kIlLinkSiteBytes;
+      rdoff = ST::kLinkOff + kIlLinkSiteBytes + rmu * kIlLinkBytes;
+      rbytes = kIlLinkBytes;
+    }
+    l.ld = l.tq < 3;
+    l.lw = l.tq < 3 && l.gq < 6;
+    const bool odd = (l.gq & 1) != 0;
+    l.psel = odd ? 0x1032u : 0x3210u;
+    l.pmf = odd ? 0x80000000u : 0u;
+    l.pmb = odd ? 0x00008000u : 0u;
+    // lane offsets in a stage: spinor words (3 s + t) * 64 + pair * 8 (pair
+    // position g, XOR 4 on colour 2).  Lanes t = 3 (no colour) read the words
+    // of t = 0: finite values against the zero B rows of colour 3.
+    const int teff = l.tq < 3 ? l.tq : 0;
+    const int woff = teff * 64 + ((teff == 2 ? l.gq ^ 4 : l.gq) * 8);
+    const int lf_off = (3 * (l.gq >> 1) + l.tq) * 4, lb_off = (3 * l.tq + (l.gq >> 1)) * 4;
+    const float nu = a.nu, shop = a.shop, inv = a.inv;
+    float al0 = 0.0f, al1 = 0.0f;
+    if constexpr (EPI == EPI_CGUPD) {
+      al0 = act0 ? (float)a.alpha[r0] : 0.0f;
+      al1 = act1 ? (float)a.alpha[r1] : 0.0f;
+    }
+    unsigned char* ring = il_smem + wq * ST::kWarpBytes;
+    const unsigned ring_s = smem_u32(ring);
+    const unsigned bar0 = smem_u32(&bars[wq][0]);
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr unsigned total = 8 * kIlSiteBytes + kIlLinkSiteBytes + 4 * kIlLinkBytes;
+    // the output site's own words (centre, r, x, p or b), straight into registers
+    const uint2* cf = a.cfield ? a.cfield : a.in;
+    uint2 cw[4], rw[4], xw[4], pw[4];
+    auto fetch_site = [&](int m) {
+      const size_t w = (obase + (size_t)(base + wq + kIlWarps * m) * kIlSiteBytes + woff) / 8;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (a.centre != 0) cw[s] = cf[w + 24 * s];
+        if constexpr (EPI == EPI_CGUPD) {
+          rw[s] = a.r[w + 24 * s];
+          xw[s] = a.x[w + 24 * s];
+          pw[s] = a.p[w + 24 * s];
+        } else if constexpr (EPI == EPI_RESID) {
+          rw[s] = a.b[w + 24 * s];
+        }
+      }
+    };
+    // issue the copies of the warp's site m into stage st: every lane computes
+    // its block's address and one bulk-copy instruction moves them all
+    auto issue = [&](int m, int st) {
+      const int lex = __shfl_sync(0xffffffffu, lexl, m);
+      const unsigned w01 = __shfl_sync(0xffffffffu, c01, m), w23 = __shfl_sync(0xffffffffu, c23, m);
+      const int cm = (int)(((rmu < 2 ? w01 : w23) >> rsh) & 0xffffu);
+      const int nlex = rbwd ? (cm > 0 ? lex - rstride : lex + (rL - 1) * rstride)
+                            : (cm + 1 < rL ? lex + rstride : lex - (rL - 1) * rstride);
+      const int idx = rnb ? (nlex >> 1) : base + wq + kIlWarps * m;
+      const unsigned bar = bar0 + st * 8;
+      // the stage was last read by this warp (generic proxy): order those reads
+      // before the copies' writes (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) mbar_expect_tx(bar, total);
+      if (rbytes) bulk_g2s(ring_s + st * ST::kBytes + rdoff, rbase + (size_t)idx * rmul, rbytes, bar);
+    };
+#pragma unroll
+    for (int st = 0; st < ST::kStages - 1; ++st)
+      if (st < nsite) issue(st, st);
+    fetch_site(0);
+    float nacc0 = 0.0f, nacc1 = 0.0f;  // norms of the current 32-site group
+    for (int m = 0; m < nsite; ++m) {
+      const int st = m % ST::kStages;
+      if (m + ST::kStages - 1 < nsite) issue(m + ST::kStages - 1, (m + ST::kStages - 1) % ST::kStages);
+      const unsigned bf = __shfl_sync(0xffffffffu, bfl, m);
+      if (!__all_sync(0xffffffffu, il_wait(bar0 + st * 8, (unsigned)((m / ST::kStages) & 1), a.err))) {
+        // a wait gave up: wait (bounded) for this warp's copies still in
+        // flight (sites m .. m + kStages - 2), then stop
+        for (int mm = m; mm < min(m + ST::kStages - 1, nsite); ++mm)
+          il_wait(bar0 + (mm % ST::kStages) * 8, (unsigned)((mm / ST::kStages) & 1), nullptr);
+        break;
+      }
+      const unsigned char* sd = ring + st * ST::kBytes;
+      // two accumulator sets (directions 0, 1 and 2, 3): shorter MMA chains
+      float d[4][4], e[4][4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[s][q] = e[s][q] = 0.0f;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        uint2 pf[4], pb[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          pf[s] = *reinterpret_cast<const uint2*>(sd + (2 * mu) * kIlSiteBytes + woff + 192 * s);
+          pb[s] = *reinterpret_cast<const uint2*>(sd + (2 * mu + 1) * kIlSiteBytes + woff + 192 * s);
+        }
+        const unsigned uf = l.lw ? *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off) : 0u;
+        const unsigned ub = l.lw ? *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + kIlLinkSiteBytes + mu * kIlLinkBytes + lb_off) : 0u;
+        const unsigned negf = (mu == 3 && (bf & 1u)) ? 0x80008000u : 0u;
+        const unsigned negb = (mu == 3 && (bf & 2u)) ? 0x80008000u : 0u;
+        if (mu == 0) il_dir<S, 0, SF>(d, l, pf, pb, uf, ub, negf, negb);
+        else if (mu == 1) il_dir<S, 1, SF>(e, l, pf, pb, uf, ub, negf, negb);
+        else if (mu == 2) il_dir<S, 2, SF>(d, l, pf, pb, uf, ub, negf, negb);
+        else il_dir<S, 3, SF>(e, l, pf, pb, uf, ub, negf, negb);
+      }
+      // epilogue: out = T_out(T_c(c) + s_hop H in), then the CG update / residual
+      const size_t wsite = (obase + (size_t)(base + wq + kIlWarps * m) * kIlSiteBytes + woff) / 8;
+      float n0 = 0.0f, n1 = 0.0f;
+      if (l.ld) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const size_t wi = wsite + 24 * s;
+          const float tw = s < 2 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
+          const float h0r = __fadd_rn(d[s][0], e[s][0]), h0i = __fadd_rn(d[s][1], e[s][1]);
+          const float h1r = __fadd_rn(d[s][2], e[s][2]), h1i = __fadd_rn(d[s][3], e[s][3]);
+          float2 o0, o1;
+          if (a.centre != 0) {
+            const uint2 c = cw[s];
+            float2 c0 = H::to_f2(c.x), c1 = H::to_f2(c.y);
+            if (a.centre == 2) {
+              c0 = make_float2(__fmaf_rn(-tw, c0.y, c0.x), __fmaf_rn(tw, c0.x, c0.y));
+              c1 = make_float2(__fmaf_rn(-tw, c1.y, c1.x), __fmaf_rn(tw, c1.x, c1.y));
+            }
+            o0 = make_float2(__fmaf_rn(shop, h0r, c0.x), __fmaf_rn(shop, h0i, c0.y));
+            o1 = make_float2(__fmaf_rn(shop, h1r, c1.x), __fmaf_rn(shop, h1i, c1.y));
+          } else {
+            o0 = make_float2(__fmul_rn(shop, h0r), __fmul_rn(shop, h0i));
+            o1 = make_float2(__fmul_rn(shop, h1r), __fmul_rn(shop, h1i));
+          }
+          if (a.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
+            o0 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o0.y, o0.x)), __fmul_rn(inv, __fmaf_rn(-tw, o0.x, o0.y)));
+            o1 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o1.y, o1.x)), __fmul_rn(inv, __fmaf_rn(-tw, o1.x, o1.y)));
+          }
+          if constexpr (EPI == EPI_OUT) {
+            if (a.g5_out && s >= 2) {
+              o0 = make_float2(-o0.x, -o0.y);
+              o1 = make_float2(-o1.x, -o1.y);
+            }
+            // every system's output (inactive and padding systems get the
+            // operator applied to their own unchanged input)
+            a.out[wi] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
+            if (want_norm) {
+              n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
+              n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+            }
+          } else if constexpr (EPI == EPI_CGUPD) {
+            // r and x of inactive systems keep their bits
+            float2 q0 = H::to_f2(rw[s].x), q1 = H::to_f2(rw[s].y);
+            q0 = make_float2(__fmaf_rn(-al0, o0.x, q0.x), __fmaf_rn(-al0, o0.y, q0.y));
+            q1 = make_float2(__fmaf_rn(-al1, o1.x, q1.x), __fmaf_rn(-al1, o1.y, q1.y));
+            a.r[wi] = make_uint2(act0 ? H::pack(q0.x, q0.y) : rw[s].x, act1 ? H::pack(q1.x, q1.y) : rw[s].y);
+            n0 = __fmaf_rn(q0.x, q0.x, n0); n0 = __fmaf_rn(q0.y, q0.y, n0);
+            n1 = __fmaf_rn(q1.x, q1.x, n1); n1 = __fmaf_rn(q1.y, q1.y, n1);
+            const float2 x0 = H::to_f2(xw[s].x), x1 = H::to_f2(xw[s].y), p0 = H::to_f2(pw[s].x), p1 = H::to_f2(pw[s].y);
+            a.x[wi] = make_uint2(act0 ? H::pack(__fmaf_rn(al0, p0.x, x0.x), __fmaf_rn(al0, p0.y, x0.y)) : xw[s].x,
+                                 act1 ? H::pack(__fmaf_rn(al1, p1.x, x1.x), __fmaf_rn(al1, p1.y, x1.y)) : xw[s].y);
+          } else {  // EPI_RESID: out = b - D in
+            const float2 b0 = H::to_f2(rw[s].x), b1 = H::to_f2(rw[s].y);
+            o0 = make_float2(__fsub_rn(b0.x, o0.x), __fsub_rn(b0.y, o0.y));
+            o1 = make_float2(__fsub_rn(b1.x, o1.x), __fsub_rn(b1.y, o1.y));
+            a.out[wi] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
+            n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
+            n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+          }
+        }
+      }
+      if (want_norm) {
+        if (act0) nacc0 = __fadd_rn(nacc0, n0);
+        if (act1) nacc1 = __fadd_rn(nacc1, n1);
+        // site base + wq + 4 m lies in 32-site group m / 8: flush at the group's end
+        if ((m & 7) == 7 || m == nsite - 1) {
+          nacc0 = __fadd_rn(nacc0, __shfl_xor_sync(0xffffffffu, nacc0, 1));
+          nacc0 = __fadd_rn(nacc0, __shfl_xor_sync(0xffffffffu, nacc0, 2));
+          nacc1 = __fadd_rn(nacc1, __shfl_xor_sync(0xffffffffu, nacc1, 1));
+          nacc1 = __fadd_rn(nacc1, __shfl_xor_sync(0xffffffffu, nacc1, 2));
+          if (l.tq == 0) {
+            red[wq][m >> 3][l.gq] = nacc0;
+            red[wq][m >> 3][l.gq + 8] = nacc1;
+          }
+          nacc0 = nacc1 = 0.0f;
+        }
+      }
+      if (m + 1 < nsite) fetch_site(m + 1);
+      __syncwarp();  // every lane is done with the stage before it is refilled
+    }
+  }
+  if (want_norm) {
+    // the warps' sums of each 32-site group, fixed order
+    __syncthreads();
+    if (threadIdx.x < kIlGroups * kIlRows) {
+      const int j = threadIdx.x / kIlRows, sy = threadIdx.x % kIlRows;
+      const int r = blk * kIlRows + sy;
+      const int grp = cg * kIlGroups + j;
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < kIlWarps; ++q) t += (double)red[q][j][sy];
+      if (r < a.nrhs && grp < a.nwarp) a.partial[((size_t)r * 2 + par) * a.nwarp + grp] = t;
+    }
+  }
+}
+
+template <class S, bool DAG, int EPI>
+static tm_status_t il_prepare_t() {
+  const cudaError_t e = cudaFuncSetAttribute(dslash_il_kernel<S, DAG, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             IlStage<EPI>::kSmem);
+  if (e != cudaSuccess) {
+    set_error("dslash_il: shared-memory limit: %s", cudaGetErrorString(e));
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
+// raise the dynamic shared-memory limit of every instantiation (once)
+tm_status_t il_prepare() {
+  static std::mutex mu;
+  static bool done = false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done) return TM_OK;
+  TM_TRY((il_prepare_t<__half, false, EPI_OUT>()));
+  TM_TRY((il_prepare_t<__half, false, EPI_CGUPD>()));
+  TM_TRY((il_prepare_t<__half, false, EPI_RESID>()));
+  TM_TRY((il_prepare_t<__half, true, EPI_OUT>()));
+  TM_TRY((il_prepare_t<__half, true, EPI_CGUPD>()));
+  TM_TRY((il_prepare_t<__half, true, EPI_RESID>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_OUT>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_CGUPD>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_RESID>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_OUT>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_CGUPD>()));
+  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_RESID>()));
+  done = true;
+  return TM_OK;
+}
+
+template <class S, bool DAG, int EPI>
+static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_t st, tm_prec_t prec) {
+  IlArgs a{};
+  const Geom& g = op->g;
+  a.g = g;
+  a.links_il = op->links_il[prec];
+  a.err = op->il_err;
+  a.in = static_cast<const uint2*>(c.in);
+  a.out = static_cast<uint2*>(c.out);
+  a.cfield = static_cast<const uint2*>(c.cfield);
+  a.p = static_cast<const uint2*>(c.p);
+  a.x = static_cast<uint2*>(c.x);
+  a.r = static_cast<uint2*>(c.r);
+  a.b = static_cast<const uint2*>(c.b);
+  a.active = c.active;
+  a.alpha = c.alpha;
+  a.partial = c.partial;
+  a.nrhs = c.nrhs;
+  a.nblk = (c.nrhs + kIlRows - 1) / kIlRows;
+  a.parity = c.parity;
+  a.nwarp = nwarp_of(g);
+  a.g5_out = c.g5_out ? 1 : 0;
+  double nu, hop;
+  if (c.custom) {
+    nu = c.nu;
+    hop = c.hop_scale;
+    a.centre = c.centre;
+    a.out_inv = c.out_inv ? 1 : 0;
+  } else {
+    nu = c.mu_zero ? 0.0 : (DAG ? -2.0 * op->kappa * op->mu : 2.0 * op->kappa * op->mu);
+    hop = -op->kappa;
+    a.centre = 2;
+    a.cfield = nullptr;
+    a.out_inv = 0;
+  }
+  a.nu = (float)nu;
+  a.shop = (float)hop;
+  a.inv = (float)(1.0 / (1.0 + nu * nu));
+  // every field the bulk copies read must sit on a 16-byte boundary
+  const void* ptrs[6] = {a.in, a.cfield, a.p, a.x, a.r, a.b};
+  for (const void* q : ptrs)
+    if (q && ((uintptr_t)q & 15u)) {
+      set_error("dslash_il: fields must be 16-byte aligned");
+      return TM_ERR_ARG;
+    }
+  const int npar = c.parity < 0 ? 2 : 1;
+  const long chunks = ((long)g.Vh + kIlGroups * 32 - 1) / (kIlGroups * 32);
+  const long blocks = (long)a.nblk * npar * chunks;  // one block per 128 sites and 16 systems
+  if (blocks > 0x7fffffffL) {
+    set_error("dslash_il: launch grid too large");
+    return TM_ERR_ARG;
+  }
+  TM_TRY(il_prepare());
+  static const char* const kNames[2][3] = {{"dslash.f16il.out", "dslash.f16il.cgupd", "dslash.f16il.resid"},
+                                           {"dslash.bf16il.out", "dslash.bf16il.cgupd", "dslash.bf16il.resid"}};
+  const char* name = kNames[std::is_same<S, __half>::value ? 0 : 1][EPI];
+  // algorithmic bytes as for the CUDA-core kernel: per active system the
+  // neighbour field (one parity per output parity), the centre field unless it
+  // is the input read on both parities, the epilogue's streams; per launch the
+  // links of all sites (18 reals)
+  const double e = 2.0;
+  const double out_sites = (double)npar * g.Vh;
+  const bool centre_is_in = a.cfield == nullptr || a.cfield == a.in;
+  const int centre = (a.centre != 0 && !(c.parity < 0 && centre_is_in)) ? 1 : 0;
+  const int epi_streams = EPI == EPI_OUT ? 1 : (EPI == EPI_CGUPD ? 5 : 2);
+  const double per_rhs = out_sites * 24.0 * e * (1 + centre + epi_streams);
+  const double fixed = 4.0 * 2.0 * g.Vh * 18.0 * e;
+  const double site_flops = 1320.0 + 48.0 + (a.centre == 2 ? 48.0 : 0.0) + (a.out_inv ? 72.0 : 0.0) +
+                            (EPI == EPI_CGUPD ? 144.0 : EPI == EPI_RESID ? 72.0 : (a.partial ? 48.0 : 0.0));
+  cudaEvent_t ev = nullptr;
+  a.trace_count = trace_begin(st, &ev);
+  dslash_il_kernel<S, DAG, EPI><<<(unsigned)blocks, kIlWarps * 32, IlStage<EPI>::kSmem, st>>>(a);
+  count_launch();
+  trace_end(st, name, ev, a.trace_count, per_rhs, fixed, 0, out_sites * site_flops);
+  return check_launch("dslash_il");
+}
+
+template <class S>
+static tm_status_t il_launch_s(const tm_op* op, const DslashCall& c, cudaStream_t st, tm_prec_t prec) {
+  if (c.dagger) {
+    switch (c.epi) {
+      case EPI_OUT: return il_launch_t<S, true, EPI_OUT>(op, c, st, prec);
+      case EPI_CGUPD: return il_launch_t<S, true, EPI_CGUPD>(op, c, st, prec);
+      default: return il_launch_t<S, true, EPI_RESID>(op, c, st, prec);
+    }
+  }
+  switch (c.epi) {
+    case EPI_OUT: return il_launch_t<S, false, EPI_OUT>(op, c, st, prec);
+    case EPI_CGUPD: return il_launch_t<S, false, EPI_CGUPD>(op, c, st, prec);
+    default: return il_launch_t<S, false, EPI_RESID>(op, c, st, prec);
+  }
+}
+
+tm_status_t dslash_il_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s) {
+  if (prec != TM_PREC_F16 && prec != TM_PREC_BF16) {
+    set_error("dslash_il: the interleaved layout holds F16 or BF16 fields");
+    return TM_ERR_ARG;
+  }
+  if (op->recon_p[prec] != 18 || !op->links_il[prec] || !op->il_err) {
+    set_error("dslash_il: needs the 18-real 16-bit link copy (recon 18 or 0)");
+    return TM_ERR_UNSUPPORTED;
+  }
+  if (c.nrhs <= 0) return TM_OK;
+  return prec == TM_PREC_F16 ? il_launch_s<__half>(op, c, s, prec) : il_launch_s<__nv_bfloat16>(op, c, s, prec);
+}
+
+// ------------------------------------------------ site-major links
+// [mu][par][unit][cb] (three 16-byte units of the 18-real 16-bit copy, the
+// last word pair zero) -> [par][cb][mu][unit]: one site's forward links are
+// 192 contiguous bytes, one direction 48.
+size_t il_link_bytes(const Geom& g) { return 2 * (size_t)g.Vh * kIlLinkSiteBytes; }
+
+__global__ void il_pack_links_kernel(size_t Vh, uint4* __restrict__ out, const uint4* __restrict__ in) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (par, cb, mu)
+  if (i >= 2 * Vh * 4) return;
+  const int mu = (int)(i & 3);
+  const size_t pc = i >> 2;  // par * Vh + cb
+  const int par = (int)(pc / Vh);
+  const size_t cb = pc % Vh;
+#pragma unroll
+  for (int u = 0; u < 3; ++u) out[i * 3 + u] = in[((size_t)(mu * 2 + par) * 3 + u) * Vh + cb];
+}
+
+tm_status_t il_pack_links(const Geom& g, void* out, const void* links18, cudaStream_t s) {
+  const size_t n = 2 * (size_t)g.Vh * 4;
+  il_pack_links_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((size_t)g.Vh, static_cast<uint4*>(out),
+                                                                    static_cast<const uint4*>(links18));
+  count_launch();
+  return check_launch("interleaved link packing");
+}
+
+// ------------------------------------------------- layout conversions
+// 32 sites x 16 systems per block of 512 threads, through shared memory:
+// reads of the standard layout (warp = system, lane = site: 512 contiguous
+// bytes per chunk) and writes of the interleaved rows (thread = 4-byte slot
+// of 32 consecutive 64-byte rows) are both coalesced.  The 16-bit formats
+// move as bytes; slots of systems >= nrhs are written as zero.
+constexpr int kIlCvSites = 32;
+
+// system (0..15 in its block) held by slot 0..15 of row k of a site
+__device__ __forceinline__ int il_system(int k, int slot) {
+  const int pos = (slot >> 1) ^ (k % 3 == 2 ? 4 : 0);
+  return (slot & 1) ? pos + 8 : pos;
+}
+
+__global__ void __launch_bounds__(512) il_from_std_kernel(Geom g, uint4* __restrict__ out,
+                                                          const uint4* __restrict__ in, int nrhs) {
+  __shared__ unsigned sm[kIlRows][kIlCvSites + 1][13];
+  const int blk = blockIdx.z, par = blockIdx.y;
+  const int cb0 = blockIdx.x * kIlCvSites;
+  const int tid = threadIdx.x;
+  const size_t Vh = (size_t)g.Vh;
+  {
+    const int s = tid >> 5, j = tid & 31;
+    const int r = blk * kIlRows + s;
+    const int cb = cb0 + j;
+    uint4 q[3] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    if (r < nrhs && cb < g.Vh) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c] = in[(((size_t)r * 2 + par) * 3 + c) * Vh + cb];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sm[s][j][4 * c] = q[c].x;
+      sm[s][j][4 * c + 1] = q[c].y;
+      sm[s][j][4 * c + 2] = q[c].z;
+      sm[s][j][4 * c + 3] = q[c].w;
+    }
+  }
+  __syncthreads();
+  // the block's 32 sites are 32 x 192 contiguous words of the interleaved field
+  unsigned* o = reinterpret_cast<unsigned*>(out) + (((size_t)blk * 2 + par) * Vh + cb0) * 192;
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    const int w = tid + 512 * m;
+    const int j = w / 192, k = (w % 192) >> 4, slot = w & 15;
+    const int s = il_system(k, slot);
+    if (cb0 + j < g.Vh) o[w] = sm[s][j][k];
+  }
+}
+
+__global__ void __launch_bounds__(512) il_to_std_kernel(Geom g, uint4* __restrict__ out,
+                                                        const uint4* __restrict__ in, int nrhs) {
+  __shared__ unsigned sm[kIlRows][kIlCvSites + 1][13];
+  const int blk = blockIdx.z, par = blockIdx.y;
+  const int cb0 = blockIdx.x * kIlCvSites;
+  const int tid = threadIdx.x;
+  const size_t Vh = (size_t)g.Vh;
+  {
+    const unsigned* ip = reinterpret_cast<const unsigned*>(in) + (((size_t)blk * 2 + par) * Vh + cb0) * 192;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      const int w = tid + 512 * m;
+      const int j = w / 192, k = (w % 192) >> 4, slot = w & 15;
+      const int s = il_system(k, slot);
+      sm[s][j][k] = cb0 + j < g.Vh ? ip[w] : 0u;
+    }
+  }
+  __syncthreads();
+  const int s = tid >> 5, j = tid & 31;
+  const int r = blk * kIlRows + s;
+  const int cb = cb0 + j;
+  if (r >= nrhs || cb >= g.Vh) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    out[(((size_t)r * 2 + par) * 3 + c) * Vh + cb] =
+        make_uint4(sm[s][j][4 * c], sm[s][j][4 * c + 1], sm[s][j][4 * c + 2], sm[s][j][4 * c + 3]);
+}
+
+tm_status_t il_convert(const Geom& g, void* out, const void* in, int nrhs, bool to_il, cudaStream_t s) {
+  if (nrhs <= 0) return TM_OK;
+  const int nblk = (nrhs + kIlRows - 1) / kIlRows;
+  if (nblk > 65535) {
+    set_error("interleaved layout: too many systems (%d)", nrhs);
+    return TM_ERR_ARG;
+  }
+  const dim3 grid((unsigned)((g.Vh + kIlCvSites - 1) / kIlCvSites), 2, (unsigned)nblk);
+  if (to_il)
+    il_from_std_kernel<<<grid, 512, 0, s>>>(g, static_cast<uint4*>(out), static_cast<const uint4*>(in), nrhs);
+  else
+    il_to_std_kernel<<<grid, 512, 0, s>>>(g, static_cast<uint4*>(out), static_cast<const uint4*>(in), nrhs);
+  count_launch();
+  return check_launch("interleaved layout conversion");
+}
+
+// ------------------------------------------------ solver BLAS on IL16
+// One thread per 8-byte word pair (systems j, j + 8 of one (k, site) row) of
+// the parities par0 .. par0 + npar - 1.
+template <class S>
+__global__ void il_xpay_kernel(size_t Vh, uint2* p, const uint2* r, const double* beta, const int* active,
+                               int nrhs, int nblk, int par0, int npar) {
+  using H = H16<S>;
+  const size_t per_par = Vh * kIlSiteU2;
+  const size_t per_blk = (size_t)npar * per_par;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per_blk * nblk) return;
+  const int blk = (int)(i / per_blk);
+  const size_t rem = i % per_blk;
+  const int pi = (int)(rem / per_par);
+  const size_t j = rem % per_par;
+  const int k = (int)((j >> 3) % 12);
+  const int gq = (int)(j & 7) ^ (k % 3 == 2 ? 4 : 0);  // pair position -> system pair
+  const size_t w = ((size_t)blk * 2 + par0 + pi) * per_par + j;
+  const int r0 = blk * kIlRows + gq, r1 = r0 + 8;
+  const bool a0 = r0 < nrhs && active[r0] != 0, a1 = r1 < nrhs && active[r1] != 0;
+  if (!a0 && !a1) return;
+  const float b0 = a0 ? (float)beta[r0] : 0.0f, b1 = a1 ? (float)beta[r1] : 0.0f;
+  const uint2 rv = r[w], pv = p[w];
+  const float2 rr0 = H::to_f2(rv.x), rr1 = H::to_f2(rv.y), pp0 = H::to_f2(pv.x), pp1 = H::to_f2(pv.y);
+  il_store(p + w, H::pack(__fmaf_rn(b0, pp0.x, rr0.x), __fmaf_rn(b0, pp0.y, rr0.y)),
+           H::pack(__fmaf_rn(b1, pp1.x, rr1.x), __fmaf_rn(b1, pp1.y, rr1.y)), a0, a1);
+}
+
+tm_status_t il_xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
+                    const int* active, int nrhs, int par0, int npar, cudaStream_t s) {
+  const int nblk = (nrhs + kIlRows - 1) / kIlRows;
+  const size_t n = (size_t)nblk * npar * (size_t)g.Vh * kIlSiteU2;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  TraceScope tr(s, "blas.xpay", 3.0 * 24.0 * 2.0 * npar * g.Vh, 0.0, nrhs);
+  if (prec == TM_PREC_F16)
+    il_xpay_kernel<__half><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(p), static_cast<const uint2*>(r),
+                                               beta, active, nrhs, nblk, par0, npar);
+  else
+    il_xpay_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(p),
+                                                      static_cast<const uint2*>(r), beta, active, nrhs, nblk,
+                                                      par0, npar);
+  count_launch();
+  return check_launch("xpay (interleaved)");
+}
+
+// out = A in (inverse = 0) or A^-1 in (inverse = 1) on one parity, as twist()
+template <class S>
+__global__ void il_twist_kernel(size_t Vh, uint2* out, const uint2* in, float tn, float sc, int nblk, int par) {
+  using H = H16<S>;
+  const size_t per_blk = Vh * kIlSiteU2;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per_blk * nblk) return;
+  const int blk = (int)(i / per_blk);
+  const size_t rem = i % per_blk;
+  const int k = (int)((rem >> 3) % 12);
+  const size_t w = ((size_t)blk * 2 + par) * per_blk + rem;
+  const float tw = k < 6 ? tn : -tn;
+  const uint2 v = in[w];
+  const float2 c0 = H::to_f2(v.x), c1 = H::to_f2(v.y);
+  out[w] = make_uint2(H::pack(__fmul_rn(sc, __fmaf_rn(-tw, c0.y, c0.x)), __fmul_rn(sc, __fmaf_rn(tw, c0.x, c0.y))),
+                      H::pack(__fmul_rn(sc, __fmaf_rn(-tw, c1.y, c1.x)), __fmul_rn(sc, __fmaf_rn(tw, c1.x, c1.y))));
+}
+
+tm_status_t il_twist(const Geom& g, tm_prec_t prec, void* out, const void* in, double nu, int inverse, int par,
+                     int nrhs, cudaStream_t s) {
+  const int nblk = (nrhs + kIlRows - 1) / kIlRows;
+  const size_t n = (size_t)nblk * (size_t)g.Vh * kIlSiteU2;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const float sc = inverse ? (float)(1.0 / (1.0 + nu * nu)) : 1.0f;
+  const float tn = inverse ? (float)(-nu) : (float)nu;
+  if (prec == TM_PREC_F16)
+    il_twist_kernel<__half><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(out),
+                                                static_cast<const uint2*>(in), tn, sc, nblk, par);
+  else
+    il_twist_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(out),
+                                                       static_cast<const uint2*>(in), tn, sc, nblk, par);
+  count_launch();
+  return check_launch("twist (interleaved)");
+}
+
+}  // namespace tml
+
+using namespace tml;
+
+// ------------------------------------------------------------ C ABI
+extern "C" size_t tm_spinor_bytes_il(const tm_geom_t* gg, int nrhs) {
+  if (!gg || nrhs < 0 || check_geom(gg->L) != TM_OK) return 0;
+  return il_bytes(make_geom(gg->L, 1), nrhs);
+}
+
+static tm_status_t il_conv_api(const char* what, const tm_geom_t* gg, void* out, const void* in, tm_prec_t prec,
+                               int nrhs, bool to_il, tm_stream_t s) {
+  if (!gg || !out || !in || nrhs < 0) {
+    set_error("%s: null argument", what);
+    return TM_ERR_ARG;
+  }
+  if (prec != TM_PREC_F16 && prec != TM_PREC_BF16) {
+    set_error("%s: the interleaved layout holds F16 or BF16 fields", what);
+    return TM_ERR_ARG;
+  }
+  if (out == in) {
+    set_error("%s: out and in must not overlap", what);
+    return TM_ERR_ARG;
+  }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  return il_convert(make_geom(gg->L, 1), out, in, nrhs, to_il, (cudaStream_t)s);
+}
+
+extern "C" tm_status_t tm_spinor_to_il(const tm_geom_t* gg, void* out_il, const void* in, tm_prec_t prec,
+                                       int nrhs, tm_stream_t s) {
+  return il_conv_api("tm_spinor_to_il", gg, out_il, in, prec, nrhs, true, s);
+}
+
+extern "C" tm_status_t tm_spinor_from_il(const tm_geom_t* gg, void* out, const void* in_il, tm_prec_t prec,
+                                         int nrhs, tm_stream_t s) {
+  return il_conv_api("tm_spinor_from_il", gg, out, in_il, prec, nrhs, false, s);
+}
+
+extern "C" tm_status_t tm_dslash_il(tm_op_t* op, void* out_il, const void* in_il, int nrhs, int dagger,
+                                    int mu_zero, tm_prec_t prec, tm_stream_t s) {
+  if (!op || !out_il || !in_il || nrhs < 0) {
+    set_error("tm_dslash_il: null argument");
+    return TM_ERR_ARG;
+  }
+  if (out_il == in_il) {
+    set_error("tm_dslash_il: out and in must not overlap");
+    return TM_ERR_ARG;
+  }
+  DslashCall c;
+  c.in = in_il;
+  c.out = out_il;
+  c.nrhs = nrhs;
+  c.dagger = dagger != 0;
+  c.mu_zero = mu_zero != 0;
+  return dslash_il_dispatch(op, prec, c, (cudaStream_t)s);
+}
+
+extern "C" tm_status_t tm_op_check(tm_op_t* op) {
+  if (!op) {
+    set_error("tm_op_check: null argument");
+    return TM_ERR_ARG;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("tm_op_check: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  if (!op->il_err) return TM_OK;
+  int v = 0;
+  if (cudaMemcpy(&v, op->il_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("tm_op_check: %s", cudaGetErrorString(cudaGetLastError()));
+    return TM_ERR_CUDA;
+  }
+  if (v != 0) {
+    cudaMemset(op->il_err, 0, sizeof(int));
+    set_error("tm_op_check: a bounded wait of the interleaved Dslash gave up");
+    return TM_ERR_TIMEOUT;
+  }
+  return TM_OK;
+}
+
+extern "C" tm_status_t tm_cg_il_enable(int on) {
+  g_il_on.store(on ? 1 : 0);
+  return TM_OK;
+}

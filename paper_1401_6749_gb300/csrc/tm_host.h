@@ -20,6 +20,12 @@ struct tm_op {
   int* host_flags;
   int host_flags_n;
   bool owns_links;    // false for clones, which share the links of their source
+  // F16/BF16 links in the site-major layout of the interleaved Dslash
+  // ([par][cb][mu][9 words + 3 zero], 48 bytes per direction), when the
+  // 18-real copy exists; null otherwise
+  void* links_il[tml::kNumPrec];
+  // device flag: a bounded wait of the interleaved Dslash gave up (shared by clones)
+  int* il_err;
 };
 
 namespace tml {
@@ -92,6 +98,7 @@ struct DslashCall {
   void* x = nullptr;
   void* r = nullptr;
   const void* b = nullptr;
+  bool il = false;  // fields in the system-interleaved 16-bit layout (dslash_il.cu)
 };
 
 inline int nwarp_of(const Geom& g) { return (g.Vh + 31) / 32; }
@@ -104,6 +111,21 @@ template <class S>
 tm_status_t dslash_mma_prepare();
 
 tm_status_t dslash_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s);
+
+// System-interleaved 16-bit layout (dslash_il.cu): bytes of nrhs systems,
+// the tensor-core Dslash on it, conversions from/to the standard layout and
+// the solver's BLAS on it; cg_il_on: the plain F16/BF16 solver runs on it.
+size_t il_bytes(const Geom& g, int nrhs);
+tm_status_t dslash_il_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall& c, cudaStream_t s);
+tm_status_t il_convert(const Geom& g, void* out, const void* in, int nrhs, bool to_il, cudaStream_t s);
+tm_status_t il_xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
+                    const int* active, int nrhs, int par0, int npar, cudaStream_t s);
+tm_status_t il_twist(const Geom& g, tm_prec_t prec, void* out, const void* in, double nu, int inverse, int par,
+                     int nrhs, cudaStream_t s);
+bool cg_il_on();
+size_t il_link_bytes(const Geom& g);
+tm_status_t il_pack_links(const Geom& g, void* out, const void* links18, cudaStream_t s);
+tm_status_t il_prepare();
 
 // per-warp partial sums -> result[rhs] (fixed summation order): system rhs sums
 // partial[rhs * stride + i], i < nper (stride 0 means nper)

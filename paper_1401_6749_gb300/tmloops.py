@@ -95,12 +95,19 @@ _SIGS = {
     "tm_tune_reset": [],
     "tm_tune_count": [],
     "tm_tune_get": [_i, _P(_i), _P(_i), _P(_i), _P(_i)],
+    "tm_spinor_bytes_il": [_P(tm_geom_t), _i],
+    "tm_spinor_to_il": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
+    "tm_spinor_from_il": [_P(tm_geom_t), _vp, _vp, _i, _i, _vp],
+    "tm_dslash_il": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
+    "tm_cg_il_enable": [_i],
+    "tm_op_check": [_vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = _i
 _lib.tm_spinor_bytes.restype = _sz
+_lib.tm_spinor_bytes_il.restype = _sz
 _lib.tm_last_error.restype = ctypes.c_char_p
 _lib.tm_launch_count.restype = _u64
 _lib.tm_trace_enable.restype = None
@@ -229,6 +236,42 @@ def tm_gamma5(L, out, inp, prec, nrhs, stream=None):
 def tm_dslash(op, out, inp, nrhs, dagger=False, mu_zero=False, prec=F32, stream=None):
     _check(_lib.tm_dslash(op.handle, _ptr(out), _ptr(inp), int(nrhs), int(bool(dagger)),
                           int(bool(mu_zero)), int(prec), _stream(stream)))
+
+
+def tm_spinor_bytes_il(L, nrhs):
+    return int(_lib.tm_spinor_bytes_il(ctypes.byref(geom(L)), int(nrhs)))
+
+
+def empty_field_il(L, nrhs, device="cuda"):
+    """Uninitialised storage of nrhs 16-bit fields in the system-interleaved layout."""
+    return torch.empty(tm_spinor_bytes_il(L, nrhs), dtype=torch.uint8, device=device)
+
+
+def tm_spinor_to_il(L, out_il, inp, prec, nrhs, stream=None):
+    _check(_lib.tm_spinor_to_il(ctypes.byref(geom(L)), _ptr(out_il), _ptr(inp), int(prec), int(nrhs),
+                                _stream(stream)))
+
+
+def tm_spinor_from_il(L, out, inp_il, prec, nrhs, stream=None):
+    _check(_lib.tm_spinor_from_il(ctypes.byref(geom(L)), _ptr(out), _ptr(inp_il), int(prec), int(nrhs),
+                                  _stream(stream)))
+
+
+def tm_dslash_il(op, out_il, inp_il, nrhs, dagger=False, mu_zero=False, prec=F16, stream=None):
+    """M (M^dag, D_W) on 16-bit fields in the system-interleaved layout (tensor cores)."""
+    _check(_lib.tm_dslash_il(op.handle, _ptr(out_il), _ptr(inp_il), int(nrhs), int(bool(dagger)),
+                             int(bool(mu_zero)), int(prec), _stream(stream)))
+
+
+def tm_op_check(op):
+    """Wait for the device; raise TM_ERR_TIMEOUT if a bounded wait of a kernel
+    on this operator gave up since the last check."""
+    _check(_lib.tm_op_check(op.handle))
+
+
+def tm_cg_il_enable(on=True):
+    """Plain F16/BF16 solves on the interleaved layout (default) or the standard one."""
+    _check(_lib.tm_cg_il_enable(int(bool(on))))
 
 
 def tm_dslash_g5(op, out, inp, nrhs, dagger=False, mu_zero=False, prec=F32, stream=None):
