@@ -43,6 +43,7 @@
 // in the per-warp layout of the CUDA-core kernel.  A system's result depends only on
 // its own MMA row: rows do not mix in the products, and the per-lane sums run
 // in a fixed order, whatever the other systems of the block are.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <mutex>
@@ -186,7 +187,7 @@ struct IlArgs {
   double* partial;
   int* trace_count;
   int nrhs, nblk, parity, nwarp;
-  int centre, out_inv, g5_out;
+  int centre, out_inv;
   float nu, shop, inv;
 };
 
@@ -303,9 +304,12 @@ __device__ __forceinline__ bool il_wait(unsigned bar, unsigned phase, int* err) 
   return false;
 }
 
-template <class S, bool DAG, int EPI>
-__global__ void __launch_bounds__(kIlWarps * 32, 4) dslash_il_kernel(const IlArgs a) {
+// FORM = 2 * centre + out_inv: centre 0 (none), 1 (c), 2 (A c); out_inv: A^-1 on the result
+template <class S, bool DAG, int EPI, int FORM>
+__global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslash_il_kernel(const IlArgs a) {
   using H = H16<S>;
+  constexpr int CENTRE = FORM >> 1;
+  constexpr bool INV = (FORM & 1) != 0;
   using ST = IlStage<EPI>;
   extern __shared__ __align__(128) unsigned char il_smem[];
   __shared__ __align__(8) unsigned long long bars[kIlWarps][ST::kStages];
@@ -406,25 +410,31 @@ __global__ void __launch_bounds__(kIlWarps * 32, 4) dslash_il_kernel(const IlArg
     const unsigned bar0 = smem_u32(&bars[wq][0]);
     constexpr int SF = DAG ? +1 : -1;
     constexpr unsigned total = 8 * kIlSiteBytes + kIlLinkSiteBytes + 4 * kIlLinkBytes;
-    // the output site's own words (centre, r, x, p or b), straight into registers
-    const uint2* cf = a.cfield ? a.cfield : a.in;
+    // the output site's own words (centre, r, x, p or b), straight into
+    // registers; per-lane base pointers of the output parity, so that a site
+    // adds one offset and the spins are immediate offsets
+    const size_t lbase = (obase + woff) / 8;
+    const uint2* cf = (a.cfield ? a.cfield : a.in) + lbase;
+    const uint2* rp = (EPI == EPI_RESID ? a.b : a.r) + lbase;
+    const uint2* xp = a.x + lbase;
+    const uint2* pp = a.p + lbase;
+    uint2* op = (EPI == EPI_CGUPD ? a.r : a.out) + lbase;
+    uint2* oxp = a.x + lbase;
     uint2 cw[4], rw[4], xw[4], pw[4];
     auto fetch_site = [&](int m) {
-      const size_t w = (obase + (size_t)(base + wq + kIlWarps * m) * kIlSiteBytes + woff) / 8;
+      const unsigned w = (unsigned)(base + wq + kIlWarps * m) * (kIlSiteBytes / 8);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        if (a.centre != 0) cw[s] = cf[w + 24 * s];
+        if constexpr (CENTRE != 0) cw[s] = cf[w + 24 * s];
         if constexpr (EPI == EPI_CGUPD) {
-          rw[s] = a.r[w + 24 * s];
-          xw[s] = a.x[w + 24 * s];
-          pw[s] = a.p[w + 24 * s];
+          rw[s] = rp[w + 24 * s];
+          xw[s] = xp[w + 24 * s];
+          pw[s] = pp[w + 24 * s];
         } else if constexpr (EPI == EPI_RESID) {
-          rw[s] = a.b[w + 24 * s];
+          rw[s] = rp[w + 24 * s];
         }
       }
     };
-    // issue the copies of the warp's site m into stage st: every lane computes
-    // its block's address and one bulk-copy instruction moves them all
     auto issue = [&](int m, int st) {
       const int lex = __shfl_sync(0xffffffffu, lexl, m);
       const unsigned w01 = __shfl_sync(0xffffffffu, c01, m), w23 = __shfl_sync(0xffffffffu, c23, m);
@@ -479,67 +489,64 @@ __global__ void __launch_bounds__(kIlWarps * 32, 4) dslash_il_kernel(const IlArg
         else if (mu == 2) il_dir<S, 2, SF>(d, l, pf, pb, uf, ub, negf, negb);
         else il_dir<S, 3, SF>(e, l, pf, pb, uf, ub, negf, negb);
       }
-      // epilogue: out = T_out(T_c(c) + s_hop H in), then the CG update / residual
-      const size_t wsite = (obase + (size_t)(base + wq + kIlWarps * m) * kIlSiteBytes + woff) / 8;
+      // epilogue: out = T_out(T_c(c) + s_hop H in), then the CG update / residual;
+      // lanes t = 3 compute on the words of t = 0 and store nothing
+      uint2* const ost = op + (unsigned)(base + wq + kIlWarps * m) * (kIlSiteBytes / 8);
+      uint2* const xst = oxp + (unsigned)(base + wq + kIlWarps * m) * (kIlSiteBytes / 8);
       float n0 = 0.0f, n1 = 0.0f;
-      if (l.ld) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const size_t wi = wsite + 24 * s;
-          const float tw = s < 2 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
-          const float h0r = __fadd_rn(d[s][0], e[s][0]), h0i = __fadd_rn(d[s][1], e[s][1]);
-          const float h1r = __fadd_rn(d[s][2], e[s][2]), h1i = __fadd_rn(d[s][3], e[s][3]);
-          float2 o0, o1;
-          if (a.centre != 0) {
-            const uint2 c = cw[s];
-            float2 c0 = H::to_f2(c.x), c1 = H::to_f2(c.y);
-            if (a.centre == 2) {
-              c0 = make_float2(__fmaf_rn(-tw, c0.y, c0.x), __fmaf_rn(tw, c0.x, c0.y));
-              c1 = make_float2(__fmaf_rn(-tw, c1.y, c1.x), __fmaf_rn(tw, c1.x, c1.y));
-            }
-            o0 = make_float2(__fmaf_rn(shop, h0r, c0.x), __fmaf_rn(shop, h0i, c0.y));
-            o1 = make_float2(__fmaf_rn(shop, h1r, c1.x), __fmaf_rn(shop, h1i, c1.y));
-          } else {
-            o0 = make_float2(__fmul_rn(shop, h0r), __fmul_rn(shop, h0i));
-            o1 = make_float2(__fmul_rn(shop, h1r), __fmul_rn(shop, h1i));
+      for (int s = 0; s < 4; ++s) {
+        const float tw = s < 2 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
+        const float h0r = __fadd_rn(d[s][0], e[s][0]), h0i = __fadd_rn(d[s][1], e[s][1]);
+        const float h1r = __fadd_rn(d[s][2], e[s][2]), h1i = __fadd_rn(d[s][3], e[s][3]);
+        float2 o0, o1;
+        if constexpr (CENTRE != 0) {
+          float2 c0 = H::to_f2(cw[s].x), c1 = H::to_f2(cw[s].y);
+          if constexpr (CENTRE == 2) {
+            c0 = make_float2(__fmaf_rn(-tw, c0.y, c0.x), __fmaf_rn(tw, c0.x, c0.y));
+            c1 = make_float2(__fmaf_rn(-tw, c1.y, c1.x), __fmaf_rn(tw, c1.x, c1.y));
           }
-          if (a.out_inv) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
-            o0 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o0.y, o0.x)), __fmul_rn(inv, __fmaf_rn(-tw, o0.x, o0.y)));
-            o1 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o1.y, o1.x)), __fmul_rn(inv, __fmaf_rn(-tw, o1.x, o1.y)));
+          o0 = make_float2(__fmaf_rn(shop, h0r, c0.x), __fmaf_rn(shop, h0i, c0.y));
+          o1 = make_float2(__fmaf_rn(shop, h1r, c1.x), __fmaf_rn(shop, h1i, c1.y));
+        } else {
+          o0 = make_float2(__fmul_rn(shop, h0r), __fmul_rn(shop, h0i));
+          o1 = make_float2(__fmul_rn(shop, h1r), __fmul_rn(shop, h1i));
+        }
+        if constexpr (INV) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
+          o0 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o0.y, o0.x)), __fmul_rn(inv, __fmaf_rn(-tw, o0.x, o0.y)));
+          o1 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o1.y, o1.x)), __fmul_rn(inv, __fmaf_rn(-tw, o1.x, o1.y)));
+        }
+        if constexpr (EPI == EPI_OUT) {
+          // every system's output (inactive and padding systems get the
+          // operator applied to their own unchanged input)
+          if (l.ld) ost[24 * s] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
+          n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
+          n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+        } else if constexpr (EPI == EPI_CGUPD) {
+          // r and x of inactive systems keep their bits
+          float2 q0 = H::to_f2(rw[s].x), q1 = H::to_f2(rw[s].y);
+          q0 = make_float2(__fmaf_rn(-al0, o0.x, q0.x), __fmaf_rn(-al0, o0.y, q0.y));
+          q1 = make_float2(__fmaf_rn(-al1, o1.x, q1.x), __fmaf_rn(-al1, o1.y, q1.y));
+          const uint2 rn = make_uint2(act0 ? H::pack(q0.x, q0.y) : rw[s].x, act1 ? H::pack(q1.x, q1.y) : rw[s].y);
+          n0 = __fmaf_rn(q0.x, q0.x, n0); n0 = __fmaf_rn(q0.y, q0.y, n0);
+          n1 = __fmaf_rn(q1.x, q1.x, n1); n1 = __fmaf_rn(q1.y, q1.y, n1);
+          const float2 x0 = H::to_f2(xw[s].x), x1 = H::to_f2(xw[s].y), p0 = H::to_f2(pw[s].x), p1 = H::to_f2(pw[s].y);
+          const uint2 xn = make_uint2(act0 ? H::pack(__fmaf_rn(al0, p0.x, x0.x), __fmaf_rn(al0, p0.y, x0.y)) : xw[s].x,
+                                      act1 ? H::pack(__fmaf_rn(al1, p1.x, x1.x), __fmaf_rn(al1, p1.y, x1.y)) : xw[s].y);
+          if (l.ld) {
+            ost[24 * s] = rn;
+            xst[24 * s] = xn;
           }
-          if constexpr (EPI == EPI_OUT) {
-            if (a.g5_out && s >= 2) {
-              o0 = make_float2(-o0.x, -o0.y);
-              o1 = make_float2(-o1.x, -o1.y);
-            }
-            // every system's output (inactive and padding systems get the
-            // operator applied to their own unchanged input)
-            a.out[wi] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
-            if (want_norm) {
-              n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
-              n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
-            }
-          } else if constexpr (EPI == EPI_CGUPD) {
-            // r and x of inactive systems keep their bits
-            float2 q0 = H::to_f2(rw[s].x), q1 = H::to_f2(rw[s].y);
-            q0 = make_float2(__fmaf_rn(-al0, o0.x, q0.x), __fmaf_rn(-al0, o0.y, q0.y));
-            q1 = make_float2(__fmaf_rn(-al1, o1.x, q1.x), __fmaf_rn(-al1, o1.y, q1.y));
-            a.r[wi] = make_uint2(act0 ? H::pack(q0.x, q0.y) : rw[s].x, act1 ? H::pack(q1.x, q1.y) : rw[s].y);
-            n0 = __fmaf_rn(q0.x, q0.x, n0); n0 = __fmaf_rn(q0.y, q0.y, n0);
-            n1 = __fmaf_rn(q1.x, q1.x, n1); n1 = __fmaf_rn(q1.y, q1.y, n1);
-            const float2 x0 = H::to_f2(xw[s].x), x1 = H::to_f2(xw[s].y), p0 = H::to_f2(pw[s].x), p1 = H::to_f2(pw[s].y);
-            a.x[wi] = make_uint2(act0 ? H::pack(__fmaf_rn(al0, p0.x, x0.x), __fmaf_rn(al0, p0.y, x0.y)) : xw[s].x,
-                                 act1 ? H::pack(__fmaf_rn(al1, p1.x, x1.x), __fmaf_rn(al1, p1.y, x1.y)) : xw[s].y);
-          } else {  // EPI_RESID: out = b - D in
-            const float2 b0 = H::to_f2(rw[s].x), b1 = H::to_f2(rw[s].y);
-            o0 = make_float2(__fsub_rn(b0.x, o0.x), __fsub_rn(b0.y, o0.y));
-            o1 = make_float2(__fsub_rn(b1.x, o1.x), __fsub_rn(b1.y, o1.y));
-            a.out[wi] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
-            n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
-            n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
-          }
+        } else {  // EPI_RESID: out = b - D in
+          const float2 b0 = H::to_f2(rw[s].x), b1 = H::to_f2(rw[s].y);
+          o0 = make_float2(__fsub_rn(b0.x, o0.x), __fsub_rn(b0.y, o0.y));
+          o1 = make_float2(__fsub_rn(b1.x, o1.x), __fsub_rn(b1.y, o1.y));
+          if (l.ld) ost[24 * s] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
+          n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
+          n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
         }
       }
+      if (!l.ld) n0 = n1 = 0.0f;
       if (want_norm) {
         if (act0) nacc0 = __fadd_rn(nacc0, n0);
         if (act1) nacc1 = __fadd_rn(nacc1, n1);
@@ -575,14 +582,29 @@ __global__ void __launch_bounds__(kIlWarps * 32, 4) dslash_il_kernel(const IlArg
   }
 }
 
-template <class S, bool DAG, int EPI>
+template <class S, bool DAG, int EPI, int FORM>
 static tm_status_t il_prepare_t() {
-  const cudaError_t e = cudaFuncSetAttribute(dslash_il_kernel<S, DAG, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             IlStage<EPI>::kSmem);
+  const cudaError_t e = cudaFuncSetAttribute(dslash_il_kernel<S, DAG, EPI, FORM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, IlStage<EPI>::kSmem);
   if (e != cudaSuccess) {
     set_error("dslash_il: shared-memory limit: %s", cudaGetErrorString(e));
     return TM_ERR_CUDA;
   }
+  return TM_OK;
+}
+
+// the instantiated forms: every (centre, A^-1) combination for the plain
+// output, the twisted centre without A^-1 for the CG update and the residual
+template <class S, bool DAG>
+static tm_status_t il_prepare_sd() {
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 0>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 1>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 2>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 3>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 4>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 5>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_CGUPD, 4>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_RESID, 4>()));
   return TM_OK;
 }
 
@@ -592,18 +614,10 @@ tm_status_t il_prepare() {
   static bool done = false;
   std::lock_guard<std::mutex> lk(mu);
   if (done) return TM_OK;
-  TM_TRY((il_prepare_t<__half, false, EPI_OUT>()));
-  TM_TRY((il_prepare_t<__half, false, EPI_CGUPD>()));
-  TM_TRY((il_prepare_t<__half, false, EPI_RESID>()));
-  TM_TRY((il_prepare_t<__half, true, EPI_OUT>()));
-  TM_TRY((il_prepare_t<__half, true, EPI_CGUPD>()));
-  TM_TRY((il_prepare_t<__half, true, EPI_RESID>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_OUT>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_CGUPD>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, false, EPI_RESID>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_OUT>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_CGUPD>()));
-  TM_TRY((il_prepare_t<__nv_bfloat16, true, EPI_RESID>()));
+  TM_TRY((il_prepare_sd<__half, false>()));
+  TM_TRY((il_prepare_sd<__half, true>()));
+  TM_TRY((il_prepare_sd<__nv_bfloat16, false>()));
+  TM_TRY((il_prepare_sd<__nv_bfloat16, true>()));
   done = true;
   return TM_OK;
 }
@@ -629,7 +643,6 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
   a.nblk = (c.nrhs + kIlRows - 1) / kIlRows;
   a.parity = c.parity;
   a.nwarp = nwarp_of(g);
-  a.g5_out = c.g5_out ? 1 : 0;
   double nu, hop;
   if (c.custom) {
     nu = c.nu;
@@ -653,6 +666,10 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
       set_error("dslash_il: fields must be 16-byte aligned");
       return TM_ERR_ARG;
     }
+  if ((size_t)g.Vh * kIlSiteBytes / 8 >= (size_t)0xffffffffu) {
+    set_error("dslash_il: lattice too large for the interleaved kernel (V/2 * 96 >= 2^32)");
+    return TM_ERR_UNSUPPORTED;
+  }
   const int npar = c.parity < 0 ? 2 : 1;
   const long chunks = ((long)g.Vh + kIlGroups * 32 - 1) / (kIlGroups * 32);
   const long blocks = (long)a.nblk * npar * chunks;  // one block per 128 sites and 16 systems
@@ -677,9 +694,27 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
   const double fixed = 4.0 * 2.0 * g.Vh * 18.0 * e;
   const double site_flops = 1320.0 + 48.0 + (a.centre == 2 ? 48.0 : 0.0) + (a.out_inv ? 72.0 : 0.0) +
                             (EPI == EPI_CGUPD ? 144.0 : EPI == EPI_RESID ? 72.0 : (a.partial ? 48.0 : 0.0));
+  const int form = 2 * a.centre + a.out_inv;
+  if (EPI != EPI_OUT && form != 4) {
+    set_error("dslash_il: the CG update and residual forms need the twisted centre without A^-1");
+    return TM_ERR_UNSUPPORTED;
+  }
   cudaEvent_t ev = nullptr;
   a.trace_count = trace_begin(st, &ev);
-  dslash_il_kernel<S, DAG, EPI><<<(unsigned)blocks, kIlWarps * 32, IlStage<EPI>::kSmem, st>>>(a);
+  const dim3 grid((unsigned)blocks);
+  constexpr int kT = kIlWarps * 32, kM = IlStage<EPI>::kSmem;
+  if constexpr (EPI == EPI_OUT) {
+    switch (form) {
+      case 0: dslash_il_kernel<S, DAG, EPI, 0><<<grid, kT, kM, st>>>(a); break;
+      case 1: dslash_il_kernel<S, DAG, EPI, 1><<<grid, kT, kM, st>>>(a); break;
+      case 2: dslash_il_kernel<S, DAG, EPI, 2><<<grid, kT, kM, st>>>(a); break;
+      case 3: dslash_il_kernel<S, DAG, EPI, 3><<<grid, kT, kM, st>>>(a); break;
+      case 4: dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a); break;
+      default: dslash_il_kernel<S, DAG, EPI, 5><<<grid, kT, kM, st>>>(a); break;
+    }
+  } else {
+    dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a);
+  }
   count_launch();
   trace_end(st, name, ev, a.trace_count, per_rhs, fixed, 0, out_sites * site_flops);
   return check_launch("dslash_il");
@@ -708,6 +743,10 @@ tm_status_t dslash_il_dispatch(const tm_op* op, tm_prec_t prec, const DslashCall
   }
   if (op->recon_p[prec] != 18 || !op->links_il[prec] || !op->il_err) {
     set_error("dslash_il: needs the 18-real 16-bit link copy (recon 18 or 0)");
+    return TM_ERR_UNSUPPORTED;
+  }
+  if (c.g5_out || (c.custom && (c.centre < 0 || c.centre > 2))) {
+    set_error("dslash_il: unsupported output form");
     return TM_ERR_UNSUPPORTED;
   }
   if (c.nrhs <= 0) return TM_OK;
@@ -834,46 +873,56 @@ tm_status_t il_convert(const Geom& g, void* out, const void* in, int nrhs, bool 
 }
 
 // ------------------------------------------------ solver BLAS on IL16
-// One thread per 8-byte word pair (systems j, j + 8 of one (k, site) row) of
-// the parities par0 .. par0 + npar - 1.
+// p = r + beta p for the active systems on parities par0 .. par0 + npar - 1.
+// One plane (block of systems, parity) per grid row; a thread takes 16-byte
+// words (pair positions 2q, 2q + 1 of a row), the systems' beta and flags
+// come from shared memory.
 template <class S>
-__global__ void il_xpay_kernel(size_t Vh, uint2* p, const uint2* r, const double* beta, const int* active,
-                               int nrhs, int nblk, int par0, int npar) {
+__global__ void il_xpay_kernel(uint4* p, const uint4* r, const double* beta, const int* active, int nrhs,
+                               int par0, int npar, unsigned plane_u4) {
   using H = H16<S>;
-  const size_t per_par = Vh * kIlSiteU2;
-  const size_t per_blk = (size_t)npar * per_par;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= per_blk * nblk) return;
-  const int blk = (int)(i / per_blk);
-  const size_t rem = i % per_blk;
-  const int pi = (int)(rem / per_par);
-  const size_t j = rem % per_par;
-  const int k = (int)((j >> 3) % 12);
-  const int gq = (int)(j & 7) ^ (k % 3 == 2 ? 4 : 0);  // pair position -> system pair
-  const size_t w = ((size_t)blk * 2 + par0 + pi) * per_par + j;
-  const int r0 = blk * kIlRows + gq, r1 = r0 + 8;
-  const bool a0 = r0 < nrhs && active[r0] != 0, a1 = r1 < nrhs && active[r1] != 0;
-  if (!a0 && !a1) return;
-  const float b0 = a0 ? (float)beta[r0] : 0.0f, b1 = a1 ? (float)beta[r1] : 0.0f;
-  const uint2 rv = r[w], pv = p[w];
-  const float2 rr0 = H::to_f2(rv.x), rr1 = H::to_f2(rv.y), pp0 = H::to_f2(pv.x), pp1 = H::to_f2(pv.y);
-  il_store(p + w, H::pack(__fmaf_rn(b0, pp0.x, rr0.x), __fmaf_rn(b0, pp0.y, rr0.y)),
-           H::pack(__fmaf_rn(b1, pp1.x, rr1.x), __fmaf_rn(b1, pp1.y, rr1.y)), a0, a1);
+  __shared__ float sb[kIlRows];
+  __shared__ int sa[kIlRows];
+  const int blk = blockIdx.y / npar, pi = blockIdx.y % npar;
+  if (threadIdx.x < kIlRows) {
+    const int rr = blk * kIlRows + threadIdx.x;
+    const int on = rr < nrhs && active[rr] != 0;
+    sa[threadIdx.x] = on;
+    sb[threadIdx.x] = on ? (float)beta[rr] : 0.0f;
+  }
+  __syncthreads();
+  uint4* pp = p + ((size_t)blk * 2 + par0 + pi) * plane_u4;
+  const uint4* rp = r + ((size_t)blk * 2 + par0 + pi) * plane_u4;
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < plane_u4; j += gridDim.x * blockDim.x) {
+    const unsigned k = (j >> 2) % 12u;  // row j / 4 = site * 12 + k
+    const int sw = k % 3u == 2u ? 4 : 0;
+    const int g0 = (int)(2 * (j & 3)) ^ sw, g1 = (int)(2 * (j & 3) + 1) ^ sw;
+    const bool a0 = sa[g0], a1 = sa[g0 + 8], a2 = sa[g1], a3 = sa[g1 + 8];
+    if (!(a0 || a1 || a2 || a3)) continue;
+    const float b0 = sb[g0], b1 = sb[g0 + 8], b2 = sb[g1], b3 = sb[g1 + 8];
+    const uint4 rv = rp[j], pv = pp[j];
+    auto upd = [&](unsigned rw, unsigned pw, float b, bool on) -> unsigned {
+      const float2 x = H::to_f2(rw), y = H::to_f2(pw);
+      return on ? H::pack(__fmaf_rn(b, y.x, x.x), __fmaf_rn(b, y.y, x.y)) : pw;
+    };
+    pp[j] = make_uint4(upd(rv.x, pv.x, b0, a0), upd(rv.y, pv.y, b1, a1), upd(rv.z, pv.z, b2, a2),
+                       upd(rv.w, pv.w, b3, a3));
+  }
 }
 
 tm_status_t il_xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
                     const int* active, int nrhs, int par0, int npar, cudaStream_t s) {
   const int nblk = (nrhs + kIlRows - 1) / kIlRows;
-  const size_t n = (size_t)nblk * npar * (size_t)g.Vh * kIlSiteU2;
-  const unsigned nb = (unsigned)((n + 255) / 256);
+  const unsigned plane_u4 = (unsigned)((size_t)g.Vh * (kIlSiteBytes / 16));
+  const unsigned gx = std::min<unsigned>((plane_u4 + 255) / 256, 152u * 8u);
+  const dim3 grid(gx, (unsigned)(nblk * npar));
   TraceScope tr(s, "blas.xpay", 3.0 * 24.0 * 2.0 * npar * g.Vh, 0.0, nrhs);
   if (prec == TM_PREC_F16)
-    il_xpay_kernel<__half><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(p), static_cast<const uint2*>(r),
-                                               beta, active, nrhs, nblk, par0, npar);
+    il_xpay_kernel<__half><<<grid, 256, 0, s>>>(static_cast<uint4*>(p), static_cast<const uint4*>(r), beta, active,
+                                                nrhs, par0, npar, plane_u4);
   else
-    il_xpay_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>((size_t)g.Vh, static_cast<uint2*>(p),
-                                                      static_cast<const uint2*>(r), beta, active, nrhs, nblk,
-                                                      par0, npar);
+    il_xpay_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<uint4*>(p), static_cast<const uint4*>(r), beta,
+                                                       active, nrhs, par0, npar, plane_u4);
   count_launch();
   return check_launch("xpay (interleaved)");
 }
