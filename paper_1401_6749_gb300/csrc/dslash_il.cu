@@ -204,18 +204,29 @@ struct IlLane {
 // at ((blk * 2 + par) * Vh + cb) * 96; lane (g, t) reads spin s at + (3 s + t) * 8 + g.
 constexpr int kIlSiteU2 = 96;
 
-// One direction: both hops of 16 systems into the four spin accumulators,
-// from the loaded neighbour words pf / pb (spins 0..3, systems g and g + 8)
-// and link words uf / ub; negf / negb the antiperiodic signs (0 or 0x80008000).
+// Lower-spin accumulators by phase class.  Lower spin 2 + r receives, from
+// direction mu, i^bk_r(mu) (SF W_f h_f + SB W_b h_b)_bc_r(mu): one product per
+// (r, mu) with the un-phased B = [SF U_f; SB U_b^dag], accumulated into the
+// quad of its phase; the epilogue multiplies each quad by its phase (a swap
+// and sign of FP32 values) and adds.  In the DeGrand-Rossi basis r = 0 meets
+// the phases i^3, i^0 and r = 1 all four.
+__host__ __device__ constexpr int il_quad(int r, int k) {
+  return r == 0 ? (k == 3 ? 0 : 1) : (k == 3 ? 2 : k == 2 ? 3 : k == 1 ? 4 : 5);
+}
+
+// One direction: both hops of 16 systems into the upper-spin accumulators
+// up (spins 0, 1) and the lower-spin phase quads q, from the loaded neighbour
+// words pf / pb (spins 0..3, systems g and g + 8) and link words uf / ub;
+// negf / negb the antiperiodic signs (0 or 0x80008000).
 template <class S, int MU, int SF>
-__device__ __forceinline__ void il_dir(float (&d)[4][4], const IlLane& l, const uint2 (&pf)[4],
+__device__ __forceinline__ void il_dir(float (&up)[2][4], float (&q)[6][4], const IlLane& l, const uint2 (&pf)[4],
                                        const uint2 (&pb)[4], unsigned uf, unsigned ub, unsigned negf,
                                        unsigned negb) {
   using G = IlG<MU>;
   constexpr int SB = -SF;
   constexpr int pf2 = SF < 0 ? 2 : 0, pb2 = SB < 0 ? 2 : 0;
   // lane phase (odd columns: forward words times -i, backward words times +i)
-  // and the time-boundary sign; every B word below is then a fixed rotation
+  // and the time-boundary sign; every B word below is then a fixed sign flip
   uf = __byte_perm(uf, 0u, l.psel) ^ l.pmf ^ negf;
   ub = __byte_perm(ub, 0u, l.psel) ^ l.pmb ^ negb;
   // projected words (rows g, g + 8) of the two upper spins for both hops
@@ -227,16 +238,17 @@ __device__ __forceinline__ void il_dir(float (&d)[4][4], const IlLane& l, const 
   const unsigned h1f1 = proj_w<G::ak1 + pf2, S>(pf[1].y, pf[2 + G::ac1].y);
   const unsigned h1b0 = proj_w<G::ak1 + pb2, S>(pb[1].x, pb[2 + G::ac1].x);
   const unsigned h1b1 = proj_w<G::ak1 + pb2, S>(pb[1].y, pb[2 + G::ac1].y);
-  // B words: forward conj(i^k u), backward i^-k u (k: phase of W)
+  // B words: [U_f; U_b^dag] (forward conj(u), backward u) and the signed
+  // [SF U_f; SB U_b^dag]
   const unsigned bf_up = uf ^ 0x80000000u, bb_up = ub;
-  const unsigned bf_l0 = il_rot<G::bk0 + pf2>(uf) ^ 0x80000000u, bb_l0 = il_rot<-(G::bk0 + pb2)>(ub);
-  const unsigned bf_l1 = il_rot<G::bk1 + pf2>(uf) ^ 0x80000000u, bb_l1 = il_rot<-(G::bk1 + pb2)>(ub);
-  il_mma<S>(d[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
-  il_mma<S>(d[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
-  if constexpr (G::bc0 == 0) il_mma<S>(d[2], h0f0, h0f1, h0b0, h0b1, bf_l0, bb_l0);
-  else il_mma<S>(d[2], h1f0, h1f1, h1b0, h1b1, bf_l0, bb_l0);
-  if constexpr (G::bc1 == 0) il_mma<S>(d[3], h0f0, h0f1, h0b0, h0b1, bf_l1, bb_l1);
-  else il_mma<S>(d[3], h1f0, h1f1, h1b0, h1b1, bf_l1, bb_l1);
+  const unsigned bf_m = SF < 0 ? uf ^ 0x00008000u : bf_up;
+  const unsigned bb_m = SB < 0 ? ub ^ 0x80008000u : bb_up;
+  il_mma<S>(up[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
+  il_mma<S>(up[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
+  if constexpr (G::bc0 == 0) il_mma<S>(q[il_quad(0, G::bk0)], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
+  else il_mma<S>(q[il_quad(0, G::bk0)], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
+  if constexpr (G::bc1 == 0) il_mma<S>(q[il_quad(1, G::bk1)], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
+  else il_mma<S>(q[il_quad(1, G::bk1)], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
 }
 
 // store one 8-byte pair of words, only the halves of active systems
@@ -349,15 +361,16 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
   const int left = g.Vh - base - wq;
   const int nsite = left <= 0 ? 0 : min(32, (left + kIlWarps - 1) / kIlWarps);
   if (__any_sync(0xffffffffu, act0 || act1) && nsite > 0) {
-    // lane m: the warp's site m (lex index, coordinates, time-boundary flags)
+    // lane m: the warp's site m: lex index and a mask of the hops that wrap
+    // around the lattice (bit 2 mu: forward, 2 mu + 1: backward)
     int lexl = 0;
-    unsigned c01 = 0u, c23 = 0u, bfl = 0u;
+    unsigned bml = 0u;
     if (lane < nsite) {
       const Site s = site_of(g, par, base + wq + kIlWarps * lane);
       lexl = s.lex;
-      c01 = (unsigned)s.c[0] | ((unsigned)s.c[1] << 16);
-      c23 = (unsigned)s.c[2] | ((unsigned)s.c[3] << 16);
-      if (g.antiperiodic) bfl = (s.c[3] == g.L[3] - 1 ? 1u : 0u) | (s.c[3] == 0 ? 2u : 0u);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+        bml |= (s.c[mu] == g.L[mu] - 1 ? 1u : 0u) << (2 * mu) | (s.c[mu] == 0 ? 2u : 0u) << (2 * mu);
     }
     const size_t obase = ((size_t)blk * 2 + par) * Vh * kIlSiteBytes;
     // copy role of this lane (one bulk copy per lane and site): lanes 0..7 the
@@ -367,8 +380,10 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     const int rmu = lane < 8 ? (lane >> 1) : (lane >= 10 && lane < 14 ? lane - 10 : 0);
     const bool rbwd = lane < 8 ? (lane & 1) != 0 : true;
     const bool rnb = lane < 8 || (lane >= 10 && lane < 14);
-    const int rstride = g.stride[rmu], rL = g.L[rmu];
-    const int rsh = (rmu & 1) ? 16 : 0;
+    // the role's hop: lex step, and the step when it wraps around
+    const int rbit = 2 * rmu + (rbwd ? 1 : 0);
+    const int rstep = rbwd ? -g.stride[rmu] : g.stride[rmu];
+    const int rwrap = rbwd ? (g.L[rmu] - 1) * g.stride[rmu] : -(g.L[rmu] - 1) * g.stride[rmu];
     const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il);
     const unsigned char* rbase = nullptr;
     unsigned rmul = kIlSiteBytes, rdoff = 0, rbytes = 0;
@@ -437,10 +452,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     };
     auto issue = [&](int m, int st) {
       const int lex = __shfl_sync(0xffffffffu, lexl, m);
-      const unsigned w01 = __shfl_sync(0xffffffffu, c01, m), w23 = __shfl_sync(0xffffffffu, c23, m);
-      const int cm = (int)(((rmu < 2 ? w01 : w23) >> rsh) & 0xffffu);
-      const int nlex = rbwd ? (cm > 0 ? lex - rstride : lex + (rL - 1) * rstride)
-                            : (cm + 1 < rL ? lex + rstride : lex - (rL - 1) * rstride);
+      const unsigned msk = __shfl_sync(0xffffffffu, bml, m);
+      const int nlex = lex + (((msk >> rbit) & 1u) ? rwrap : rstep);
       const int idx = rnb ? (nlex >> 1) : base + wq + kIlWarps * m;
       const unsigned bar = bar0 + st * 8;
       // the stage was last read by this warp (generic proxy): order those reads
@@ -457,7 +470,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     for (int m = 0; m < nsite; ++m) {
       const int st = m % ST::kStages;
       if (m + ST::kStages - 1 < nsite) issue(m + ST::kStages - 1, (m + ST::kStages - 1) % ST::kStages);
-      const unsigned bf = __shfl_sync(0xffffffffu, bfl, m);
+      // antiperiodic time boundary: the hops that wrap in direction 3
+      const unsigned bf = g.antiperiodic ? (__shfl_sync(0xffffffffu, bml, m) >> 6) & 3u : 0u;
       if (!__all_sync(0xffffffffu, il_wait(bar0 + st * 8, (unsigned)((m / ST::kStages) & 1), a.err))) {
         // a wait gave up: wait (bounded) for this warp's copies still in
         // flight (sites m .. m + kStages - 2), then stop
@@ -466,12 +480,17 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         break;
       }
       const unsigned char* sd = ring + st * ST::kBytes;
-      // two accumulator sets (directions 0, 1 and 2, 3): shorter MMA chains
-      float d[4][4], e[4][4];
+      // upper spins: two sets (even and odd directions: shorter MMA chains);
+      // lower spins: the six phase quads
+      float ua[2][4], ub4[2][4], qq[6][4];
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d[s][q] = e[s][q] = 0.0f;
+        for (int c = 0; c < 4; ++c) ua[s][c] = ub4[s][c] = 0.0f;
+#pragma unroll
+      for (int s = 0; s < 6; ++s)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) qq[s][c] = 0.0f;
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
         uint2 pf[4], pb[4];
@@ -484,21 +503,35 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         const unsigned ub = l.lw ? *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + kIlLinkSiteBytes + mu * kIlLinkBytes + lb_off) : 0u;
         const unsigned negf = (mu == 3 && (bf & 1u)) ? 0x80008000u : 0u;
         const unsigned negb = (mu == 3 && (bf & 2u)) ? 0x80008000u : 0u;
-        if (mu == 0) il_dir<S, 0, SF>(d, l, pf, pb, uf, ub, negf, negb);
-        else if (mu == 1) il_dir<S, 1, SF>(e, l, pf, pb, uf, ub, negf, negb);
-        else if (mu == 2) il_dir<S, 2, SF>(d, l, pf, pb, uf, ub, negf, negb);
-        else il_dir<S, 3, SF>(e, l, pf, pb, uf, ub, negf, negb);
+        if (mu == 0) il_dir<S, 0, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
+        else if (mu == 1) il_dir<S, 1, SF>(ub4, qq, l, pf, pb, uf, ub, negf, negb);
+        else if (mu == 2) il_dir<S, 2, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
+        else il_dir<S, 3, SF>(ub4, qq, l, pf, pb, uf, ub, negf, negb);
       }
       // epilogue: out = T_out(T_c(c) + s_hop H in), then the CG update / residual;
       // lanes t = 3 compute on the words of t = 0 and store nothing
       uint2* const ost = op + (unsigned)(base + wq + kIlWarps * m) * (kIlSiteBytes / 8);
       uint2* const xst = oxp + (unsigned)(base + wq + kIlWarps * m) * (kIlSiteBytes / 8);
+      // the hopping sum of each spin (rows g, g + 8: re, im, re, im)
+      float hs[4][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        hs[0][c] = __fadd_rn(ua[0][c], ub4[0][c]);
+        hs[1][c] = __fadd_rn(ua[1][c], ub4[1][c]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 4; rr += 2) {
+        // spin 2: i^3 q0 + q1;  spin 3: i^3 q2 + i^2 q3 + i q4 + q5
+        hs[2][rr] = __fadd_rn(qq[0][rr + 1], qq[1][rr]);
+        hs[2][rr + 1] = __fsub_rn(qq[1][rr + 1], qq[0][rr]);
+        hs[3][rr] = __fadd_rn(__fsub_rn(__fsub_rn(qq[2][rr + 1], qq[3][rr]), qq[4][rr + 1]), qq[5][rr]);
+        hs[3][rr + 1] = __fadd_rn(__fsub_rn(qq[4][rr], __fadd_rn(qq[2][rr], qq[3][rr + 1])), qq[5][rr + 1]);
+      }
       float n0 = 0.0f, n1 = 0.0f;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const float tw = s < 2 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
-        const float h0r = __fadd_rn(d[s][0], e[s][0]), h0i = __fadd_rn(d[s][1], e[s][1]);
-        const float h1r = __fadd_rn(d[s][2], e[s][2]), h1i = __fadd_rn(d[s][3], e[s][3]);
+        const float h0r = hs[s][0], h0i = hs[s][1], h1r = hs[s][2], h1i = hs[s][3];
         float2 o0, o1;
         if constexpr (CENTRE != 0) {
           float2 c0 = H::to_f2(cw[s].x), c1 = H::to_f2(cw[s].y);
