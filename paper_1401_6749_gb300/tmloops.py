@@ -295,13 +295,15 @@ def cg_params(tol, max_iter=10000, mode=CG_PLAIN, prec=F64, inner_prec=F32, delt
 
 
 def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
-    """Returns (status, list of per-system dicts)."""
+    """Returns (status, list of per-system dicts).  raise_on_noconv=False returns
+    the per-system solver outcomes TM_ERR_NOCONV and TM_ERR_NAN with the stats
+    instead of raising (argument and CUDA errors always raise)."""
     stats = (tm_cg_stats_t * max(int(nrhs), 1))()
     st = _lib.tm_cg_solve(op.handle, _ptr(x), _ptr(eta), int(nrhs), ctypes.byref(params), stats,
                           _stream(stream))
     out = [dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status,
                 rel_res=s.rel_res, true_res=s.true_res) for s in list(stats)[:int(nrhs)]]
-    if st != 0 and (st != 3 or raise_on_noconv):
+    if st != 0 and (st not in (3, 4) or raise_on_noconv):
         _check(st)
     return st, out
 
@@ -320,7 +322,7 @@ def tm_cg_solve_group(ops, xs, etas, nrhs, params, stream=None, raise_on_noconv=
                                 ctypes.byref(params), sp, _stream(stream))
     out = [[dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status, rel_res=s.rel_res,
                  true_res=s.true_res) for s in list(ss)[:int(k)]] for ss, k in zip(stats, nrhs)]
-    if st != 0 and (st != 3 or raise_on_noconv):
+    if st != 0 and (st not in (3, 4) or raise_on_noconv):
         _check(st)
     return st, out
 

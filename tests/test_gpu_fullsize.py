@@ -1,17 +1,23 @@
-"""Parity at the full benchmark size, in the launch configuration bench.py times:
-32^3 x 64, kappa = 0.161, mu = 0.003, the bench's gauge seed, batches of 16
-systems, FP16 LP fields and 12-real links.
+"""Parity at the full benchmark size: 32^3 x 64, kappa = 0.161, mu = 0.003, the
+bench's gauge seed and link format (recon 0: 12-real FP32 links, 18-real
+FP16/BF16 links), batches of 16 systems.
 
 Checked on sampled outputs the oracle computes one by one, or whole for one
 system where that takes seconds:
   * Z4 noise: bit-exact for one full source;
-  * Dslash on 16 FP16 systems (and one FP32 system): 2 x 512 sampled sites,
-    among them every time-boundary case, against the oracle's formula on the
-    same rounded inputs;
-  * the LP solve of a source is bit-identical inside the batch and alone;
+  * Dslash on 16 FP16 systems with the 18-real FP16 links, both on the
+    standard layout (CUDA-core kernel) and on the system-interleaved layout
+    (tensor-core kernel the LP solver uses), and on one FP32 system: 2 x 512
+    sampled sites, among them every time-boundary case, against the oracle's
+    formula on the same rounded inputs;
+  * the LP solve of a source (interleaved layout, Schur) is bit-identical
+    inside the batch and alone;
   * the HP solve (mixed precision, even/odd, 1e-9): the oracle's whole-lattice
     residual |eta - M x| / |eta|;
-  * local loops of one system: the oracle's whole-lattice contraction.
+  * local loops of one system: the oracle's whole-lattice contraction;
+  * one-derivative loops of one system in FP16 and in float-float (the HP
+    loop precision): the oracle's contraction on the time slices t = 0 and
+    T - 1 (both antiperiodic boundary crossings) and one interior slice.
 """
 import numpy as np
 import pytest
@@ -35,7 +41,7 @@ SEED = 20140126
 def setup():
     tl = require_gpu()
     U = synth.gauge_field(L, 1237, device="cuda")
-    op = tl.Operator(L, KAPPA, MU, torch.from_numpy(U.view(np.float64)).cuda(), recon=12)
+    op = tl.Operator(L, KAPPA, MU, torch.from_numpy(U.view(np.float64)).cuda(), recon=0)
     yield tl, U, op
     op.close()
 
@@ -63,13 +69,22 @@ def test_noise_full_source_bit_exact(setup):
     np.testing.assert_array_equal(_unpack_one(tl, f, tl.F16, 1, 2), oz4(L, SEED, 41, 1)[0])
 
 
-@pytest.mark.parametrize("prec,n,tol", [(2, 16, 16 * UNIT_ROUNDOFF[2]), (1, 1, 1e-6)])
-def test_dslash_sampled_sites(setup, prec, n, tol):
+@pytest.mark.parametrize("prec,n,tol,il", [(2, 16, 16 * UNIT_ROUNDOFF[2], False), (2, 16, 16 * UNIT_ROUNDOFF[2], True),
+                                            (1, 1, 1e-6, False)])
+def test_dslash_sampled_sites(setup, prec, n, tol, il):
     tl, U, op = setup
     fin = tl.empty_field(L, prec, n)
     fout = tl.empty_field(L, prec, n)
     tl.z4_noise(L, fin, prec, 7, 0, n)
-    tl.tm_dslash(op, fout, fin, n, prec=prec)
+    if il:
+        fin_il = tl.empty_field_il(L, n)
+        fout_il = tl.empty_field_il(L, n)
+        tl.tm_spinor_to_il(L, fin_il, fin, prec, n)
+        tl.tm_dslash_il(op, fout_il, fin_il, n, prec=prec)
+        tl.tm_spinor_from_il(L, fout, fout_il, prec, n)
+        del fin_il, fout_il
+    else:
+        tl.tm_dslash(op, fout, fin, n, prec=prec)
     sites = _sites(512, 3)
     for r in sorted({0, n - 1}):
         psi = _unpack_one(tl, fin, prec, r, n)
@@ -114,3 +129,42 @@ def test_hp_solution_residual_and_local_loops(setup):
     tl.loop_contract_local(L, x, x, tl.F64, 1, tl.LOOP_VV, out)
     got = from_dev(out, (16, L[3]))
     assert rel_l2(got, oloops.local_loops(s, s, "vv")) < 1e-12
+
+
+def _oneD_slice(U, left, right, mode, t):
+    """The oracle's one-derivative loops of time slice t (array (4, 16)): its
+    contraction on the three slices t - 1, t, t + 1, cut out as a lattice of
+    extent 3 in time (middle slice exact), with the antiperiodic sign moved
+    onto the slice across the boundary."""
+    T = L[3]
+    idx = [(t - 1) % T, t, (t + 1) % T]
+    lf, rf = left[idx].copy(), right[idx].copy()
+    if t == 0:
+        lf[0] *= -1
+        rf[0] *= -1
+    if t == T - 1:
+        lf[2] *= -1
+        rf[2] *= -1
+    return oloops.oneD_loops(U[:, idx], lf, rf, mode, antiperiodic=False)[..., 1]
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 4e-3), (4, 1e-10)])
+def test_oneD_loops_sampled_slices(setup, prec, tol):
+    """One system's one-derivative loops (generalised estimator, L = s, R = an
+    independent field) in FP16 (links and fields rounded to FP16: 4e-3) and in
+    float-float (1e-10) against the oracle on three time slices."""
+    tl, U, op = setup
+    a = synth.random_spinor(L, 1, seed=61)
+    b = synth.random_spinor(L, 1, seed=62)
+    fa = tl.empty_field(L, prec, 1)
+    fb = tl.empty_field(L, prec, 1)
+    tl.tm_spinor_pack(L, fa, prec, torch.from_numpy(a.view(np.float64).copy()).cuda(), 1)
+    tl.tm_spinor_pack(L, fb, prec, torch.from_numpy(b.view(np.float64).copy()).cuda(), 1)
+    out = torch.empty(64 * L[3] * 2, dtype=torch.float64, device="cuda")
+    tl.loop_contract_oneD(op, fa, fb, prec, 1, tl.LOOP_GEN, out)
+    got = from_dev(out, (4, 16, L[3]))
+    la = _unpack_one(tl, fa, prec, 0, 1)    # the values the kernel read
+    lb = _unpack_one(tl, fb, prec, 0, 1)
+    for t in (0, 17, L[3] - 1):
+        ref = _oneD_slice(U, la, lb, "gen", t)
+        assert rel_l2(got[..., t], ref) < tol, t
