@@ -31,6 +31,10 @@ CONFIGS = {
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
                   seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
+    # the same layout on 24^3 x 48 (fields larger than L2): the size of the ncu captures
+    "tsm24": dict(L=(24, 24, 24, 48), kappa=0.161, mu=0.003, n_hp=8, n_lp=24, batch=16,
+                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
+                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
@@ -156,12 +160,24 @@ def _barrier(dist):
         dist.barrier()
 
 
-def _traffic_per_launch(alg_bytes):
-    """DRAM bytes per launch of the Dslash kernel: the ncu-measured traffic per
-    algorithmic byte (profiles/dslash_traffic.txt) times this launch's
-    algorithmic bytes; None if the kernel sources changed since the capture."""
+# ncu DRAM traffic per algorithmic byte, per Dslash kernel class: the
+# committed summary and the sources its capture was taken from
+TRAFFIC_FILES = {"dslash.f16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "tm_core.cuh")),
+                 "dslash.bf16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "tm_core.cuh")),
+                 "dslash.f16": ("dslash_traffic.txt", ("dslash.cuh", "tm_core.cuh")),
+                 "dslash.bf16": ("dslash_traffic.txt", ("dslash.cuh", "tm_core.cuh"))}
+
+
+def _traffic_per_launch(alg_bytes, kernel="dslash.f16.out"):
+    """DRAM bytes per launch of a Dslash kernel class: the ncu-measured traffic
+    per algorithmic byte (profiles/<file>) times this launch's algorithmic
+    bytes; None if there is no capture for the class or its kernel sources
+    changed since the capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dslash_traffic.txt")
+    entry = TRAFFIC_FILES.get(kernel.rsplit(".", 1)[0])
+    if entry is None:
+        return None
+    path = os.path.join(ROOT, "profiles", entry[0])
     if not os.path.exists(path):
         return None
     kv = {}
@@ -171,7 +187,7 @@ def _traffic_per_launch(alg_bytes):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
     csrc = os.path.join(ROOT, "paper_1401_6749_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in ("dslash.cuh", "tm_core.cuh"))
+    src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in entry[1])
     if hashlib.sha256(src).hexdigest() != kv.get("kernel_sources_sha256"):
         return None
     return int(round(float(kv["traffic_per_algorithmic_byte"]) * alg_bytes))
@@ -252,18 +268,64 @@ def _observables(pipe, c):
     return out
 
 
-def _equal_error(obs, c, t_step, t_plain_src):
-    """1 / (R_C R_E^2) per observable: cost x error^2 of plain FP64 CG over that of TSM."""
+def _tsm_efficiency(obs_step, obs_side, c, t_step, t_plain_src, phase):
+    """The paper's efficiency ratios of the TSM (Sec. 4, Table tab:TSM and
+    Table compRatios) for three volume-summed observables.
+
+    TSM error of the step:  err^2 = Var(hp - lp) / N_HP + Var(lp) / N_LP (Eq. 4);
+    plain estimator: N_plain = N_HP + N_LP high-precision sources (as many
+    stochastic sources as the step), err^2 = Var(hp) / N_plain, cost
+    N_plain x t_plain (single-system FP64 CG on this GPU with the same
+    contractions).  R_E = err_TSM / err_plain, R_C = t_step / (N_plain t_plain),
+    R_C R_E^2 and its inverse (the equal-error speedup) do not depend on
+    N_plain.  The variances come from the step's N_HP paired (HP, LP) sources
+    plus the side run's paired sources (Var(hp), Var(hp - lp)) and from every
+    LP value (Var(lp)); errors by jackknife over the paired sources.
+    R_HP/LP (Sec. 4): time of one HP source (solve + contractions) over that
+    of one LP source, with the local loops only and with the one-derivative
+    loops as well, from the phase times of one step."""
     import numpy as np
-    n_hp = c["n_hp"]
-    res = {}
-    for name, (hp, lp) in obs.items():
-        # total (real + imaginary) sample variances of the complex observable
-        d = hp - lp[:n_hp]
-        err2 = d.var(ddof=1) / n_hp + lp[n_hp:].var(ddof=1) / (lp.size - n_hp)
-        var_plain = hp.var(ddof=1)
-        res[name] = float((t_plain_src * var_plain) / (t_step * err2)) if err2 > 0 else None
-    return res
+    n_hp, n_lp = c["n_hp"], c["n_lp"]
+    n_plain = n_hp + n_lp
+    out = {"definition": "R_E = err_TSM / err_plain, R_C = cost_TSM / cost_plain with N_plain = N_HP + N_LP "
+                         "plain FP64-CG sources; R_C R_E^2 independent of N_plain; jackknife errors over "
+                         "paired (HP, LP) sources",
+           "n_plain": n_plain, "observables": {}}
+    for name in obs_step:
+        hp = np.concatenate([obs_step[name][0], obs_side[name][0]])
+        lp_pair = np.concatenate([obs_step[name][1][:n_hp], obs_side[name][1]])
+        lp_rest = obs_step[name][1][n_hp:]
+        npair = hp.size
+
+        def ratios(keep):
+            h, lpp = hp[keep], lp_pair[keep]
+            var_d = (h - lpp).var(ddof=1)
+            var_lp = np.concatenate([lpp, lp_rest]).var(ddof=1)
+            var_plain = h.var(ddof=1)
+            err2_tsm = var_d / n_hp + var_lp / n_lp
+            err2_plain = var_plain / n_plain
+            r_e = float(np.sqrt(err2_tsm / err2_plain))
+            r_c = float(t_step / (n_plain * t_plain_src))
+            return r_e, r_c, r_c * r_e ** 2
+        r_e, r_c, prod = ratios(np.ones(npair, bool))
+        jk = np.array([ratios(np.arange(npair) != i) for i in range(npair)])
+        jerr = np.sqrt((npair - 1) / npair * ((jk - jk.mean(axis=0)) ** 2).sum(axis=0))
+        out["observables"][name] = {"R_E": round(r_e, 4), "R_E_err": round(float(jerr[0]), 4),
+                                    "R_C": round(r_c, 5), "R_C_R_E2": round(prod, 5),
+                                    "R_C_R_E2_err": round(float(jerr[2]), 5),
+                                    "equal_error_speedup": round(1.0 / prod, 2) if prod > 0 else None,
+                                    "paired_sources": int(npair), "lp_values": int(npair + lp_rest.size)}
+    if phase:
+        t_hp = {k: v / n_hp for k, v in phase["hp"].items()}
+        t_lp = {k: v / (n_hp + n_lp) for k, v in phase["lp"].items()}
+        out["R_HP_LP"] = {
+            "local": round((t_hp["solve"] + t_hp["local"]) / (t_lp["solve"] + t_lp["local"]), 2),
+            "with_one_derivative": round(sum(t_hp.values()) / sum(t_lp.values()), 2),
+            "ms_per_source": {"hp": {k: round(v, 3) for k, v in t_hp.items()},
+                              "lp": {k: round(v, 4) for k, v in t_lp.items()}}}
+    out["paper_context"] = ("paper (unnamed GPUs, real N_f=2+1+1 ensemble, one-end trick): R_C R_E^2 light "
+                            "0.73 (sigma-term) / 0.15 (g_A); R_HP/LP light ~26.7 local, ~10 with one-derivative")
+    return out
 
 
 def run_ours(args):
@@ -286,10 +348,10 @@ def run_ours(args):
     del U
     op = tl.Operator(L, c["kappa"], c["mu"], U_dev, recon=c["recon"])
     n_src = c["n_hp"] + c["n_lp"]
-    mk = lambda o: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
+    mk = lambda o, **kw: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
                                hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
                                seed=c["seed"], first_src=rank * n_src, schur=c["schur"],
-                               delta=c["delta"], overlap=c["overlap"], hp_loop_prec=tl.PREC[c["hp_loops"]])
+                               delta=c["delta"], overlap=c["overlap"], hp_loop_prec=tl.PREC[c["hp_loops"]], **kw)
     pipe = mk(op)
     _log("inputs ready")
     for _ in range(args.warmup):
@@ -343,7 +405,7 @@ def run_ours(args):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     n_dom, t_dom, b_dom = classes[dom]
     ach = kernels[dom]["GBps"]
-    traffic = _traffic_per_launch(b_dom / n_dom) if dom.startswith("dslash.") else None
+    traffic = _traffic_per_launch(b_dom / n_dom, dom) if dom.startswith("dslash.") else None
     hbm_view = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_source": peak_src}
     flops_dom = flops.get(dom, 0.0)
@@ -378,7 +440,7 @@ def run_ours(args):
 
     # ---- plain single-RHS FP64 CG on the same GPU (equal-error baseline)
     t_plain = None
-    speedup = None
+    efficiency = None
     if not args.no_baseline:
         n_plain = 2
         eta = tl.empty_field(L, tl.F64, 1)
@@ -403,7 +465,25 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_plain = (time.perf_counter() - t0) / n_plain
         _log("plain FP64 CG: %.3f s/source" % t_plain)
-        speedup = _equal_error(_observables(pipe, c), c, ms * 1e-3, t_plain)
+        # phase times of one step (solve / local loops / one-derivative loops of
+        # the LP and HP sets) and the variances from a side run of paired
+        # (HP, LP) sources beyond the step's, both outside the timed region
+        pt = mk(op, timing=True)
+        pt.run(dist)
+        phase = pt.phase_ms()
+        obs_step = _observables(pipe, c)
+        n_side = 32
+        del pt
+        side = TsmPipeline(op, n_side, 0, batch=c["n_hp"], lp_prec=tl.PREC[c["lp_prec"]],
+                           hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
+                           seed=c["seed"], first_src=world * n_src + rank * n_side, schur=c["schur"],
+                           delta=c["delta"], hp_loop_prec=tl.PREC[c["hp_loops"]])
+        side.run_sources()
+        side_ok = all(s["status"] == 0 for s in side.stats_hp + side.stats_lp)
+        obs_side = _observables(side, dict(c, n_hp=n_side))
+        efficiency = _tsm_efficiency(obs_step, obs_side, c, ms * 1e-3, t_plain, phase)
+        efficiency["side_run_converged"] = side_ok
+        del side
 
     # ---- end to end through host buffers: H2D gauge field, operator set-up,
     # the full step, D2H of the combined loops, every step
@@ -485,7 +565,7 @@ def run_ours(args):
                        "hp_true_res_max": max(s["true_res"] for s in pipe.stats_hp) if pipe.stats_hp else None,
                        "all_converged": ok},
             "fp64_cg_plain_s_per_source": round(t_plain, 4) if t_plain else None,
-            "equal_error_speedup_vs_fp64_cg": speedup,
+            "tsm_efficiency": efficiency,
             "dslash_shapes": _tuned_shapes(tl, L),
             "dslash_alone": dslash_alone,
         }
@@ -735,21 +815,16 @@ def run_solvers(args):
 
 
 # ----------------------------------------------------------------- oracle
-def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
-    """Time the FP64 oracle, as it stands, on a bounded sample: one M^dag M
+def _oracle_sample(c, Ls, seed):
+    """One unit of the oracle's work on the sample lattice Ls: one M^dag M
     application (one CG iteration's operator work) and one source's local and
-    one-derivative contractions in both one-end estimators, on a 16^3 x 32
-    lattice with the workload's kappa and mu.  The per-site cost is scaled to
-    the workload's volume and combined with the iteration counts of the
-    oracle's (unpreconditioned) CG for the LP and HP solves to give seconds
-    per source."""
-    import numpy as np
+    one-derivative contractions in both one-end estimators.  Returns the two
+    wall times (seconds)."""
     from oracle import loops as oloops
     from oracle.operator import apply_DW, apply_M
     from paper_1401_6749_gb300 import synth
-    Ls = sample_L
     U = synth.gauge_field(Ls, c["gauge_seed"])
-    psi = synth.random_spinor(Ls, 1, 5)[0]
+    psi = synth.random_spinor(Ls, 1, seed)[0]
     t0 = time.perf_counter()
     y = apply_M(U, apply_M(U, psi, c["kappa"], c["mu"]), c["kappa"], c["mu"], dagger=True)
     t_iter = time.perf_counter() - t0
@@ -761,15 +836,76 @@ def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32)):
         oloops.oneD_loops(U, left, right, mode)
     t_con = time.perf_counter() - t0
     del y
+    return t_iter, t_con
+
+
+def _oracle_worker(c, Ls, seed, barrier, queue):
+    """A process of the all-core run: its inputs built, it waits for the
+    others, then times one unit of the oracle's work."""
+    _oracle_sample(c, (2, 2, 2, 2), seed)  # imports and first-touch work outside the timing
+    barrier.wait()
+    queue.put(_oracle_sample(c, Ls, seed))
+
+
+def _oracle_all_cores(c, Ls, procs):
+    """procs single-threaded processes (spawned, one per host core) each run
+    one unit at the same time; returns the median per-process times."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier, queue = ctx.Barrier(procs), ctx.Queue()
+        ps = [ctx.Process(target=_oracle_worker, args=(c, Ls, 5 + i, barrier, queue)) for i in range(procs)]
+        for p in ps:
+            p.start()
+        res = [queue.get() for _ in ps]
+        for p in ps:
+            p.join()
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return statistics.median(r[0] for r in res), statistics.median(r[1] for r in res)
+
+
+def cpu_baseline(c, it_lp, it_hp, sample_L=(16, 16, 16, 32), all_cores=True):
+    """Time the FP64 oracle, as it stands, on a bounded sample (_oracle_sample
+    on a 16^3 x 32 lattice with the workload's kappa and mu), on one core and
+    on all host cores (one single-threaded process per core, each running the
+    same unit at the same time: the machine's throughput is procs units per
+    per-process time).  The per-site cost is scaled to the workload's volume
+    and combined with the iteration counts of the unpreconditioned CG (the
+    oracle's algorithm; counted on this GPU for the workload, since the oracle
+    cannot run it in bounded time) for the LP and HP solves to give seconds
+    per source."""
+    import numpy as np
+    Ls = sample_L
     scale = float(np.prod(c["L"])) / float(np.prod(Ls))
     n_src = c["n_hp"] + c["n_lp"]
     iters = sum(it_lp) + sum(it_hp)
-    per_src = scale * (t_iter * iters + t_con * (n_src + c["n_hp"])) / n_src
-    return {"value": round(per_src, 3), "unit": "s/source", "cores": 1, "kind": "oracle",
-            "sample": "numpy FP64 oracle on %dx%dx%dx%d: one M^dag M application %.2f s, "
-                      "local+oneD contractions (vv, gen) of one source %.2f s; scaled by volume "
-                      "(x%g) and by the unpreconditioned CG iterations of the step (%d LP + %d HP)"
-                      % (Ls + (t_iter, t_con, scale, sum(it_lp), sum(it_hp)))}
+
+    def per_source(t_iter, t_con, procs):
+        return scale * (t_iter * iters + t_con * (n_src + c["n_hp"])) / n_src / procs
+
+    t1 = _oracle_sample(c, Ls, 5)
+    one = per_source(t1[0], t1[1], 1)
+    procs = os.cpu_count() or 1
+    out = {"value": round(one, 3), "unit": "s/source", "cores": 1, "kind": "oracle"}
+    if all_cores and procs > 1:
+        tp = _oracle_all_cores(c, Ls, procs)
+        out.update(value=round(per_source(tp[0], tp[1], procs), 3), cores=procs,
+                   single_core={"value": round(one, 3), "unit": "s/source", "cores": 1})
+    else:
+        tp = t1
+    out["sample"] = ("numpy FP64 oracle on %dx%dx%dx%d: one M^dag M application %.2f s, local+oneD "
+                     "contractions (vv, gen) of one source %.2f s per process (1 core: %.2f s, %.2f s); "
+                     "scaled by volume (x%g) and by the unpreconditioned CG iterations of the step "
+                     "(%d LP + %d HP)" % (Ls + (tp[0], tp[1], t1[0], t1[1], scale, sum(it_lp), sum(it_hp))))
+    return out
 
 
 def run_reference(args):
@@ -792,12 +928,12 @@ def run_reference(args):
     v = statistics.median(vals)
     cb["value"] = v
     n_src = c["n_hp"] + c["n_lp"]
-    # ms_per_step: the oracle's time for one whole step of the workload (all
-    # sources), extrapolated from the sample; sample_ms_per_step: the wall time
-    # of one bounded sample as run
+    # a step of this arm is one bounded sample: ms_per_step is its wall time;
+    # workload_ms_per_step is the oracle's time for one whole step of the
+    # workload (all sources), extrapolated from the sample
     line = {"metric": METRIC, "value": v, "unit": "s/source", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(v * n_src * 1e3, 1),
-            "sample_ms_per_step": round(statistics.median(walls) * 1e3, 1),
+            "warmup": args.warmup, "ms_per_step": round(statistics.median(walls) * 1e3, 1),
+            "workload_ms_per_step": round(v * n_src * 1e3, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_name(c)}, "cpu_baseline": cb,

@@ -272,7 +272,7 @@ __device__ __forceinline__ void il_store(uint2* p, unsigned w0, unsigned w1, boo
 constexpr int kIlSiteBytes = 768;
 constexpr int kIlLinkBytes = 48;                 // one direction of one site: 9 words + 3 pad
 constexpr int kIlLinkSiteBytes = 4 * kIlLinkBytes;
-constexpr int kIlGroups = 4;                     // 32-site groups per block (128 sites)
+constexpr int kIlGroups = 2;                     // 32-site groups per block
 constexpr unsigned kIlWaitLimit = 1u << 22;      // try_wait rounds before a wait gives up
 
 template <int EPI>
@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
   const int base = cg * (kIlGroups * 32);
   // sites of this warp: base + wq + 4 m, m = 0 .. nsite - 1
   const int left = g.Vh - base - wq;
-  const int nsite = left <= 0 ? 0 : min(32, (left + kIlWarps - 1) / kIlWarps);
+  constexpr int kWarpSites = kIlGroups * 32 / kIlWarps;  // sites of one warp in a full block
+  const int nsite = left <= 0 ? 0 : min(kWarpSites, (left + kIlWarps - 1) / kIlWarps);
   if (__any_sync(0xffffffffu, act0 || act1) && nsite > 0) {
     // lane m: the warp's site m: lex index and a mask of the hops that wrap
     // around the lattice (bit 2 mu: forward, 2 mu + 1: backward)
@@ -584,6 +585,7 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         if (act0) nacc0 = __fadd_rn(nacc0, n0);
         if (act1) nacc1 = __fadd_rn(nacc1, n1);
         // site base + wq + 4 m lies in 32-site group m / 8: flush at the group's end
+        static_assert(kIlWarps == 4, "a warp takes 8 sites of each 32-site group");
         if ((m & 7) == 7 || m == nsite - 1) {
           nacc0 = __fadd_rn(nacc0, __shfl_xor_sync(0xffffffffu, nacc0, 1));
           nacc0 = __fadd_rn(nacc0, __shfl_xor_sync(0xffffffffu, nacc0, 2));

@@ -31,11 +31,14 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
-                 delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64):
+                 delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False):
         """overlap: run the high-precision solves and contractions on a second
         stream from a host thread, concurrently with the low-precision batches
         (FP64 work uses other units than the FP32 arithmetic of the LP solves);
-        needs its own operator handle (a clone sharing the links)."""
+        needs its own operator handle (a clone sharing the links).
+        timing: record CUDA events around the phases of every batch (solve,
+        local loops with the D_W of the generalised estimator, one-derivative
+        loops), read by phase_ms() after a run."""
         self.op = op
         self.overlap = bool(overlap)
         self.op_hp = op.clone() if self.overlap else op
@@ -70,9 +73,27 @@ class TsmPipeline:
         nf = 3 if hp_loop_prec == tl.F64 else 5
         self._hp = [tl.empty_field(self.L, tl.F64, nh) for _ in range(nf)] if self.n_hp else None
         self.stats_lp, self.stats_hp = [], []
+        self.timing = bool(timing)
+        self._events = []  # (set "lp"/"hp", [e_start, e_solved, e_local, e_oned])
 
-    def _contract(self, op, x, g5w, prec, n, dst, row0, stream, eta=None):
-        for k in self.kinds:
+    def _event(self, stream):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream if stream is not None else torch.cuda.current_stream())
+        return e
+
+    def phase_ms(self):
+        """Device milliseconds of the last run per set and phase:
+        {"lp": {"solve", "local", "oneD"}, "hp": {...}} (synchronises)."""
+        torch.cuda.synchronize()
+        out = {k: {"solve": 0.0, "local": 0.0, "oneD": 0.0} for k in ("lp", "hp")}
+        for which, ev in self._events:
+            out[which]["solve"] += ev[0].elapsed_time(ev[1])
+            out[which]["local"] += ev[1].elapsed_time(ev[2])
+            out[which]["oneD"] += ev[2].elapsed_time(ev[3])
+        return out
+
+    def _contract(self, op, x, g5w, prec, n, dst, row0, stream, eta=None, kinds=None):
+        for k in (self.kinds if kinds is None else kinds):
             kind, mode = k.split("_")
             left, right = {"vv": (x, x), "gen": (x, g5w), "std": (eta, x)}[mode]
             out = dst[k][row0:row0 + n]
@@ -82,8 +103,9 @@ class TsmPipeline:
                 tl.loop_contract_oneD(op, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
 
     def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None,
-                            loop_prec=None):
+                            loop_prec=None, which="lp"):
         eta, x, g5w = fields[:3]
+        ev = [self._event(stream)] if self.timing else None
         tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
         st, stats = tl.tm_cg_solve(op, x, eta, n, params, stream, raise_on_noconv=False)
         if loop_prec is not None and loop_prec != prec:
@@ -93,9 +115,19 @@ class TsmPipeline:
             if any(k.endswith("std") for k in self.kinds):
                 tl.tm_spinor_convert(self.L, eta_l, loop_prec, eta, prec, n, stream)
             eta, x, prec = eta_l, x_l, loop_prec
+        if ev:
+            ev.append(self._event(stream))
         if any("gen" in k for k in self.kinds):
             tl.tm_dslash_g5(op, g5w, x, n, mu_zero=True, prec=prec, stream=stream)   # g5 D_W s
-        self._contract(op, x, g5w, prec, n, dst, row0, stream, eta)
+        local = tuple(k for k in self.kinds if k.startswith("local"))
+        oned = tuple(k for k in self.kinds if k.startswith("oneD"))
+        self._contract(op, x, g5w, prec, n, dst, row0, stream, eta, local)
+        if ev:
+            ev.append(self._event(stream))
+        self._contract(op, x, g5w, prec, n, dst, row0, stream, eta, oned)
+        if ev:
+            ev.append(self._event(stream))
+            self._events.append((which, ev))
         return stats
 
     def _run_hp(self, stream):
@@ -106,7 +138,7 @@ class TsmPipeline:
             n = min(self.batch, self.n_hp - b0)
             stats += self._solve_and_contract(self.op_hp, self._hp, tl.F64, self.first + b0, n,
                                               hp_params, self.hp_loops, b0, stream,
-                                              loop_prec=self.hp_loop_prec)
+                                              loop_prec=self.hp_loop_prec, which="hp")
         self.stats_hp = stats
 
     def run(self, dist=None):
@@ -115,8 +147,17 @@ class TsmPipeline:
         With a torch.distributed module whose world size exceeds one, every rank
         runs its own sources (first_src set per rank) and the estimate combines
         the sources of all ranks (one all-gather of the per-source loops)."""
+        self.run_sources()
+        if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+            return self.combine_global(dist)
+        return self.combine()
+
+    def run_sources(self):
+        """The solves and contractions of every source (per-source loops in
+        lp_loops / hp_loops), without the combination."""
         n_all = self.n_hp + self.n_lp
         self.stats_lp, self.stats_hp = [], []
+        self._events = []
         main = torch.cuda.current_stream()
         worker = None
         if self.n_hp and self.overlap:
@@ -137,9 +178,6 @@ class TsmPipeline:
             main.wait_stream(self.hp_stream)
         elif self.n_hp:
             self._run_hp(main)
-        if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
-            return self.combine_global(dist)
-        return self.combine()
 
     def _combine_sets(self, k, hp, lphp, lp, n_hp, n_lp):
         length = self.len[k.split("_")[0]]

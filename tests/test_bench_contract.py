@@ -40,7 +40,7 @@ def test_traffic_ratio_applies_only_to_the_captured_sources():
                 kv[k.strip()] = v.strip()
     csrc = os.path.join(ROOT, "paper_1401_6749_gb300", "csrc")
     src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in ("dslash.cuh", "tm_core.cuh"))
-    got = bench._traffic_per_launch(1_000_000)
+    got = bench._traffic_per_launch(1_000_000, "dslash.f16.out")
     if hashlib.sha256(src).hexdigest() == kv["kernel_sources_sha256"]:
         assert got == round(float(kv["traffic_per_algorithmic_byte"]) * 1_000_000)
     else:
