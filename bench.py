@@ -334,7 +334,13 @@ def run_ours(args):
     dist, rank, world = _dist()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     import __graft_entry__
-    __graft_entry__.build()
+    # rank 0 builds the library; the other ranks wait, then find it up to date
+    # (the build also serialises concurrent callers on a lock file)
+    if rank == 0:
+        __graft_entry__.build()
+    _barrier(dist)
+    if rank != 0:
+        __graft_entry__.build()
     from paper_1401_6749_gb300 import synth
     from paper_1401_6749_gb300 import tmloops as tl
     from paper_1401_6749_gb300.tsm_pipeline import TsmPipeline

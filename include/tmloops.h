@@ -342,6 +342,12 @@ tm_status_t loop_contract_local_noalloc(const tm_geom_t *g, const void *left, co
 tm_status_t tsm_combine(const double *l_hp, const double *l_lp_on_hp, int n_hp,
                         const double *l_lp, int n_lp, size_t len, double scale_re,
                         double scale_im, double *mean, double *err, tm_stream_t s);
+/* The same combination (same formula and operation order per component) on
+ * HOST arrays, synchronous: for per-source loops gathered on the host or across
+ * processes, which are small (kilobytes per source).  Arguments as above. */
+tm_status_t tsm_combine_host(const double *l_hp, const double *l_lp_on_hp, int n_hp,
+                             const double *l_lp, int n_lp, size_t len, double scale_re,
+                             double scale_im, double *mean, double *err);
 
 /* Diagnostics.  tm_last_error: thread-local text of the last failure.
  * tm_launch_count: kernels this library launched so far (all threads).

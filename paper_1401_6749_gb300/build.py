@@ -1,10 +1,16 @@
 """Build the tmloops C-ABI library (libtmloops.so) in-tree for sm_103a.
 
 Each translation unit in csrc/ is compiled by nvcc in parallel, then linked
-into one shared library next to this file.  Rebuilds only when a source or
-header is newer than the library.
+into one shared library next to this file.  Rebuilds only when the contents
+of a source, a header or the flags differ from those the library was built
+from (a hash in _build/flags.txt; file times play no part).  Concurrent
+callers (e.g. the ranks of a torchrun job) serialise on a lock file: the
+first builds, the others find the library up to date.
 """
+import contextlib
+import fcntl
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -47,22 +53,49 @@ def _extra_flags():
     return os.environ.get("TMLOOPS_EXTRA_NVCC", "").split()
 
 
+def _fingerprint():
+    """Hash of the flags and of every source and header the library is built from."""
+    h = hashlib.sha256(" ".join(NVCC_FLAGS + _extra_flags()).encode())
+    for d in sorted(_deps()):
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def up_to_date():
     if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
     with open(STAMP) as f:
-        if f.read() != " ".join(NVCC_FLAGS + _extra_flags()):
-            return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+        return f.read().strip() == _fingerprint()
+
+
+@contextlib.contextmanager
+def build_lock():
+    """Exclusive lock of the build directory (blocks until it is free)."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
 
 
 def build(force=False, verbose=False, jobs=None):
     """Compile csrc/*.cu and link libtmloops.so; returns the library path."""
     if not force and up_to_date():
         return LIB
+    with build_lock():
+        if not force and up_to_date():  # another process built it meanwhile
+            return LIB
+        return _build(verbose, jobs)
+
+
+def _build(verbose, jobs):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    fp = _fingerprint()
     srcs = _sources()
 
     def compile_one(src):
@@ -86,7 +119,7 @@ def build(force=False, verbose=False, jobs=None):
         raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
     os.replace(tmp, LIB)
     with open(STAMP, "w") as f:
-        f.write(" ".join(NVCC_FLAGS + _extra_flags()))
+        f.write(fp)
     return LIB
 
 

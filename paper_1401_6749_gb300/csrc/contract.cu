@@ -13,7 +13,9 @@
 // butterfly (transpose-reduce) leaves lane j with component j, the eight warp
 // results are added in order, and a final kernel adds the chunk partials in
 // order.
+#include <cmath>
 #include <cstring>
+#include <limits>
 
 #include "dslash.cuh"
 
@@ -684,6 +686,72 @@ extern "C" tm_status_t loop_contract_oneD(tm_op_t* op, const void* left, const v
   }
   dev_free(scratch, s);
   return st;
+}
+
+// The same combination on host arrays: the per-source loop sets are small
+// (kilobytes per source), so a caller that gathered them on the host (or
+// across processes) combines them without a device round trip.  Each
+// component is computed with the device kernel's formula in the same order.
+extern "C" tm_status_t tsm_combine_host(const double* l_hp, const double* l_lp_on_hp, int n_hp,
+                                        const double* l_lp, int n_lp, size_t len, double scale_re,
+                                        double scale_im, double* mean, double* err) {
+  if (!l_lp || !mean || !err || n_hp < 0) { set_error("tsm_combine_host: null argument"); return TM_ERR_ARG; }
+  if (n_lp < 1) { set_error("tsm_combine_host: the estimator needs n_lp >= 1"); return TM_ERR_ARG; }
+  if (n_hp > 0 && (!l_hp || !l_lp_on_hp)) { set_error("tsm_combine_host: null high-precision arrays"); return TM_ERR_ARG; }
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  auto sc = [&](const double* a, size_t idx, double& re, double& im) {
+    const double xr = a[2 * idx], xi = a[2 * idx + 1];
+    re = scale_re * xr - scale_im * xi;
+    im = scale_re * xi + scale_im * xr;
+  };
+  for (size_t j = 0; j < len; ++j) {
+    double mr = 0, mi = 0, re, im;
+    for (int i = 0; i < n_lp; ++i) { sc(l_lp, (size_t)i * len + j, re, im); mr += re; mi += im; }
+    mr /= n_lp;
+    mi /= n_lp;
+    double e2r = nan, e2i = nan;
+    if (n_lp > 1) {
+      double vr = 0, vi = 0;
+      for (int i = 0; i < n_lp; ++i) {
+        sc(l_lp, (size_t)i * len + j, re, im);
+        vr += (re - mr) * (re - mr);
+        vi += (im - mi) * (im - mi);
+      }
+      e2r = vr / (n_lp - 1) / n_lp;
+      e2i = vi / (n_lp - 1) / n_lp;
+    }
+    if (n_hp > 0) {
+      double dr = 0, di = 0, hr, hi;
+      for (int i = 0; i < n_hp; ++i) {
+        sc(l_hp, (size_t)i * len + j, hr, hi);
+        sc(l_lp_on_hp, (size_t)i * len + j, re, im);
+        dr += hr - re;
+        di += hi - im;
+      }
+      dr /= n_hp;
+      di /= n_hp;
+      if (n_hp > 1) {
+        double vr = 0, vi = 0;
+        for (int i = 0; i < n_hp; ++i) {
+          sc(l_hp, (size_t)i * len + j, hr, hi);
+          sc(l_lp_on_hp, (size_t)i * len + j, re, im);
+          vr += (hr - re - dr) * (hr - re - dr);
+          vi += (hi - im - di) * (hi - im - di);
+        }
+        e2r += vr / (n_hp - 1) / n_hp;
+        e2i += vi / (n_hp - 1) / n_hp;
+      } else {
+        e2r = e2i = nan;
+      }
+      mr += dr;
+      mi += di;
+    }
+    mean[2 * j] = mr;
+    mean[2 * j + 1] = mi;
+    err[2 * j] = std::sqrt(e2r);
+    err[2 * j + 1] = std::sqrt(e2i);
+  }
+  return TM_OK;
 }
 
 extern "C" tm_status_t tsm_combine(const double* l_hp, const double* l_lp_on_hp, int n_hp,

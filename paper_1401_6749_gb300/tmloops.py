@@ -101,6 +101,7 @@ _SIGS = {
     "tm_dslash_il": [_vp, _vp, _vp, _i, _i, _i, _i, _vp],
     "tm_cg_il_enable": [_i],
     "tm_op_check": [_vp],
+    "tsm_combine_host": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -348,6 +349,16 @@ def tsm_combine(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, length, scale, mean, err, st
     scale = complex(scale)
     _check(_lib.tsm_combine(_ptr(l_hp), _ptr(l_lp_on_hp), int(n_hp), _ptr(l_lp), int(n_lp),
                             int(length), scale.real, scale.imag, _ptr(mean), _ptr(err), _stream(stream)))
+
+
+def tsm_combine_host(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, length, scale, mean, err):
+    """Eq. 4 on host (CPU) float64 tensors; synchronous."""
+    for t in (l_hp, l_lp_on_hp, l_lp, mean, err):
+        if t is not None and (t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+            raise ValueError("tsm_combine_host takes contiguous float64 host tensors")
+    sc = complex(scale)
+    _check(_lib.tsm_combine_host(_ptr(l_hp), _ptr(l_lp_on_hp), int(n_hp), _ptr(l_lp), int(n_lp),
+                                 int(length), sc.real, sc.imag, _ptr(mean), _ptr(err)))
 
 
 def z4_noise_diluted(L, eta, prec, seed, first_src, nsrc, t0, dt, stream=None):

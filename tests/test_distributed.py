@@ -1,10 +1,13 @@
-"""Multi-process source sharding on CPU (gloo, world size 2).
+"""Multi-process source sharding on CPU (gloo, world sizes 2 and 8).
 
 Each rank fabricates the per-source loop values of its own sources (a
 deterministic function of the global source index, standing in for the GPU
 solves); the gathered sets must equal those of one process that ran all
 sources, in source order, and the global TSM estimate computed from them (here
-with the oracle's combination) must equal the single-process one bit for bit.
+with the oracle's combination standing in for tsm_combine) must equal the
+single-process one bit for bit.  With 8 ranks every rank first runs the
+library build step (as bench.py's ranks do): it serialises on the build lock
+and leaves one library.
 """
 import os
 import socket
@@ -34,10 +37,14 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, out_path):
+def _worker(rank, world, port, out_path, do_build=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    if do_build:
+        from paper_1401_6749_gb300 import build
+        build.build()
+        assert build.up_to_date()
     first, n = rank_sources(rank, N_HP, N_LP)
     hp = torch.tensor(np.stack([_loops_of_source(first + j, True) for j in range(N_HP)]))
     lp = torch.tensor(np.stack([_loops_of_source(first + j, False) for j in range(n)]))
@@ -54,10 +61,10 @@ def test_rank_sources_partition():
     assert idx == list(range(4 * (N_HP + N_LP)))
 
 
-def test_two_rank_gather_matches_single_process(tmp_path):
-    world = 2
+@pytest.mark.parametrize("world", [2, 8])
+def test_rank_gather_matches_single_process(tmp_path, world):
     out = str(tmp_path / "gathered.npz")
-    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    mp.spawn(_worker, args=(world, _free_port(), out, world == 8), nprocs=world, join=True)
     got = np.load(out)
     # single process: sources 0 .. world (N_HP + N_LP) - 1, HP = first N_HP of each rank
     hp, lphp, lp = [], [], []
@@ -75,3 +82,26 @@ def test_two_rank_gather_matches_single_process(tmp_path):
     m2 = otsm.tsm_combine(c(np.stack(hp)), c(np.stack(lphp)), c(np.stack(lp)))
     for a, b in zip(m1, m2):
         np.testing.assert_array_equal(a, b)
+
+
+def _hold_lock(i, q):
+    import time
+    from paper_1401_6749_gb300 import build
+    with build.build_lock():
+        q.put(("in", i, time.monotonic()))
+        time.sleep(0.3)
+        q.put(("out", i, time.monotonic()))
+
+
+def test_build_lock_is_exclusive():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_hold_lock, args=(i, q)) for i in range(3)]
+    for p in ps:
+        p.start()
+    ev = sorted((q.get(timeout=60) for _ in range(6)), key=lambda e: e[2])
+    for p in ps:
+        p.join()
+    # strictly alternating in/out of the same process: no two holders at once
+    for k in range(0, 6, 2):
+        assert ev[k][0] == "in" and ev[k + 1][0] == "out" and ev[k][1] == ev[k + 1][1]
