@@ -328,6 +328,64 @@ def _tsm_efficiency(obs_step, obs_side, c, t_step, t_plain_src, phase):
     return out
 
 
+# twisted masses standing in for the paper's three sectors (Sec. 3: strange
+# and charm near their physical values; the ensemble's own values are not
+# given): the light mass of the workload, and strange / charm masses about
+# 13 and 170 times heavier in lattice units
+SECTOR_MU = {"strange": 0.04, "charm": 0.5}
+
+
+def _efficiency_of(tl, TsmPipeline, op, pipe, c, ms, dist, rank, world, n_src, mk):
+    """Plain FP64 CG time per source on op, phase times of one step, a side run
+    of paired sources, and the efficiency ratios (_tsm_efficiency) of the
+    pipeline `pipe` whose step took `ms` milliseconds."""
+    import torch
+    L = c["L"]
+    n_plain = 2
+    eta = tl.empty_field(L, tl.F64, 1)
+    x = tl.empty_field(L, tl.F64, 1)
+    w = tl.empty_field(L, tl.F64, 1)
+    g5w = tl.empty_field(L, tl.F64, 1)
+    T = L[3]
+    loc = torch.empty(32 * T, dtype=torch.float64, device="cuda")
+    oned = torch.empty(128 * T, dtype=torch.float64, device="cuda")
+    prm = tl.cg_params(c["tol_hp"], 20000, tl.CG_PLAIN, prec=tl.F64, check_every=8, schur=c["schur"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(n_plain):
+        tl.z4_noise(L, eta, tl.F64, c["seed"], rank * n_src + j, 1)
+        tl.tm_cg_solve(op, x, eta, 1, prm)
+        tl.tm_dslash(op, w, x, 1, mu_zero=True, prec=tl.F64)
+        tl.tm_gamma5(L, g5w, w, tl.F64, 1)
+        for left, right, mode in ((x, x, tl.LOOP_VV), (x, g5w, tl.LOOP_GEN)):
+            tl.loop_contract_local(L, left, right, tl.F64, 1, mode, loc)
+            tl.loop_contract_oneD(op, left, right, tl.F64, 1, mode, oned)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / n_plain
+    _log("plain FP64 CG (mu %g): %.3f s/source" % (c["mu"], t_plain))
+    del eta, x, w, g5w
+    # phase times of one step (solve / local loops / one-derivative loops of
+    # the LP and HP sets) and the variances from a side run of paired (HP, LP)
+    # sources beyond the step's, both outside the timed region
+    pt = mk(op, timing=True)
+    pt.run(dist)
+    phase = pt.phase_ms()
+    del pt
+    obs_step = _observables(pipe, c)
+    n_side = 32
+    side = TsmPipeline(op, n_side, 0, batch=c["n_hp"], lp_prec=tl.PREC[c["lp_prec"]],
+                       hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
+                       seed=c["seed"], first_src=world * n_src + rank * n_side, schur=c["schur"],
+                       delta=c["delta"], hp_loop_prec=tl.PREC[c["hp_loops"]])
+    side.run_sources()
+    side_ok = all(s["status"] == 0 for s in side.stats_hp + side.stats_lp)
+    obs_side = _observables(side, dict(c, n_hp=n_side))
+    eff = _tsm_efficiency(obs_step, obs_side, c, ms * 1e-3, t_plain, phase)
+    eff["side_run_converged"] = side_ok
+    eff["fp64_cg_plain_s_per_source"] = round(t_plain, 4)
+    return eff, t_plain
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -444,52 +502,39 @@ def run_ours(args):
     it_hp = [s["iters"] for s in pipe.stats_hp]
     ok = all(s["status"] == 0 for s in pipe.stats_lp + pipe.stats_hp)
 
-    # ---- plain single-RHS FP64 CG on the same GPU (equal-error baseline)
+    # ---- plain single-RHS FP64 CG on the same GPU (equal-error baseline),
+    # the paper's efficiency ratios, and the same for the heavier sectors
     t_plain = None
     efficiency = None
+    sectors = None
     if not args.no_baseline:
-        n_plain = 2
-        eta = tl.empty_field(L, tl.F64, 1)
-        x = tl.empty_field(L, tl.F64, 1)
-        w = tl.empty_field(L, tl.F64, 1)
-        g5w = tl.empty_field(L, tl.F64, 1)
-        T = L[3]
-        loc = torch.empty(32 * T, dtype=torch.float64, device="cuda")
-        oned = torch.empty(128 * T, dtype=torch.float64, device="cuda")
-        prm = tl.cg_params(c["tol_hp"], 20000, tl.CG_PLAIN, prec=tl.F64, check_every=8,
-                           schur=c["schur"])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for j in range(n_plain):
-            tl.z4_noise(L, eta, tl.F64, c["seed"], rank * n_src + j, 1)
-            tl.tm_cg_solve(op, x, eta, 1, prm)
-            tl.tm_dslash(op, w, x, 1, mu_zero=True, prec=tl.F64)
-            tl.tm_gamma5(L, g5w, w, tl.F64, 1)
-            for left, right, mode in ((x, x, tl.LOOP_VV), (x, g5w, tl.LOOP_GEN)):
-                tl.loop_contract_local(L, left, right, tl.F64, 1, mode, loc)
-                tl.loop_contract_oneD(op, left, right, tl.F64, 1, mode, oned)
-        torch.cuda.synchronize()
-        t_plain = (time.perf_counter() - t0) / n_plain
-        _log("plain FP64 CG: %.3f s/source" % t_plain)
-        # phase times of one step (solve / local loops / one-derivative loops of
-        # the LP and HP sets) and the variances from a side run of paired
-        # (HP, LP) sources beyond the step's, both outside the timed region
-        pt = mk(op, timing=True)
-        pt.run(dist)
-        phase = pt.phase_ms()
-        obs_step = _observables(pipe, c)
-        n_side = 32
-        del pt
-        side = TsmPipeline(op, n_side, 0, batch=c["n_hp"], lp_prec=tl.PREC[c["lp_prec"]],
-                           hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
-                           seed=c["seed"], first_src=world * n_src + rank * n_side, schur=c["schur"],
-                           delta=c["delta"], hp_loop_prec=tl.PREC[c["hp_loops"]])
-        side.run_sources()
-        side_ok = all(s["status"] == 0 for s in side.stats_hp + side.stats_lp)
-        obs_side = _observables(side, dict(c, n_hp=n_side))
-        efficiency = _tsm_efficiency(obs_step, obs_side, c, ms * 1e-3, t_plain, phase)
-        efficiency["side_run_converged"] = side_ok
-        del side
+        efficiency, t_plain = _efficiency_of(tl, TsmPipeline, op, pipe, c, ms, dist, rank, world, n_src, mk)
+        sectors = {"light": dict(mu=c["mu"], step_ms=round(ms, 3), **efficiency)}
+        for name, mu_s in SECTOR_MU.items():
+            cs = dict(c, mu=mu_s)
+            op_s = tl.Operator(L, c["kappa"], mu_s, U_dev, recon=c["recon"])
+            mk_s = lambda o, **kw: TsmPipeline(o, cs["n_hp"], cs["n_lp"], batch=cs["batch"],
+                                               lp_prec=tl.PREC[cs["lp_prec"]], hp_inner=tl.PREC[cs["hp_inner"]],
+                                               tol_lp=cs["tol_lp"], tol_hp=cs["tol_hp"], seed=cs["seed"],
+                                               first_src=rank * n_src, schur=cs["schur"], delta=cs["delta"],
+                                               hp_loop_prec=tl.PREC[cs["hp_loops"]], **kw)
+            p_s = mk_s(op_s)
+            p_s.run(dist)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p_s.run(dist)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_s = _max_over_ranks(dist, e0.elapsed_time(e1))
+            eff_s, _ = _efficiency_of(tl, TsmPipeline, op_s, p_s, cs, ms_s, dist, rank, world, n_src, mk_s)
+            sectors[name] = dict(mu=mu_s, step_ms=round(ms_s, 3),
+                                 lp_iters_mean=round(float(np.mean([q["iters"] for q in p_s.stats_lp])), 2),
+                                 hp_iters_mean=round(float(np.mean([q["iters"] for q in p_s.stats_hp])), 2),
+                                 **eff_s)
+            _log("sector %s (mu %g): %.3f ms/step" % (name, mu_s, ms_s))
+            del p_s
+            op_s.close()
 
     # ---- end to end through host buffers: H2D gauge field, operator set-up,
     # the full step, D2H of the combined loops, every step
@@ -572,6 +617,7 @@ def run_ours(args):
                        "all_converged": ok},
             "fp64_cg_plain_s_per_source": round(t_plain, 4) if t_plain else None,
             "tsm_efficiency": efficiency,
+            "sectors": sectors,
             "dslash_shapes": _tuned_shapes(tl, L),
             "dslash_alone": dslash_alone,
         }
