@@ -446,7 +446,7 @@ def run_ours(args):
     classes = {}
     precs = ("f64", "f32", "f16", "bf16", "ff")
     names = ["dslash.%s.%s" % (p, e) for p in precs + ("f16il", "bf16il") for e in ("out", "cgupd", "resid")]
-    names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in precs]
+    names += ["%s.%s" % (k, p) for k in ("local", "oneD") for p in precs + ("f16il", "bf16il")]
     names += ["blas.xpay", "z4_noise", "cg.graph"]
     flops = {}
     for name in names:
@@ -705,8 +705,17 @@ def run_contract(args):
     tl.z4_noise(L, b, prec, 8, 0, n)
     T = L[3]
     out = torch.empty(n * 64 * T * 2, dtype=torch.float64, device="cuda")
-    jobs = {"local": (lambda: tl.loop_contract_local(L, a, b, prec, n, tl.LOOP_VV, out), 384.0, False),
-            "oneD": (lambda: tl.loop_contract_oneD(op, a, b, prec, n, tl.LOOP_VV, out), 4224.0, True)}
+    if args.layout == "il":
+        # the same fields in the system-interleaved layout (tensor-core oneD)
+        ai, bi = tl.empty_field_il(L, n), tl.empty_field_il(L, n)
+        tl.tm_spinor_to_il(L, ai, a, prec, n)
+        tl.tm_spinor_to_il(L, bi, b, prec, n)
+        del a, b
+        jobs = {"local": (lambda: tl.loop_contract_local_il(L, ai, bi, prec, n, tl.LOOP_VV, out), 384.0, False),
+                "oneD": (lambda: tl.loop_contract_oneD_il(op, ai, bi, prec, n, tl.LOOP_VV, out), 4224.0, True)}
+    else:
+        jobs = {"local": (lambda: tl.loop_contract_local(L, a, b, prec, n, tl.LOOP_VV, out), 384.0, False),
+                "oneD": (lambda: tl.loop_contract_oneD(op, a, b, prec, n, tl.LOOP_VV, out), 4224.0, True)}
     esz = tl.ELEM_SIZE[prec]
     link_reals = tl.link_reals(args.recon, prec)
     peak, src = _peaks()
@@ -726,7 +735,9 @@ def run_contract(args):
         res[name] = {"ms_per_launch": round(ms, 4), "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
                      "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
                      "TFLOPs": round(flops * V * n / (ms * 1e-3) / 1e12, 2)}
-    print(json.dumps({"mode": "contract", "lattice": list(L), "nrhs": n, "prec": args.prec,
+    if args.layout == "il":
+        tl.tm_op_check(op)
+    print(json.dumps({"mode": "contract", "layout": args.layout, "lattice": list(L), "nrhs": n, "prec": args.prec,
                       "recon": link_reals, "peak_source": src, "kernels": res}), flush=True)
     op.close()
 
@@ -860,6 +871,17 @@ def run_solvers(args):
         res[f"uneven_{name}_sequential_graph_ms"] = timed(lambda: seq(graph))
         res[f"uneven_{name}_group_ms"] = timed(lambda: tl.tm_cg_solve_group(ops, xs, etas, ns, eager))
         res[f"uneven_{name}_group_graph_ms"] = timed(lambda: tl.tm_cg_solve_group(ops, xs, etas, ns, graph))
+        if name == "lp":
+            # the two small lattices alone (launch-bound truncated solves)
+            for j in (0, 1):
+                Lr = ragged[j][0]
+                tag = "x".join(str(v) for v in Lr[:1]) + "^4"
+                res[f"small_lp_{tag}_eager_ms"] = timed(lambda: tl.tm_cg_solve(ops[j], xs[j], etas[j], ns[j], eager))
+                res[f"small_lp_{tag}_graph_ms"] = timed(lambda: tl.tm_cg_solve(ops[j], xs[j], etas[j], ns[j], graph))
+            res["small_lp_group_eager_ms"] = timed(lambda: tl.tm_cg_solve_group(ops[:2], xs[:2], etas[:2], ns[:2],
+                                                                                eager))
+            res["small_lp_group_graph_ms"] = timed(lambda: tl.tm_cg_solve_group(ops[:2], xs[:2], etas[:2], ns[:2],
+                                                                                graph))
     for o in ops:
         o.close()
     print(json.dumps({"mode": "solvers", "steps": args.steps, "warmup": args.warmup, "results": res}),
@@ -1024,7 +1046,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--prec", default="f16", choices=["f64", "f32", "f16", "bf16", "ff"])
     ap.add_argument("--layout", default="std", choices=["std", "il"],
-                    help="--dslash: standard layout (CUDA-core kernel) or system-interleaved (tensor cores)")
+                    help="--dslash / --contract: standard layout (CUDA-core kernels) or system-interleaved (tensor cores)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
     if args.schur is not None:

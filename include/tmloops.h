@@ -145,9 +145,11 @@ tm_status_t tm_dslash_g5(tm_op_t *op, void *out, const void *in, int nrhs, int d
 
 /* System-interleaved 16-bit layout (this library's own; the paper gives no
  * layout).  nrhs F16 or BF16 fields stored as ceil(nrhs / 16) blocks of 16
- * systems: [block][parity][k = 3 spin + colour][cb][slot 0..15], 4 bytes per
- * slot (one complex number, re in the low half), 64 bytes per (k, site);
- * system j < 8 of a block sits in slot 2j and system j + 8 in slot 2j + 1.
+ * systems: [block][parity][cb][k = 3 spin + colour][slot 0..15], 4 bytes per
+ * slot (one complex number, re in the low half), 64 bytes per (site, k) and
+ * 768 per site; system j < 8 of a block sits in slot 2p and system j + 8 in
+ * slot 2p + 1, p = j in the rows k = 0, 1 (mod 3) and p = j ^ 4 in the rows
+ * k = 2 (mod 3).
  * The multi-system Dslash reads it with one 8-byte load per (spin, colour,
  * two systems) and feeds the tensor cores straight from it.
  * tm_spinor_bytes_il: bytes of nrhs systems (0 on a bad geometry).
@@ -179,6 +181,7 @@ tm_status_t tm_dslash_il(tm_op_t *op, void *out_il, const void *in_il, int nrhs,
                          tm_prec_t prec, tm_stream_t s);
 tm_status_t tm_cg_il_enable(int on);
 tm_status_t tm_op_check(tm_op_t *op);
+
 
 /* Z4 noise (Sec. 2, Eqs. 1-2): eta_r(x)_{alpha c} = i^k with k = bits
  * [2(3 alpha + c), 2(3 alpha + c) + 1] of word 0 of Philox4x32-10 applied to
@@ -262,6 +265,14 @@ typedef struct {
 tm_status_t tm_cg_solve(tm_op_t *op, void *x, const void *eta, int nrhs,
                         const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
 
+/* tm_cg_solve with the solution left in the interleaved layout: x_il (16-byte
+ * aligned, tm_spinor_bytes_il(g, nrhs) bytes) receives the solution that
+ * tm_cg_solve would convert into x (the same bits), eta as for tm_cg_solve.
+ * Only for the solves that run on the interleaved layout (plain F16/BF16,
+ * 18-real links, tm_cg_il_enable on): TM_ERR_UNSUPPORTED otherwise.        */
+tm_status_t tm_cg_solve_il(tm_op_t *op, void *x_il, const void *eta, int nrhs,
+                           const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
+
 /* Several independent batched solves advanced together (an uneven batch:
  * different lattices, kappa, mu and numbers of systems, as in a sweep over
  * volumes and quark masses; each set is the solve tm_cg_solve describes, with
@@ -302,6 +313,30 @@ tm_status_t loop_contract_local(const tm_geom_t *g, const void *left, const void
 tm_status_t loop_contract_oneD(tm_op_t *op, const void *left, const void *right,
                                tm_prec_t prec, int nrhs, tm_loop_mode_t mode,
                                double *out, tm_stream_t s);
+
+/* Loop contractions on the interleaved layout (Sec. 2.2, Table 2: the
+ * operators of loop_contract_local / loop_contract_oneD above, same modes,
+ * prefactor convention and output layout).  left_il / right_il: nrhs F16 or
+ * BF16 fields in the interleaved layout (16-byte aligned, else TM_ERR_ARG);
+ * right_g5 = 1 contracts gamma_5 right_il instead of right_il (the generalised
+ * estimator's R = gamma_5 D_W s from the D_W s that tm_dslash_il writes);
+ * out as for the standard contractions.
+ * loop_contract_local_il: the products conj(L_ac) R_bc of each site as
+ *   mixed-precision FMAs (exact products of the 16-bit numbers, FP32 sums).
+ * loop_contract_oneD_il: per site and 16 systems, the link products of all
+ *   directions as warp-level MMAs over the systems (FP32 accumulation, rounded
+ *   once to the storage format), then the 4 x 4 spin products per system as
+ *   MMAs over (colour, re/im) with FP32 sums over the sites; every site's
+ *   neighbours staged by bounded bulk copies as in tm_dslash_il (its
+ *   time-outs set the operator's flag: tm_op_check).  Needs the 18-real
+ *   16-bit links (recon 18 or 0, else TM_ERR_UNSUPPORTED).
+ * Results agree with the standard contractions of the same fields to the
+ * 16-bit tolerance; each system's values depend on its own fields only.      */
+tm_status_t loop_contract_local_il(const tm_geom_t *g, const void *left_il, const void *right_il,
+                                   tm_prec_t prec, int nrhs, tm_loop_mode_t mode, int right_g5,
+                                   double *out, tm_stream_t s);
+tm_status_t loop_contract_oneD_il(tm_op_t *op, const void *left_il, const void *right_il, tm_prec_t prec,
+                                  int nrhs, tm_loop_mode_t mode, int right_g5, double *out, tm_stream_t s);
 
 /* Momentum-projected local loops:
  *   out[r][q][g][t] = sum_{x_t = t} exp(-i p_q . x) L_r(x)^dag (P Gamma_g) R_r(x),

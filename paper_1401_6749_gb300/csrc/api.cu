@@ -466,7 +466,8 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
     }
   }
   if (op->il_err) {
-    const tm_status_t s4 = il_prepare();
+    tm_status_t s4 = il_prepare();
+    if (s4 == TM_OK) s4 = oned_il_prepare();
     if (s4 != TM_OK) { tm_op_destroy(op); return s4; }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) {

@@ -330,6 +330,7 @@ struct CgRun {
   // Dslash): eta is converted into eta_il at set-up, x_il back into x at the end
   bool il = false;
   void *eta_il = nullptr, *x_il = nullptr;
+  bool x_is_il = false;  // the caller's x is in the interleaved layout (tm_cg_solve_il)
   tm_prec_t lo = TM_PREC_F64, hi = TM_PREC_F64;
   int par0 = 0, npar = 2, nwarp = 0;
   void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
@@ -379,6 +380,10 @@ tm_status_t CgRun::setup() {
   npar = schur ? 1 : 2;
   const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
   il = !mixed && (lo == TM_PREC_F16 || lo == TM_PREC_BF16) && op->recon_p[lo] == 18 && cg_il_on();
+  if (x_is_il && !il) {
+    set_error("tm_cg_solve_il: needs a plain F16/BF16 solve with 18-real links and the interleaved solver enabled");
+    return TM_ERR_UNSUPPORTED;
+  }
   const size_t F = il ? il_bytes(g, nrhs) : tm_spinor_bytes(&gg, lo, nrhs);
   const size_t F64 = tm_spinor_bytes(&gg, TM_PREC_F64, nrhs);
   nwarp = nwarp_of(g);
@@ -392,7 +397,7 @@ tm_status_t CgRun::setup() {
       y = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
     } else {
       b = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
-      if (il) { eta_il = c.take(F); x_il = c.take(F); }
+      if (il) { eta_il = c.take(F); x_il = x_is_il ? x : c.take(F); }
     }
     partial = (double*)c.take(P);
     st.bb = (double*)c.take(sizeof(double) * nrhs);
@@ -555,7 +560,7 @@ tm_status_t CgRun::finish(tm_status_t* worst_out) {
     }
   }
   if (schur) TM_TRY(Op.reconstruct(hi, il ? eta_il : eta, mixed ? x : xs));
-  if (il) TM_TRY(il_convert(g, x, x_il, nrhs, false, s));
+  if (il && !x_is_il) TM_TRY(il_convert(g, x, x_il, nrhs, false, s));
   const bool want_true = mixed || prm.true_residual;
   tm_status_t worst = TM_OK;
   for (int i = 0; i < nrhs; ++i) {
@@ -765,6 +770,26 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   std::vector<CgRun> runs(1);
   runs[0].op = op; runs[0].x = x; runs[0].eta = eta; runs[0].nrhs = nrhs;
   runs[0].prm = *prm; runs[0].stats = stats;
+  tm_status_t worst = TM_OK;
+  TM_TRY(solve_group(runs, prm, (cudaStream_t)strm, &worst));
+  return report(worst);
+}
+
+extern "C" tm_status_t tm_cg_solve_il(tm_op_t* op, void* x_il, const void* eta, int nrhs,
+                                      const tm_cg_params_t* prm, tm_cg_stats_t* stats, tm_stream_t strm) {
+  if (!op || !x_il || !eta || !prm || nrhs < 0) { set_error("tm_cg_solve_il: null argument"); return TM_ERR_ARG; }
+  if (x_il == eta) { set_error("tm_cg_solve_il: x and eta must not overlap"); return TM_ERR_ARG; }
+  if (reinterpret_cast<uintptr_t>(x_il) & 15u) { set_error("tm_cg_solve_il: x must be 16-byte aligned"); return TM_ERR_ARG; }
+  TM_TRY(check_params(prm));
+  const tm_prec_t lo = prm->prec;
+  if (prm->mode != TM_CG_PLAIN || (lo != TM_PREC_F16 && lo != TM_PREC_BF16) || op->recon_p[lo] != 18 || !cg_il_on()) {
+    set_error("tm_cg_solve_il: needs a plain F16/BF16 solve with 18-real links and the interleaved solver enabled");
+    return TM_ERR_UNSUPPORTED;
+  }
+  if (nrhs == 0) return TM_OK;
+  std::vector<CgRun> runs(1);
+  runs[0].op = op; runs[0].x = x_il; runs[0].eta = eta; runs[0].nrhs = nrhs;
+  runs[0].prm = *prm; runs[0].stats = stats; runs[0].x_is_il = true;
   tm_status_t worst = TM_OK;
   TM_TRY(solve_group(runs, prm, (cudaStream_t)strm, &worst));
   return report(worst);

@@ -560,6 +560,22 @@ tm_status_t local_contract_into(const Geom& g, const void* left, const void* rig
   return check_launch("loop_contract_local final");
 }
 
+// The final reductions as host entry points (the interleaved contractions of
+// loops_il.cu write partial sums in the layouts of these kernels).
+tm_status_t local_final(const double* partial, int nchunk, const Geom& g, int nrhs, int p_g5, double* out,
+                        cudaStream_t s) {
+  local_final_kernel<<<dim3(g.L[3], nrhs), 32, 0, s>>>(partial, nchunk, g.L[3], gamma_tab(), p_g5, out);
+  count_launch();
+  return check_launch("local loops final");
+}
+
+tm_status_t oned_final(const double* partial, int nchunk, const Geom& g, int nrhs, int p_g5, double* out,
+                       cudaStream_t s) {
+  oneD_final_kernel<<<dim3(g.L[3], nrhs), 160, 0, s>>>(partial, nchunk, g.L[3], gamma_tab(), p_g5, out);
+  count_launch();
+  return check_launch("one-derivative loops final");
+}
+
 }  // namespace tml
 
 using namespace tml;

@@ -127,6 +127,15 @@ size_t il_link_bytes(const Geom& g);
 tm_status_t il_pack_links(const Geom& g, void* out, const void* links18, cudaStream_t s);
 tm_status_t il_prepare();
 
+// Loop contractions on the interleaved layout (loops_il.cu): set-up of the
+// one-derivative kernel (its shared-memory limit), and the final reductions
+// of the partial sums [rhs][t][par][chunk][32 | 128] (contract.cu).
+tm_status_t oned_il_prepare();
+tm_status_t local_final(const double* partial, int nchunk, const Geom& g, int nrhs, int p_g5, double* out,
+                        cudaStream_t s);
+tm_status_t oned_final(const double* partial, int nchunk, const Geom& g, int nrhs, int p_g5, double* out,
+                       cudaStream_t s);
+
 // per-warp partial sums -> result[rhs] (fixed summation order): system rhs sums
 // partial[rhs * stride + i], i < nper (stride 0 means nper)
 tm_status_t reduce_partials(const double* partial, int nper, int nrhs, double* result,

@@ -102,6 +102,9 @@ _SIGS = {
     "tm_cg_il_enable": [_i],
     "tm_op_check": [_vp],
     "tsm_combine_host": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp],
+    "tm_cg_solve_il": [_vp, _vp, _vp, _i, _P(tm_cg_params_t), _P(tm_cg_stats_t), _vp],
+    "loop_contract_local_il": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _i, _vp, _vp],
+    "loop_contract_oneD_il": [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -166,6 +169,7 @@ class Operator:
     def __init__(self, L, kappa, mu, U, antiperiodic=True, recon=12, stream=None):
         self.L = tuple(int(v) for v in L)
         self.kappa, self.mu = float(kappa), float(mu)
+        self.recon = int(recon)
         p = tm_params_t()
         for i in range(4):
             p.L[i] = self.L[i]
@@ -178,7 +182,7 @@ class Operator:
         """Handle sharing these links with its own solver work space (for a
         concurrent solve on another thread and stream); close it before self."""
         c = Operator.__new__(Operator)
-        c.L, c.kappa, c.mu = self.L, self.kappa, self.mu
+        c.L, c.kappa, c.mu, c.recon = self.L, self.kappa, self.mu, self.recon
         h = ctypes.c_void_p()
         _check(_lib.tm_op_clone(ctypes.byref(h), self.handle))
         c.handle = h
@@ -309,6 +313,19 @@ def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
     return st, out
 
 
+def tm_cg_solve_il(op, x_il, eta, nrhs, params, stream=None, raise_on_noconv=True):
+    """tm_cg_solve with the solution left in the interleaved layout (x_il from
+    empty_field_il); the same return values."""
+    stats = (tm_cg_stats_t * max(int(nrhs), 1))()
+    st = _lib.tm_cg_solve_il(op.handle, _ptr(x_il), _ptr(eta), int(nrhs), ctypes.byref(params), stats,
+                             _stream(stream))
+    out = [dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status,
+                rel_res=s.rel_res, true_res=s.true_res) for s in list(stats)[:int(nrhs)]]
+    if st != 0 and (st not in (3, 4) or raise_on_noconv):
+        _check(st)
+    return st, out
+
+
 def tm_cg_solve_group(ops, xs, etas, nrhs, params, stream=None, raise_on_noconv=True):
     """Several solves (one per operator) advanced together; returns
     (status, [per-set list of per-system dicts])."""
@@ -343,6 +360,19 @@ def loop_contract_local_noalloc(L, left, right, prec, nrhs, mode, out, stream=No
 def loop_contract_oneD(op, left, right, prec, nrhs, mode, out, stream=None):
     _check(_lib.loop_contract_oneD(op.handle, _ptr(left), _ptr(right), int(prec), int(nrhs), int(mode),
                                    _ptr(out), _stream(stream)))
+
+
+def loop_contract_local_il(L, left_il, right_il, prec, nrhs, mode, out, right_g5=False, stream=None):
+    """Local loops of fields in the interleaved layout (right_g5: R = gamma_5 right_il)."""
+    _check(_lib.loop_contract_local_il(ctypes.byref(geom(L)), _ptr(left_il), _ptr(right_il), int(prec),
+                                       int(nrhs), int(mode), int(bool(right_g5)), _ptr(out), _stream(stream)))
+
+
+def loop_contract_oneD_il(op, left_il, right_il, prec, nrhs, mode, out, right_g5=False, stream=None):
+    """One-derivative loops of fields in the interleaved layout (tensor cores;
+    right_g5: R = gamma_5 right_il)."""
+    _check(_lib.loop_contract_oneD_il(op.handle, _ptr(left_il), _ptr(right_il), int(prec), int(nrhs),
+                                      int(mode), int(bool(right_g5)), _ptr(out), _stream(stream)))
 
 
 def tsm_combine(l_hp, l_lp_on_hp, n_hp, l_lp, n_lp, length, scale, mean, err, stream=None):

@@ -31,8 +31,14 @@ KINDS = ("local_vv", "local_gen", "oneD_vv", "oneD_gen")
 class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
-                 delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False):
-        """overlap: run the high-precision solves and contractions on a second
+                 delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False,
+                 lp_layout=None):
+        """lp_layout: "il" keeps the LP solutions in the system-interleaved
+        layout (tm_cg_solve_il), applies D_W there (tm_dslash_il) and contracts
+        there (loop_contract_*_il, gamma_5 of the generalised estimator as
+        right_g5); "std" uses the standard layout throughout.  Default: "il"
+        for FP16/BF16 with 18-real 16-bit links (recon 18 or 0), else "std".
+        overlap: run the high-precision solves and contractions on a second
         stream from a host thread, concurrently with the low-precision batches
         (FP64 work uses other units than the FP32 arithmetic of the LP solves);
         needs its own operator handle (a clone sharing the links).
@@ -56,6 +62,12 @@ class TsmPipeline:
             raise ValueError("hp_loop_prec must be F64 or FF")
         self.hp_loop_prec = hp_loop_prec
         self.kinds = tuple(kinds)
+        il_ok = lp_prec in (tl.F16, tl.BF16) and op.recon in (0, 18)
+        if lp_layout is None:
+            lp_layout = "il" if il_ok else "std"
+        if lp_layout not in ("il", "std") or (lp_layout == "il" and not il_ok):
+            raise ValueError("lp_layout 'il' needs F16/BF16 and 18-real 16-bit links; 'std' always works")
+        self.lp_il = lp_layout == "il"
         self.nu = 2.0 * op.kappa * op.mu
         n_all = self.n_hp + self.n_lp
         self.len = {"local": 16 * self.T, "oneD": 64 * self.T}
@@ -66,7 +78,12 @@ class TsmPipeline:
         self.hp_loops = {k: torch.empty((max(self.n_hp, 1), self.len[k.split("_")[0]] * 2),
                                         dtype=torch.float64, device=dev) for k in self.kinds}
         b = min(self.batch, n_all)
-        self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(3)]  # eta, x, g5 D_W x
+        if self.lp_il:
+            # eta (standard layout, from the noise generator); x, D_W x and, for
+            # the standard estimator, eta in the interleaved layout
+            self._lp = [tl.empty_field(self.L, lp_prec, b)] + [tl.empty_field_il(self.L, b) for _ in range(3)]
+        else:
+            self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(3)]  # eta, x, g5 D_W x
         nh = max(min(self.batch, self.n_hp), 1)
         # eta, x, g5 D_W x (the last in hp_loop_prec, same byte size), and the copies of
         # eta and x in hp_loop_prec when that is not F64
@@ -101,6 +118,41 @@ class TsmPipeline:
                 tl.loop_contract_local(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
             else:
                 tl.loop_contract_oneD(op, left, right, prec, n, tl.LOOP_MODE[mode], out, stream)
+
+    def _contract_il(self, op, x, dw, eta, prec, n, dst, row0, stream, kinds):
+        for k in kinds:
+            kind, mode = k.split("_")
+            left, right, g5 = {"vv": (x, x, False), "gen": (x, dw, True), "std": (eta, x, False)}[mode]
+            out = dst[k][row0:row0 + n]
+            if kind == "local":
+                tl.loop_contract_local_il(self.L, left, right, prec, n, tl.LOOP_MODE[mode], out, right_g5=g5,
+                                          stream=stream)
+            else:
+                tl.loop_contract_oneD_il(op, left, right, prec, n, tl.LOOP_MODE[mode], out, right_g5=g5,
+                                         stream=stream)
+
+    def _solve_and_contract_il(self, op, fields, prec, first, n, params, dst, row0, stream=None):
+        """An LP batch on the interleaved layout: solve, D_W, contractions."""
+        eta, x, dw, eta_il = fields
+        ev = [self._event(stream)] if self.timing else None
+        tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
+        st, stats = tl.tm_cg_solve_il(op, x, eta, n, params, stream, raise_on_noconv=False)
+        if any(k.endswith("std") for k in self.kinds):
+            tl.tm_spinor_to_il(self.L, eta_il, eta, prec, n, stream)
+        if ev:
+            ev.append(self._event(stream))
+        if any("gen" in k for k in self.kinds):
+            tl.tm_dslash_il(op, dw, x, n, mu_zero=True, prec=prec, stream=stream)   # D_W s
+        local = tuple(k for k in self.kinds if k.startswith("local"))
+        oned = tuple(k for k in self.kinds if k.startswith("oneD"))
+        self._contract_il(op, x, dw, eta_il, prec, n, dst, row0, stream, local)
+        if ev:
+            ev.append(self._event(stream))
+        self._contract_il(op, x, dw, eta_il, prec, n, dst, row0, stream, oned)
+        if ev:
+            ev.append(self._event(stream))
+            self._events.append(("lp", ev))
+        return stats
 
     def _solve_and_contract(self, op, fields, prec, first, n, params, dst, row0, stream=None,
                             loop_prec=None, which="lp"):
@@ -171,8 +223,12 @@ class TsmPipeline:
                                  check_every=min(2, self.check_every), schur=self.schur)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
-            self.stats_lp += self._solve_and_contract(self.op, self._lp, self.lp_prec, self.first + b0, n,
-                                                      lp_params, self.lp_loops, b0, main)
+            if self.lp_il:
+                self.stats_lp += self._solve_and_contract_il(self.op, self._lp, self.lp_prec, self.first + b0, n,
+                                                             lp_params, self.lp_loops, b0, main)
+            else:
+                self.stats_lp += self._solve_and_contract(self.op, self._lp, self.lp_prec, self.first + b0, n,
+                                                          lp_params, self.lp_loops, b0, main)
         if worker is not None:
             worker.join()
             main.wait_stream(self.hp_stream)
