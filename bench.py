@@ -162,8 +162,8 @@ def _barrier(dist):
 
 # ncu DRAM traffic per algorithmic byte, per Dslash kernel class: the
 # committed summary and the sources its capture was taken from
-TRAFFIC_FILES = {"dslash.f16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "tm_core.cuh")),
-                 "dslash.bf16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "tm_core.cuh")),
+TRAFFIC_FILES = {"dslash.f16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "il_core.cuh", "tm_core.cuh")),
+                 "dslash.bf16il": ("dslash_il_traffic.txt", ("dslash_il.cu", "il_core.cuh", "tm_core.cuh")),
                  "dslash.f16": ("dslash_traffic.txt", ("dslash.cuh", "tm_core.cuh")),
                  "dslash.bf16": ("dslash_traffic.txt", ("dslash.cuh", "tm_core.cuh"))}
 

@@ -488,6 +488,7 @@ extern "C" tm_status_t tm_op_clone(tm_op_t** out, const tm_op_t* src) {
   op->host_flags = nullptr;
   op->host_flags_n = 0;
   op->owns_links = false;
+  op->cg_graph = tm_cg_graph_cache{};  // the source's graph stays its own
   *out = op;
   return TM_OK;
 }
@@ -504,6 +505,7 @@ extern "C" tm_status_t tm_op_destroy(tm_op_t* op) {
       dev_free(op->links_il[i], nullptr);
     }
   if (op->owns_links) dev_free(op->il_err, nullptr);
+  if (op->cg_graph.exec) cudaGraphExecDestroy(op->cg_graph.exec);
   dev_free(op->work, nullptr);
   cudaStreamSynchronize(nullptr);
   pinned_give(op->host_flags, op->host_flags_n);

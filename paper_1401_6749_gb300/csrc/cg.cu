@@ -675,6 +675,36 @@ struct PrivateStream {
   }
 };
 
+static tm_cg_graph_key graph_key(const CgRun& r, int k) {
+  tm_cg_graph_key key{};
+  key.x = r.x;
+  key.xs = r.xs;
+  key.work = r.op->work;
+  key.work_bytes = r.op->work_bytes;
+  key.host_flags = r.op->host_flags;
+  key.nrhs = r.nrhs;
+  key.k = k;
+  key.il = r.il ? 1 : 0;
+  key.tol = r.prm.tol;
+  key.delta = r.prm.delta;
+  key.max_iter = r.prm.max_iter;
+  key.mode = (int)r.prm.mode;
+  key.prec = (int)r.prm.prec;
+  key.inner_prec = (int)r.prm.inner_prec;
+  key.check_every = r.prm.check_every;
+  key.true_residual = r.prm.true_residual;
+  key.schur = r.prm.schur;
+  return key;
+}
+
+static bool same_key(const tm_cg_graph_key& a, const tm_cg_graph_key& b) {
+  return a.x == b.x && a.xs == b.xs && a.work == b.work && a.work_bytes == b.work_bytes &&
+         a.host_flags == b.host_flags && a.nrhs == b.nrhs && a.k == b.k && a.il == b.il && a.tol == b.tol &&
+         a.delta == b.delta && a.max_iter == b.max_iter && a.mode == b.mode && a.prec == b.prec &&
+         a.inner_prec == b.inner_prec && a.check_every == b.check_every && a.true_residual == b.true_residual &&
+         a.schur == b.schur;
+}
+
 static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* prm, cudaStream_t s_user,
                                tm_status_t* worst) {
   PrivateStream ps;
@@ -693,10 +723,20 @@ static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* p
   const int check_every = prm->check_every > 0 ? prm->check_every : 1;
   GraphHolder gh;
   int per_replay = 0;
+  // a single-set solve replays the graph its operator kept from the last solve
+  // whose launches were the same (same buffers, systems and parameters): the
+  // graph embeds nothing else, so the replay is the capture it would make
+  tm_cg_graph_cache* cache = (prm->graph && runs.size() == 1) ? &runs[0].op->cg_graph : nullptr;
+  const tm_cg_graph_key key = cache ? graph_key(runs[0], check_every) : tm_cg_graph_key{};
+  cudaGraphExec_t exec = nullptr;
+  if (cache && cache->valid && same_key(cache->key, key)) {
+    exec = cache->exec;
+    per_replay = cache->per_replay;
+  }
   for (int done = 0; done < prm->max_iter;) {
     const int k = std::min(check_every, prm->max_iter - done);
     if (prm->graph && k == check_every) {
-      if (!gh.exec) {
+      if (!exec) {
         // capture k iterations of every set (and the flag copies) once; the
         // device-side masks make every replay the same sequence of launches
         capture_begin();
@@ -714,9 +754,19 @@ static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* p
           set_error("tm_cg_solve: graph capture failed: %s", cudaGetErrorString(cudaGetLastError()));
           return TM_ERR_CUDA;
         }
+        exec = gh.exec;
+        if (cache) {
+          // the operator keeps the new graph in place of the old one
+          if (cache->exec) cudaGraphExecDestroy(cache->exec);
+          cache->exec = gh.exec;
+          cache->key = key;
+          cache->per_replay = per_replay;
+          cache->valid = true;
+          gh.exec = nullptr;
+        }
       }
       TraceScope ts(s0, "cg.graph", 0.0, 0.0, 0);
-      if (cudaGraphLaunch(gh.exec, s0) != cudaSuccess) {
+      if (cudaGraphLaunch(exec, s0) != cudaSuccess) {
         set_error("tm_cg_solve: graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return TM_ERR_CUDA;
       }

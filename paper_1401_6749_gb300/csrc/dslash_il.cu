@@ -120,6 +120,20 @@ __host__ __device__ constexpr int il_quad(int r, int k) {
   return r == 0 ? (k == 3 ? 0 : 1) : (k == 3 ? 2 : k == 2 ? 3 : k == 1 ? 4 : 5);
 }
 
+// The direction whose product reaches a phase quad first (directions run 0..3)
+__host__ __device__ constexpr int il_quad_first(int q) {
+  int first = 4;
+  for (int mu = 3; mu >= 0; --mu) {
+    const int k0 = mu == 0 ? IlG<0>::bk0 : mu == 1 ? IlG<1>::bk0 : mu == 2 ? IlG<2>::bk0 : IlG<3>::bk0;
+    const int k1 = mu == 0 ? IlG<0>::bk1 : mu == 1 ? IlG<1>::bk1 : mu == 2 ? IlG<2>::bk1 : IlG<3>::bk1;
+    if (il_quad(0, k0) == q || il_quad(1, k1) == q) first = mu;
+  }
+  return first;
+}
+static_assert(il_quad_first(0) < 4 && il_quad_first(1) < 4 && il_quad_first(2) < 4 && il_quad_first(3) < 4 &&
+                  il_quad_first(4) < 4 && il_quad_first(5) < 4,
+              "every phase quad receives a product");
+
 // One direction: both hops of 16 systems into the upper-spin accumulators
 // up (spins 0, 1) and the lower-spin phase quads q, from the loaded neighbour
 // words pf / pb (spins 0..3, systems g and g + 8) and link words uf / ub;
@@ -149,12 +163,15 @@ __device__ __forceinline__ void il_dir(float (&up)[2][4], float (&q)[6][4], cons
   const unsigned bf_up = uf ^ 0x80000000u, bb_up = ub;
   const unsigned bf_m = SF < 0 ? uf ^ 0x00008000u : bf_up;
   const unsigned bb_m = SB < 0 ? ub ^ 0x80008000u : bb_up;
-  il_mma<S>(up[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
-  il_mma<S>(up[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
-  if constexpr (G::bc0 == 0) il_mma<S>(q[il_quad(0, G::bk0)], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
-  else il_mma<S>(q[il_quad(0, G::bk0)], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
-  if constexpr (G::bc1 == 0) il_mma<S>(q[il_quad(1, G::bk1)], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
-  else il_mma<S>(q[il_quad(1, G::bk1)], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
+  // the first product into each accumulator of the site seeds it (directions
+  // 0 and 1 for the two upper sets, il_quad_first for the quads)
+  constexpr int q0 = il_quad(0, G::bk0), q1 = il_quad(1, G::bk1);
+  il_mma_acc<S, (MU < 2)>(up[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
+  il_mma_acc<S, (MU < 2)>(up[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
+  if constexpr (G::bc0 == 0) il_mma_acc<S, il_quad_first(q0) == MU>(q[q0], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
+  else il_mma_acc<S, il_quad_first(q0) == MU>(q[q0], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
+  if constexpr (G::bc1 == 0) il_mma_acc<S, il_quad_first(q1) == MU>(q[q1], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
+  else il_mma_acc<S, il_quad_first(q1) == MU>(q[q1], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
 }
 
 // store one 8-byte pair of words, only the halves of active systems
@@ -322,7 +339,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         }
       }
     };
-    auto issue = [&](int m, int st) {
+    // returns the site's wrap mask (the next iteration's time-boundary signs)
+    auto issue = [&](int m, int st) -> unsigned {
       const int lex = __shfl_sync(0xffffffffu, lexl, m);
       const unsigned msk = __shfl_sync(0xffffffffu, bml, m);
       const int nlex = lex + (((msk >> rbit) & 1u) ? rwrap : rstep);
@@ -333,17 +351,18 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (lane == 0) mbar_expect_tx(bar, total);
       if (rbytes) bulk_g2s(ring_s + st * ST::kBytes + rdoff, rbase + (size_t)idx * rmul, rbytes, bar);
+      return msk;
     };
-#pragma unroll
-    for (int st = 0; st < ST::kStages - 1; ++st)
-      if (st < nsite) issue(st, st);
+    static_assert(ST::kStages == 2, "one site in flight while one is computed");
+    unsigned mskc = issue(0, 0);
     fetch_site(0);
     float nacc0 = 0.0f, nacc1 = 0.0f;  // norms of the current 32-site group
     for (int m = 0; m < nsite; ++m) {
       const int st = m % ST::kStages;
-      if (m + ST::kStages - 1 < nsite) issue(m + ST::kStages - 1, (m + ST::kStages - 1) % ST::kStages);
+      const unsigned mskn = m + 1 < nsite ? issue(m + 1, st ^ 1) : 0u;
       // antiperiodic time boundary: the hops that wrap in direction 3
-      const unsigned bf = g.antiperiodic ? (__shfl_sync(0xffffffffu, bml, m) >> 6) & 3u : 0u;
+      const unsigned bf = g.antiperiodic ? (mskc >> 6) & 3u : 0u;
+      mskc = mskn;
       if (!__all_sync(0xffffffffu, il_wait(bar0 + st * 8, (unsigned)((m / ST::kStages) & 1), a.err))) {
         // a wait gave up: wait (bounded) for this warp's copies still in
         // flight (sites m .. m + kStages - 2), then stop
@@ -354,15 +373,7 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       const unsigned char* sd = ring + st * ST::kBytes;
       // upper spins: two sets (even and odd directions: shorter MMA chains);
       // lower spins: the six phase quads
-      float ua[2][4], ub4[2][4], qq[6][4];
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) ua[s][c] = ub4[s][c] = 0.0f;
-#pragma unroll
-      for (int s = 0; s < 6; ++s)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) qq[s][c] = 0.0f;
+      float ua[2][4], ub4[2][4], qq[6][4];  // seeded by their first products
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
         uint2 pf[4], pb[4];

@@ -106,6 +106,32 @@ __device__ __forceinline__ void il_mma(float (&d)[4], unsigned a0, unsigned a1, 
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// D = A B (the accumulators' first product: C = 0, which the tensor core adds
+// exactly as it would add zeroed registers)
+template <class S>
+__device__ __forceinline__ void il_mma0(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                        unsigned b0, unsigned b1) {
+  const float z = 0.0f;
+  if constexpr (std::is_same<S, __half>::value)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(z));
+  else
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(z));
+}
+
+// first product into an accumulator (FIRST) or one more
+template <class S, bool FIRST>
+__device__ __forceinline__ void il_mma_acc(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                           unsigned b0, unsigned b1) {
+  if constexpr (FIRST) il_mma0<S>(d, a0, a1, a2, a3, b0, b1);
+  else il_mma<S>(d, a0, a1, a2, a3, b0, b1);
+}
+
 // Words of one site in uint2 units: site cb of parity par in block blk starts
 // at ((blk * 2 + par) * Vh + cb) * 96; lane (g, t) reads spin s at + (3 s + t) * 8 + g.
 constexpr int kIlSiteU2 = 96;

@@ -240,10 +240,7 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
         const unsigned b1 = __byte_perm(ub, 0u, psel) ^ pad ^ 0x80008000u;
         float d[4][4];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          d[s][0] = d[s][1] = d[s][2] = d[s][3] = 0.0f;
-          il_mma<S>(d[s], pf[s].x, pf[s].y, pb[s].x, pb[s].y, b0, b1);
-        }
+        for (int s = 0; s < 4; ++s) il_mma0<S>(d[s], pf[s].x, pf[s].y, pb[s].x, pb[s].y, b0, b1);
         __syncwarp();  // every lane has read the slots before they are overwritten
         if (tq < 3) od_store<S>(sd + ST::w(mu) + gq * 48 + tq * 16, d);
       }
@@ -262,10 +259,8 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
         float d1[4][4], d2[4][4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          d1[s][0] = d1[s][1] = d1[s][2] = d1[s][3] = 0.0f;
-          d2[s][0] = d2[s][1] = d2[s][2] = d2[s][3] = 0.0f;
-          il_mma<S>(d1[s], pf[s].x, pf[s].y, pc[s].x, pc[s].y, bt, 0u);
-          il_mma<S>(d2[s], pf[s].x, pf[s].y, pc[s].x, pc[s].y, 0u, ba);
+          il_mma0<S>(d1[s], pf[s].x, pf[s].y, pc[s].x, pc[s].y, bt, 0u);
+          il_mma0<S>(d2[s], pf[s].x, pf[s].y, pc[s].x, pc[s].y, 0u, ba);
         }
         __syncwarp();
         if (tq < 3) {

@@ -7,6 +7,26 @@
 
 #include "tm_core.cuh"
 
+// The CUDA graph of a single-set solve's iterations between two polls, kept by
+// the operator for the next solve whose captured launches would be the same
+// (cg.cu): same work space, solution and flag buffers, systems, parameters.
+struct tm_cg_graph_key {
+  const void* x;
+  const void* xs;
+  const void* work;
+  size_t work_bytes;
+  const int* host_flags;
+  int nrhs, k, il;
+  double tol, delta;
+  int max_iter, mode, prec, inner_prec, check_every, true_residual, schur;
+};
+struct tm_cg_graph_cache {
+  bool valid;
+  tm_cg_graph_key key;
+  cudaGraphExec_t exec;
+  int per_replay;  // kernel launches in one replay
+};
+
 struct tm_op {
   tml::Geom g;
   double kappa;
@@ -26,6 +46,8 @@ struct tm_op {
   void* links_il[tml::kNumPrec];
   // device flag: a bounded wait of the interleaved Dslash gave up (shared by clones)
   int* il_err;
+  // the last single-set solve's iteration graph (owned; not shared by clones)
+  tm_cg_graph_cache cg_graph;
 };
 
 namespace tml {

@@ -32,12 +32,16 @@ class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
                  delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False,
-                 lp_layout=None):
+                 lp_layout=None, lp_graph=None):
         """lp_layout: "il" keeps the LP solutions in the system-interleaved
         layout (tm_cg_solve_il), applies D_W there (tm_dslash_il) and contracts
         there (loop_contract_*_il, gamma_5 of the generalised estimator as
         right_g5); "std" uses the standard layout throughout.  Default: "il"
         for FP16/BF16 with 18-real 16-bit links (recon 18 or 0), else "std".
+        lp_graph: replay the truncated LP solves' iterations as CUDA graphs
+        (bit-identical; the operator keeps the graph for the next batch).
+        Default: on where launches weigh (half volume <= 2^17 sites), off on
+        larger lattices, whose kernels run for a millisecond or more.
         overlap: run the high-precision solves and contractions on a second
         stream from a host thread, concurrently with the low-precision batches
         (FP64 work uses other units than the FP32 arithmetic of the LP solves);
@@ -68,6 +72,8 @@ class TsmPipeline:
         if lp_layout not in ("il", "std") or (lp_layout == "il" and not il_ok):
             raise ValueError("lp_layout 'il' needs F16/BF16 and 18-real 16-bit links; 'std' always works")
         self.lp_il = lp_layout == "il"
+        vh = op.L[0] * op.L[1] * op.L[2] * op.L[3] // 2
+        self.lp_graph = (vh <= 1 << 17) if lp_graph is None else bool(lp_graph)
         self.nu = 2.0 * op.kappa * op.mu
         n_all = self.n_hp + self.n_lp
         self.len = {"local": 16 * self.T, "oneD": 64 * self.T}
@@ -220,7 +226,7 @@ class TsmPipeline:
         # the truncated solves stop after a handful of iterations: poll often so
         # that no masked-out iterations are launched past convergence
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
-                                 check_every=min(2, self.check_every), schur=self.schur)
+                                 check_every=min(2, self.check_every), schur=self.schur, graph=self.lp_graph)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
             if self.lp_il:

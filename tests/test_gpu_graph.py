@@ -121,3 +121,42 @@ def test_group_rejects_a_shared_operator_and_accepts_clones():
     assert st == 0 and torch.equal(f[2], f[3])
     twin.close()
     op.close()
+
+
+@pytest.mark.parametrize("mode", ["lp_il", "hp"])
+def test_kept_graph_replays_are_bit_identical(mode):
+    """The operator keeps the iteration graph of its last single-set solve and
+    replays it for the next solve with the same buffers, systems and
+    parameters: every such solve (new sources in the same buffers) gives the
+    bits and the launch count of an eager solve; a solve with other buffers in
+    between captures its own graph and leaves the results unchanged."""
+    tl = require_gpu()
+    L = (8, 8, 8, 8)
+    op = tl.Operator(L, 0.161, 0.003, to_dev(synth.gauge_field(L, 7)), recon=18)
+    if mode == "lp_il":
+        kw = dict(mode=tl.CG_PLAIN, prec=tl.F16, check_every=2)
+        tol, fp = 1e-2, tl.F16
+    else:
+        kw = dict(mode=tl.CG_MIXED, inner_prec=tl.F32, delta=3e-5, check_every=4)
+        tol, fp = 1e-9, tl.F64
+    n = 4
+    eta = tl.empty_field(L, fp, n)
+    x = tl.empty_field(L, fp, n)
+
+    def solve(first, graph, xb=x, eb=eta, k=n):
+        tl.z4_noise(L, eb, fp, 11, first, k)
+        c0 = tl.tm_launch_count()
+        _, st = tl.tm_cg_solve(op, xb, eb, k, tl.cg_params(tol, 3000, schur=True, graph=graph, **kw))
+        torch.cuda.synchronize()
+        return xb.clone(), [s["iters"] for s in st], tl.tm_launch_count() - c0
+
+    solve(0, False)                                      # the autotuner's first launches
+    ref = [solve(f, False) for f in (0, 4, 8)]
+    got = [solve(f, True) for f in (0, 4)]              # capture, then replay of the kept graph
+    x2 = tl.empty_field(L, fp, 2)
+    e2 = tl.empty_field(L, fp, 2)
+    solve(0, True, x2, e2, 2)                            # other buffers and systems: a new graph
+    got.append(solve(8, True))                           # captured again for the first buffers
+    for (xr, ir, cr), (xg, ig, cg) in zip(ref, got):
+        assert torch.equal(xr, xg) and ir == ig and cr == cg
+    op.close()
