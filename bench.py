@@ -30,15 +30,15 @@ CONFIGS = {
     # the paper's production volume and TSM layout (Secs. 2.1, 3), synthetic links
     "tsm32": dict(L=(32, 32, 32, 64), kappa=0.161, mu=0.003, n_hp=8, n_lp=256, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
+                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff", hp_ru="f64"),
     # the same layout on 24^3 x 48 (fields larger than L2): the size of the ncu captures
     "tsm24": dict(L=(24, 24, 24, 48), kappa=0.161, mu=0.003, n_hp=8, n_lp=24, batch=16,
                   lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
+                  seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff", hp_ru="f64"),
     # small case for quick checks
     "tsm8": dict(L=(8, 8, 8, 8), kappa=0.161, mu=0.003, n_hp=4, n_lp=28, batch=16,
                  lp_prec="f16", hp_inner="f32", tol_lp=1e-2, tol_hp=1e-9, gauge_seed=1237,
-                 seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff"),
+                 seed=20140126, schur=True, delta=3e-5, recon=0, overlap=False, hp_loops="ff", hp_ru="f64"),
 }
 
 FP32_LANES_PER_SM = 128    # FP32 FMA lanes per SM (4 partitions x 32)
@@ -48,10 +48,11 @@ METRIC = "Dslash HBM GB/s and % roofline; TSM loop sec/source at fixed error vs 
 
 def workload_name(c):
     X, Y, Z, T = c["L"]
-    return ("TSM loops %dx%dx%dx%d kappa=%g mu=%g: %d LP (%s, |r|<=%g) + %d HP (mixed %s/FP64, "
+    return ("TSM loops %dx%dx%dx%d kappa=%g mu=%g: %d LP (%s, |r|<=%g) + %d HP (mixed %s/FP64, %s residuals, "
             "|r|<=%g, delta=%g%s), batches of %d, %s CG, local+oneD x (one-end, generalised one-end)" % (
                 X, Y, Z, T, c["kappa"], c["mu"], c["n_lp"] + c["n_hp"], c["lp_prec"], c["tol_lp"],
-                c["n_hp"], c["hp_inner"], c["tol_hp"], c["delta"],
+                c["n_hp"], c["hp_inner"], "float-float" if c.get("hp_ru") == "ff" else "FP64",
+                c["tol_hp"], c["delta"],
                 ", on a second stream" if c.get("overlap") else "", c["batch"],
                 "even/odd-preconditioned" if c["schur"] else "unpreconditioned"))
 
@@ -376,7 +377,7 @@ def _efficiency_of(tl, TsmPipeline, op, pipe, c, ms, dist, rank, world, n_src, m
     side = TsmPipeline(op, n_side, 0, batch=c["n_hp"], lp_prec=tl.PREC[c["lp_prec"]],
                        hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
                        seed=c["seed"], first_src=world * n_src + rank * n_side, schur=c["schur"],
-                       delta=c["delta"], hp_loop_prec=tl.PREC[c["hp_loops"]])
+                       delta=c["delta"], hp_loop_prec=tl.PREC[c["hp_loops"]], hp_ru_prec=tl.PREC[c["hp_ru"]])
     side.run_sources()
     side_ok = all(s["status"] == 0 for s in side.stats_hp + side.stats_lp)
     obs_side = _observables(side, dict(c, n_hp=n_side))
@@ -415,7 +416,8 @@ def run_ours(args):
     mk = lambda o, **kw: TsmPipeline(o, c["n_hp"], c["n_lp"], batch=c["batch"], lp_prec=tl.PREC[c["lp_prec"]],
                                hp_inner=tl.PREC[c["hp_inner"]], tol_lp=c["tol_lp"], tol_hp=c["tol_hp"],
                                seed=c["seed"], first_src=rank * n_src, schur=c["schur"],
-                               delta=c["delta"], overlap=c["overlap"], hp_loop_prec=tl.PREC[c["hp_loops"]], **kw)
+                               delta=c["delta"], overlap=c["overlap"], hp_loop_prec=tl.PREC[c["hp_loops"]],
+                               hp_ru_prec=tl.PREC[c["hp_ru"]], **kw)
     pipe = mk(op)
     _log("inputs ready")
     for _ in range(args.warmup):
@@ -517,7 +519,8 @@ def run_ours(args):
                                                lp_prec=tl.PREC[cs["lp_prec"]], hp_inner=tl.PREC[cs["hp_inner"]],
                                                tol_lp=cs["tol_lp"], tol_hp=cs["tol_hp"], seed=cs["seed"],
                                                first_src=rank * n_src, schur=cs["schur"], delta=cs["delta"],
-                                               hp_loop_prec=tl.PREC[cs["hp_loops"]], **kw)
+                                               hp_loop_prec=tl.PREC[cs["hp_loops"]],
+                                               hp_ru_prec=tl.PREC[cs["hp_ru"]], **kw)
             p_s = mk_s(op_s)
             p_s.run(dist)  # warm-up
             torch.cuda.synchronize()
@@ -599,8 +602,9 @@ def run_ours(args):
             "metric": METRIC, "value": round(ms * 1e-3 / (world * n_src), 6), "unit": "s/source",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
-            "dtype_detail": ("LP solves f16 (f32 arithmetic); HP solves f32 inner + f64 reliable updates, "
-                             "f64 solution accumulation and dot products; HP loops (D_W s and contractions) "
+            "dtype_detail": ("LP solves f16 (f32 arithmetic); HP solves f32 inner, reliable-update and final "
+                             "residuals " + ("float-float (~48-bit)" if c["hp_ru"] == "ff" else "f64") +
+                             ", f64 solution accumulation and dot products; HP loops (D_W s and contractions) "
                              + ("float-float (~48-bit) arithmetic on the f64 solutions" if c["hp_loops"] == "ff"
                                 else "f64") + "; loop sums f64"),
             "data": "synthetic: smooth random SU(3) links U = exp(0.3 i H), Z4 sources",
@@ -1034,6 +1038,8 @@ def main():
     ap.add_argument("--recon", type=int, default=None, choices=[0, 12, 18],
                     help="reals per link in the narrow copies; 0 = per precision")
     ap.add_argument("--overlap", type=int, default=None, help="override HP/LP stream overlap")
+    ap.add_argument("--hp-ru", default=None, choices=["f64", "ff"],
+                    help="override the arithmetic of the HP solves' true residuals")
     ap.add_argument("--lp-prec", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-inner", default=None, choices=["f16", "bf16", "f32"])
     ap.add_argument("--hp-loops", default=None, choices=["f64", "ff"],
@@ -1055,6 +1061,8 @@ def main():
         c["delta"] = args.delta
     if args.overlap is not None:
         c["overlap"] = bool(args.overlap)
+    if args.hp_ru is not None:
+        c["hp_ru"] = args.hp_ru
     if args.recon is not None:
         c["recon"] = args.recon
     else:

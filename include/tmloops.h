@@ -238,7 +238,16 @@ tm_status_t tm_hpe_exact(const tm_params_t *p, double *out);
  *   CUDA graph and replayed, one graph launch per poll; the results are
  *   bit-identical to graph = 0 (converged systems are masked on the device
  *   either way).  Launches inside the graph are not traced individually: each
- *   replay is one trace record "cg.graph".                                  */
+ *   replay is one trace record "cg.graph".  A single-set solve keeps its graph
+ *   in the operator and replays it, without capturing, in the next solve whose
+ *   launches are the same (same buffers, systems and parameters).
+ * ru_prec (MIXED): TM_PREC_F64 (0) computes the true residuals
+ *   r = b - M^dag M x of the reliable updates (and the final one) in FP64;
+ *   TM_PREC_FF in float-float on the FP32 pipes (about 48-bit significands,
+ *   from float-float copies of x and b; x itself still accumulates in FP64).
+ *   FF residuals are exact to about 2^-48 cond(M^dag M) |b|, so only solves
+ *   conditioned well enough for that to stay far below tol should use them.
+ *   Other values: TM_ERR_ARG.                                               */
 typedef enum { TM_CG_PLAIN = 0, TM_CG_MIXED = 1 } tm_cg_mode_t;
 
 typedef struct {
@@ -252,6 +261,7 @@ typedef struct {
   int true_residual;     /* PLAIN: compute |b - M^dag M x| / |b| at the end */
   int schur;             /* 1: even/odd preconditioned solve (see below), 0: plain M */
   int graph;             /* 1: replay the iterations between polls as one CUDA graph */
+  tm_prec_t ru_prec;     /* MIXED: arithmetic of the true residuals, F64 (0) or FF   */
 } tm_cg_params_t;
 
 typedef struct {

@@ -37,10 +37,12 @@ namespace tml {
 tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const double* beta,
                  const int* active, int nrhs, int par0, int npar, cudaStream_t s);
 tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
-                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s);
+                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s, void* xff = nullptr);
 tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
                     void* p, const double* ratio, const int* mask, int nrhs, int par0, int npar,
-                    cudaStream_t s);
+                    cudaStream_t s, bool r_ff = false);
+tm_status_t convert_masked(const Geom& g, void* out, tm_prec_t po, const void* in, tm_prec_t pi,
+                           int nrhs, const int* active, cudaStream_t s);
 tm_status_t twist(const Geom& g, tm_prec_t prec, void* out, const void* in, double nu, int inverse,
                   int par, int nrhs, cudaStream_t s);
 
@@ -335,6 +337,12 @@ struct CgRun {
   int par0 = 0, npar = 2, nwarp = 0;
   void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
   void *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr;
+  // MIXED with ru_prec = FF: the true residuals in float-float from the
+  // float-float copies of x (written by every fold) and b; r64 and tmp64 then
+  // hold float-float fields of the same size
+  bool ru_ff = false;
+  void *xff = nullptr, *bff = nullptr;
+  tm_prec_t ru = TM_PREC_F64;
   double* partial = nullptr;
   CgState st{};
   CgScalars sc{};
@@ -363,6 +371,10 @@ static tm_status_t check_params(const tm_cg_params_t* prm) {
   if (prm->mode != TM_CG_PLAIN && !mixed) { set_error("tm_cg_solve: unknown mode %d", (int)prm->mode); return TM_ERR_ARG; }
   if (mixed && !(prm->delta > 0.0 && prm->delta < 1.0)) { set_error("tm_cg_solve: delta must be in (0, 1)"); return TM_ERR_ARG; }
   if (prm->schur != 0 && prm->schur != 1) { set_error("tm_cg_solve: schur must be 0 or 1"); return TM_ERR_ARG; }
+  if (mixed && prm->ru_prec != TM_PREC_F64 && prm->ru_prec != TM_PREC_FF) {
+    set_error("tm_cg_solve: ru_prec must be F64 or FF");
+    return TM_ERR_ARG;
+  }
   if (prm->graph != 0 && prm->graph != 1) { set_error("tm_cg_solve: graph must be 0 or 1"); return TM_ERR_ARG; }
   const tm_prec_t lo = mixed ? prm->inner_prec : prm->prec;
   if ((int)lo < 0 || (int)lo > 3) { set_error("tm_cg_solve: precision must be F64, F32, F16 or BF16"); return TM_ERR_ARG; }
@@ -379,6 +391,8 @@ tm_status_t CgRun::setup() {
   par0 = schur ? 1 : 0;
   npar = schur ? 1 : 2;
   const tm_geom_t gg = {{g.L[0], g.L[1], g.L[2], g.L[3]}};
+  ru_ff = mixed && prm.ru_prec == TM_PREC_FF;
+  ru = ru_ff ? TM_PREC_FF : TM_PREC_F64;
   il = !mixed && (lo == TM_PREC_F16 || lo == TM_PREC_BF16) && op->recon_p[lo] == 18 && cg_il_on();
   if (x_is_il && !il) {
     set_error("tm_cg_solve_il: needs a plain F16/BF16 solve with 18-real links and the interleaved solver enabled");
@@ -394,6 +408,7 @@ tm_status_t CgRun::setup() {
     Carver c{pass ? (char*)op->work : nullptr};
     if (mixed) {
       b64 = c.take(F64); r64 = c.take(F64); tmp64 = c.take(F64);
+      if (ru_ff) { xff = c.take(F64); bff = c.take(F64); }
       y = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
     } else {
       b = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
@@ -457,6 +472,10 @@ tm_status_t CgRun::setup() {
     TM_TRY(rescale(g, lo, r, b64, st.sigma, nullptr, nullptr, nullptr, nrhs, par0, npar, s));
     TM_TRY(memset_d(x, F64, s));
     TM_TRY(memset_d(y, F, s));
+    if (ru_ff) {
+      TM_TRY(convert_masked(g, bff, TM_PREC_FF, b64, TM_PREC_F64, nrhs, nullptr, s));
+      TM_TRY(memset_d(xff, F64, s));
+    }
   } else {
     TM_TRY(memcpy_d2d(r, b, F, s));
     TM_TRY(memset_d(xs, F, s));
@@ -482,16 +501,16 @@ tm_status_t CgRun::iteration() {
     TM_TRY(scalar_launch(cg_beta_plain_kernel, st, sc, s));
   } else {
     TM_TRY(scalar_launch(cg_beta_mixed_kernel, st, sc, s));
-    // reliable update for the systems that asked for one: x += sigma y,
-    // r = b - Op^dag Op x in FP64
-    TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, par0, npar, s));
-    TM_TRY(Op.apply(TM_PREC_F64, x, tmp64, nullptr, st.ru));
+    // reliable update for the systems that asked for one: x += sigma y (FP64),
+    // r = b - Op^dag Op x in FP64 or float-float (ru_prec)
+    TM_TRY(fold(g, lo, x, y, st.sigma, st.ru, nrhs, par0, npar, s, ru_ff ? xff : nullptr));
+    TM_TRY(Op.apply(ru, ru_ff ? xff : x, tmp64, nullptr, st.ru));
     DslashCall e4;
-    e4.out = r64; e4.b = b64; e4.epi = EPI_RESID; e4.partial = partial; e4.active = st.ru;
-    TM_TRY(Op.apply_dag(TM_PREC_F64, tmp64, e4));
+    e4.out = r64; e4.b = ru_ff ? bff : b64; e4.epi = EPI_RESID; e4.partial = partial; e4.active = st.ru;
+    TM_TRY(Op.apply_dag(ru, tmp64, e4));
     TM_TRY(reduce());
     TM_TRY(scalar_launch(cg_ru_kernel, st, sc, s));
-    TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s));
+    TM_TRY(rescale(g, lo, r, r64, st.sigma, p, st.ratio, st.ru, nrhs, par0, npar, s, ru_ff));
   }
   if (il) return il_xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s);
   return xpay(g, lo, p, r, st.beta, st.active, nrhs, par0, npar, s);
@@ -519,7 +538,7 @@ bool CgRun::any_active() const {
 tm_status_t CgRun::finish(tm_status_t* worst_out) {
   const Geom& g = op->g;
   const SolveOp Op = A();
-  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, par0, npar, s));
+  if (mixed) TM_TRY(fold(g, lo, x, y, st.sigma, nullptr, nrhs, par0, npar, s, ru_ff ? xff : nullptr));
   std::vector<double> h_bb(nrhs), h_rr(nrhs), h_sig(nrhs);
   std::vector<int> h_it(nrhs), h_nru(nrhs), h_status(nrhs);
   auto fetch = [&]() -> bool {
@@ -548,10 +567,11 @@ tm_status_t CgRun::finish(tm_status_t* worst_out) {
   if (recompute) {
     void* tmp = mixed ? tmp64 : t;
     void* res = mixed ? r64 : r;
-    TM_TRY(Op.apply(hi, mixed ? x : xs, tmp, nullptr, nullptr));
+    const tm_prec_t pr = mixed ? ru : hi;
+    TM_TRY(Op.apply(pr, mixed ? (ru_ff ? xff : x) : xs, tmp, nullptr, nullptr));
     DslashCall e4;
-    e4.out = res; e4.b = bb_field; e4.epi = EPI_RESID; e4.partial = partial;
-    TM_TRY(Op.apply_dag(hi, tmp, e4));
+    e4.out = res; e4.b = ru_ff ? bff : bb_field; e4.epi = EPI_RESID; e4.partial = partial;
+    TM_TRY(Op.apply_dag(pr, tmp, e4));
     TM_TRY(reduce());
     if (cudaMemcpyAsync(h_true.data(), st.red, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -694,6 +714,7 @@ static tm_cg_graph_key graph_key(const CgRun& r, int k) {
   key.check_every = r.prm.check_every;
   key.true_residual = r.prm.true_residual;
   key.schur = r.prm.schur;
+  key.ru_prec = (int)r.prm.ru_prec;
   return key;
 }
 
@@ -702,7 +723,7 @@ static bool same_key(const tm_cg_graph_key& a, const tm_cg_graph_key& b) {
          a.host_flags == b.host_flags && a.nrhs == b.nrhs && a.k == b.k && a.il == b.il && a.tol == b.tol &&
          a.delta == b.delta && a.max_iter == b.max_iter && a.mode == b.mode && a.prec == b.prec &&
          a.inner_prec == b.inner_prec && a.check_every == b.check_every && a.true_residual == b.true_residual &&
-         a.schur == b.schur;
+         a.schur == b.schur && a.ru_prec == b.ru_prec;
 }
 
 static tm_status_t solve_group(std::vector<CgRun>& runs, const tm_cg_params_t* prm, cudaStream_t s_user,

@@ -285,10 +285,10 @@ __global__ void xpay_kernel(Geom g, void* p, const void* r, const double* beta, 
 }
 
 // x64 += sigma[rhs] * y (exact widening), y = 0, for systems with mask[rhs] != 0;
-// sigma may be null (scale 1)
+// sigma may be null (scale 1); xff (may be null) receives x64 in float-float
 template <class S>
 __global__ void fold_kernel(Geom g, void* x64, void* y, const double* sigma, const int* mask,
-                            int nrhs, int par0, int npar) {
+                            int nrhs, int par0, int npar, void* xff) {
   const long n = (long)npar * g.Vh;
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * nrhs) return;
@@ -309,11 +309,13 @@ __global__ void fold_kernel(Geom g, void* x64, void* y, const double* sigma, con
   }
   store_spinor<double>(x64, bx, (size_t)g.Vh, a);
   store_spinor_f64<S>(y, by, (size_t)g.Vh, b);
+  if (xff) store_spinor_f64<FFloat>(xff, SpinorRef<FFloat>::base(g, rhs, par, cb), (size_t)g.Vh, a);
 }
 
 // Reliable-update rescaling of the inner iteration (masked systems):
 //   r = r64 / sigma[rhs]   and, if p != null,   p *= ratio[rhs]
-template <class S>
+// (r64 stored as SR: FP64, or float-float)
+template <class S, class SR>
 __global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* sigma, void* p,
                                const double* ratio, const int* mask, int nrhs, int par0, int npar) {
   const long n = (long)npar * g.Vh;
@@ -323,11 +325,11 @@ __global__ void rescale_kernel(Geom g, void* r, const void* r64, const double* s
   if (mask && !mask[rhs]) return;
   const int rem = (int)(i % n);
   const int par = par0 + rem / g.Vh, cb = rem % g.Vh;
-  const size_t b64 = SpinorRef<double>::base(g, rhs, par, cb);
+  const size_t b64 = SpinorRef<SR>::base(g, rhs, par, cb);
   const size_t bs = SpinorRef<S>::base(g, rhs, par, cb);
   const double inv = 1.0 / sigma[rhs];
   Cx<double> v[12];
-  load_spinor<double>(v, r64, b64, (size_t)g.Vh);
+  load_spinor_f64<SR>(v, r64, b64, (size_t)g.Vh);
 #pragma unroll
   for (int j = 0; j < 12; ++j) v[j] = inv * v[j];
   store_spinor_f64<S>(r, bs, (size_t)g.Vh, v);
@@ -353,11 +355,11 @@ tm_status_t xpay(const Geom& g, tm_prec_t prec, void* p, const void* r, const do
 }
 
 tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double* sigma,
-                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s) {
+                 const int* mask, int nrhs, int par0, int npar, cudaStream_t s, void* xff) {
   const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    fold_kernel<S><<<nb, 256, 0, s>>>(g, x64, y, sigma, mask, nrhs, par0, npar);
+    fold_kernel<S><<<nb, 256, 0, s>>>(g, x64, y, sigma, mask, nrhs, par0, npar, xff);
     count_launch();
     return check_launch("fold");
   });
@@ -365,11 +367,14 @@ tm_status_t fold(const Geom& g, tm_prec_t prec, void* x64, void* y, const double
 
 tm_status_t rescale(const Geom& g, tm_prec_t prec, void* r, const void* r64, const double* sigma,
                     void* p, const double* ratio, const int* mask, int nrhs, int par0, int npar,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool r_ff) {
   const unsigned nb = blocks_for((long)npar * g.Vh * nrhs, 256);
   return by_prec(prec, [&](auto tag) {
     using S = decltype(tag);
-    rescale_kernel<S><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs, par0, npar);
+    if (r_ff)
+      rescale_kernel<S, FFloat><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs, par0, npar);
+    else
+      rescale_kernel<S, double><<<nb, 256, 0, s>>>(g, r, r64, sigma, p, ratio, mask, nrhs, par0, npar);
     count_launch();
     return check_launch("rescale");
   });

@@ -18,7 +18,7 @@ struct tm_cg_graph_key {
   const int* host_flags;
   int nrhs, k, il;
   double tol, delta;
-  int max_iter, mode, prec, inner_prec, check_every, true_residual, schur;
+  int max_iter, mode, prec, inner_prec, check_every, true_residual, schur, ru_prec;
 };
 struct tm_cg_graph_cache {
   bool valid;

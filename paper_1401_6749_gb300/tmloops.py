@@ -48,7 +48,7 @@ class tm_cg_params_t(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("prec", ctypes.c_int), ("inner_prec", ctypes.c_int), ("delta", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("true_residual", ctypes.c_int), ("schur", ctypes.c_int),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("ru_prec", ctypes.c_int)]
 
 
 class tm_cg_stats_t(ctypes.Structure):
@@ -291,11 +291,11 @@ def z4_noise(L, eta, prec, seed, first_src, nsrc, stream=None):
 
 
 def cg_params(tol, max_iter=10000, mode=CG_PLAIN, prec=F64, inner_prec=F32, delta=0.1,
-              check_every=8, true_residual=False, schur=False, graph=False):
+              check_every=8, true_residual=False, schur=False, graph=False, ru_prec=F64):
     p = tm_cg_params_t()
     p.tol, p.max_iter, p.mode, p.prec, p.inner_prec = float(tol), int(max_iter), int(mode), int(prec), int(inner_prec)
     p.delta, p.check_every, p.true_residual = float(delta), int(check_every), int(bool(true_residual))
-    p.schur, p.graph = int(bool(schur)), int(bool(graph))
+    p.schur, p.graph, p.ru_prec = int(bool(schur)), int(bool(graph)), int(ru_prec)
     return p
 
 

@@ -32,12 +32,16 @@ class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
                  delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False,
-                 lp_layout=None, lp_graph=None):
+                 lp_layout=None, lp_graph=None, hp_ru_prec=None):
         """lp_layout: "il" keeps the LP solutions in the system-interleaved
         layout (tm_cg_solve_il), applies D_W there (tm_dslash_il) and contracts
         there (loop_contract_*_il, gamma_5 of the generalised estimator as
         right_g5); "std" uses the standard layout throughout.  Default: "il"
         for FP16/BF16 with 18-real 16-bit links (recon 18 or 0), else "std".
+        hp_ru_prec: arithmetic of the HP solves' true residuals (reliable
+        updates), F64 (default) or FF.  FF is exact to about 2^-48 cond(M^dag M)
+        relative to |b|: only for solves well enough conditioned that this
+        stays far below tol_hp.
         lp_graph: replay the truncated LP solves' iterations as CUDA graphs
         (bit-identical; the operator keeps the graph for the next batch).
         Default: on where launches weigh (half volume <= 2^17 sites), off on
@@ -65,6 +69,9 @@ class TsmPipeline:
         if hp_loop_prec not in (tl.F64, tl.FF):
             raise ValueError("hp_loop_prec must be F64 or FF")
         self.hp_loop_prec = hp_loop_prec
+        self.hp_ru_prec = tl.F64 if hp_ru_prec is None else hp_ru_prec
+        if self.hp_ru_prec not in (tl.F64, tl.FF):
+            raise ValueError("hp_ru_prec must be F64 or FF")
         self.kinds = tuple(kinds)
         il_ok = lp_prec in (tl.F16, tl.BF16) and op.recon in (0, 18)
         if lp_layout is None:
@@ -190,7 +197,8 @@ class TsmPipeline:
 
     def _run_hp(self, stream):
         hp_params = tl.cg_params(self.tol_hp, self.max_iter, tl.CG_MIXED, inner_prec=self.hp_inner,
-                                 delta=self.delta, check_every=self.check_every, schur=self.schur)
+                                 delta=self.delta, check_every=self.check_every, schur=self.schur,
+                                 ru_prec=self.hp_ru_prec)
         stats = []
         for b0 in range(0, self.n_hp, self.batch):
             n = min(self.batch, self.n_hp - b0)
