@@ -163,11 +163,11 @@ __device__ __forceinline__ void il_dir(float (&up)[2][4], float (&q)[6][4], cons
   const unsigned bf_up = uf ^ 0x80000000u, bb_up = ub;
   const unsigned bf_m = SF < 0 ? uf ^ 0x00008000u : bf_up;
   const unsigned bb_m = SB < 0 ? ub ^ 0x80008000u : bb_up;
-  // the first product into each accumulator of the site seeds it (directions
-  // 0 and 1 for the two upper sets, il_quad_first for the quads)
+  // the first product into each accumulator of the site seeds it (direction 0
+  // for the upper spins, il_quad_first for the quads)
   constexpr int q0 = il_quad(0, G::bk0), q1 = il_quad(1, G::bk1);
-  il_mma_acc<S, (MU < 2)>(up[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
-  il_mma_acc<S, (MU < 2)>(up[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
+  il_mma_acc<S, (MU == 0)>(up[0], h0f0, h0f1, h0b0, h0b1, bf_up, bb_up);
+  il_mma_acc<S, (MU == 0)>(up[1], h1f0, h1f1, h1b0, h1b1, bf_up, bb_up);
   if constexpr (G::bc0 == 0) il_mma_acc<S, il_quad_first(q0) == MU>(q[q0], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
   else il_mma_acc<S, il_quad_first(q0) == MU>(q[q0], h1f0, h1f1, h1b0, h1b1, bf_m, bb_m);
   if constexpr (G::bc1 == 0) il_mma_acc<S, il_quad_first(q1) == MU>(q[q1], h0f0, h0f1, h0b0, h0b1, bf_m, bb_m);
@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         break;
       }
       const unsigned char* sd = ring + st * ST::kBytes;
-      // upper spins: two sets (even and odd directions: shorter MMA chains);
-      // lower spins: the six phase quads
-      float ua[2][4], ub4[2][4], qq[6][4];  // seeded by their first products
+      // upper spins: one accumulator pair over the four directions; lower
+      // spins: the six phase quads
+      float ua[2][4], qq[6][4];  // seeded by their first products
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
         uint2 pf[4], pb[4];
@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         const unsigned negf = (mu == 3 && (bf & 1u)) ? 0x80008000u : 0u;
         const unsigned negb = (mu == 3 && (bf & 2u)) ? 0x80008000u : 0u;
         if (mu == 0) il_dir<S, 0, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
-        else if (mu == 1) il_dir<S, 1, SF>(ub4, qq, l, pf, pb, uf, ub, negf, negb);
+        else if (mu == 1) il_dir<S, 1, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
         else if (mu == 2) il_dir<S, 2, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
-        else il_dir<S, 3, SF>(ub4, qq, l, pf, pb, uf, ub, negf, negb);
+        else il_dir<S, 3, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
       }
       // epilogue: out = T_out(T_c(c) + s_hop H in), then the CG update / residual;
       // lanes t = 3 compute on the words of t = 0 and store nothing
@@ -399,8 +399,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       float hs[4][4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        hs[0][c] = __fadd_rn(ua[0][c], ub4[0][c]);
-        hs[1][c] = __fadd_rn(ua[1][c], ub4[1][c]);
+        hs[0][c] = ua[0][c];
+        hs[1][c] = ua[1][c];
       }
 #pragma unroll
       for (int rr = 0; rr < 4; rr += 2) {

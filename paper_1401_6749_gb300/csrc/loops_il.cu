@@ -328,11 +328,13 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
 }
 
 // ----------------------------------------------------------------- local
-// Lane (g, t) of a warp reads the words of systems g, g + 8 at colour t of
-// both fields (one 8-byte load per spin and field, coalesced rows) and keeps
-// the 16 products conj(L_a) R_b of both systems in FP32 (mixed-precision
-// FMAs on the 16-bit halves: exact products); the colour sum is the final
-// shuffle over t.
+// A warp takes two sites at a time: lane 16 h + j holds system j of site h,
+// whose word of row k sits in slot 2 ((j & 7) ^ (k = 2 mod 3 ? 4 : 0)) + j / 8,
+// so each half-warp reads one 64-byte row per load.  A lane keeps the 16
+// products conj(L_a) R_b of its system summed over the colours in FP32
+// (mixed-precision FMAs on the 16-bit halves: exact products); the two
+// half-warps' sums are added at the end.  The next site's 24 words are in
+// flight while one site is computed.
 constexpr int kLcWarps = 4;
 constexpr int kLcChunk = 512;
 
@@ -345,103 +347,81 @@ __device__ __forceinline__ void mfma(float& d, unsigned short a, unsigned short 
 }
 
 template <class S>
-__global__ void __launch_bounds__(kLcWarps * 32) local_il_kernel(Geom g, const uint2* L, const uint2* R, int nrhs,
-                                                                 int nblk, int nchunk, int right_g5, double* partial) {
+__global__ void __launch_bounds__(kLcWarps * 32) local_il_kernel(Geom g, const unsigned* L, const unsigned* R,
+                                                                 int nrhs, int nblk, int nchunk, int right_g5,
+                                                                 double* partial) {
   __shared__ float red[kLcWarps][kIlRows][32];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int blk = blockIdx.x % nblk, chunk = blockIdx.x / nblk;
   const int t = blockIdx.y >> 1, par = blockIdx.y & 1;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int teff = tq < 3 ? tq : 0;
-  const int woff = teff * 8 + (teff == 2 ? gq ^ 4 : gq);  // uint2 units
-  // acc[h][a][b][re/im]: system g (h = 0) and g + 8 (h = 1)
-  float acc[2][4][4][2];
+  const int h = lane >> 4, j = lane & 15;
+  const int slot01 = 2 * (j & 7) + (j >> 3), slot2 = 2 * ((j & 7) ^ 4) + (j >> 3);
+  float acc[16][2];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) acc[h][x][y][0] = acc[h][x][y][1] = 0.0f;
-  const size_t plane = ((size_t)blk * 2 + par) * (size_t)g.Vh * kIlSiteU2;
-  const uint2* lp = L + plane + woff;
-  const uint2* rp = R + plane + woff;
-  const int iend = min(g.V3h, (chunk + 1) * kLcChunk);
-  // the words of site i + 4 are in flight while site i is computed
-  uint2 ln[4], rn[4];
+  for (int q = 0; q < 16; ++q) acc[q][0] = acc[q][1] = 0.0f;
+  const size_t plane = ((size_t)blk * 2 + par) * (size_t)g.Vh * (kIlSiteBytes / 4);
+  const unsigned* lp = L + plane;
+  const unsigned* rp = R + plane;
+  const int i0 = chunk * kLcChunk, iend = min(g.V3h, i0 + kLcChunk);
+  // site i0 + 2 (wq + 4 m) + h of slice t
+  unsigned ln[12], rn[12];
   auto fetch = [&](int i) {
-    const size_t w = (size_t)(t * g.V3h + i) * kIlSiteU2;
+    const size_t w = (size_t)(t * g.V3h + i) * (kIlSiteBytes / 4);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      ln[s] = lp[w + 24 * s];
-      rn[s] = rp[w + 24 * s];
+    for (int k = 0; k < 12; ++k) {
+      const int sl = k % 3 == 2 ? slot2 : slot01;
+      ln[k] = lp[w + 16 * k + sl];
+      rn[k] = rp[w + 16 * k + sl];
     }
   };
-  int i = chunk * kLcChunk + wq;
+  int i = i0 + 2 * wq + h;
   if (i < iend) fetch(i);
-  for (; i < iend; i += kLcWarps) {
-    uint2 l[4], r[4];
+  for (; i < iend; i += 2 * kLcWarps) {
+    unsigned l[12], r[12];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      l[s] = ln[s];
-      r[s] = rn[s];
+    for (int k = 0; k < 12; ++k) {
+      l[k] = ln[k];
+      r[k] = rn[k];
     }
-    if (i + kLcWarps < iend) fetch(i + kLcWarps);
-    if (tq == 3) continue;
+    if (i + 2 * kLcWarps < iend) fetch(i + 2 * kLcWarps);
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const unsigned lw = h ? l[x].y : l[x].x;
-        const unsigned short lre = (unsigned short)(lw & 0xffffu), lim = (unsigned short)(lw >> 16);
+      for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          const unsigned rw = h ? r[y].y : r[y].x;
+        for (int c = 0; c < 3; ++c) {
+          const unsigned lw = l[3 * a + c], rw = r[3 * b + c];
+          const unsigned short lre = (unsigned short)(lw & 0xffffu), lim = (unsigned short)(lw >> 16);
           const unsigned short rre = (unsigned short)(rw & 0xffffu), rim = (unsigned short)(rw >> 16);
           // conj(l) r = (lre rre + lim rim) + i (lre rim - lim rre)
-          mfma<S>(acc[h][x][y][0], lre, rre);
-          mfma<S>(acc[h][x][y][0], lim, rim);
-          mfma<S>(acc[h][x][y][1], lre, rim);
-          mfma<S>(acc[h][x][y][1], (unsigned short)(lim ^ 0x8000u), rre);
+          mfma<S>(acc[4 * a + b][0], lre, rre);
+          mfma<S>(acc[4 * a + b][0], lim, rim);
+          mfma<S>(acc[4 * a + b][1], lre, rim);
+          mfma<S>(acc[4 * a + b][1], (unsigned short)(lim ^ 0x8000u), rre);
         }
-      }
   }
-  // colour sum over the lanes t = 0, 1, 2 (t = 3 holds zeros)
+  // the two sites of a step hold the same system: add the half-warps
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int q = 0; q < 16; ++q) {
+    acc[q][0] += __shfl_xor_sync(0xffffffffu, acc[q][0], 16);
+    acc[q][1] += __shfl_xor_sync(0xffffffffu, acc[q][1], 16);
+  }
+  if (h == 0) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          float v = acc[h][x][y][c];
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          acc[h][x][y][c] = v;
-        }
-  // lane t writes the components 8t .. 8t + 7 of systems g and g + 8
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int comp = 2 * (4 * x + y) + c;
-          if ((comp >> 3) == tq) {
-            const float sg = (right_g5 && y >= 2) ? -1.0f : 1.0f;
-            red[wq][gq + 8 * h][comp] = sg * acc[h][x][y][c];
-          }
-        }
+    for (int q = 0; q < 16; ++q) {
+      const float sg = (right_g5 && (q & 3) >= 2) ? -1.0f : 1.0f;  // q = 4 a + b
+      red[wq][j][2 * q] = sg * acc[q][0];
+      red[wq][j][2 * q + 1] = sg * acc[q][1];
+    }
+  }
   __syncthreads();
-  for (int j = threadIdx.x; j < kIlRows * 32; j += blockDim.x) {
-    const int s = j >> 5, comp = j & 31;
-    const int rhs = blk * kIlRows + s;
+  for (int k = threadIdx.x; k < kIlRows * 32; k += blockDim.x) {
+    const int sy = k >> 5, comp = k & 31;
+    const int rhs = blk * kIlRows + sy;
     if (rhs >= nrhs) continue;
     double v = 0.0;
 #pragma unroll
-    for (int q = 0; q < kLcWarps; ++q) v += (double)red[q][s][comp];
+    for (int q = 0; q < kLcWarps; ++q) v += (double)red[q][sy][comp];
     const size_t slot = (((size_t)rhs * g.L[3] + t) * 2 + par) * nchunk + chunk;
     partial[slot * 32 + comp] = v;
   }
@@ -501,8 +481,8 @@ extern "C" tm_status_t loop_contract_local_il(const tm_geom_t* gg, const void* l
   {
     TraceScope tr(s, prec == TM_PREC_F16 ? "local.f16il" : "local.bf16il", 2.0 * 24.0 * 2.0 * 2.0 * g.Vh, 0.0,
                   nrhs);
-    const uint2* l = static_cast<const uint2*>(left);
-    const uint2* r = static_cast<const uint2*>(right);
+    const unsigned* l = static_cast<const unsigned*>(left);
+    const unsigned* r = static_cast<const unsigned*>(right);
     if (prec == TM_PREC_F16)
       local_il_kernel<__half><<<grid, kLcWarps * 32, 0, s>>>(g, l, r, nrhs, nblk, nchunk, right_g5 != 0, scratch);
     else

@@ -15,6 +15,8 @@ not leak into the next result):
 This file is collected last so that a failure here leaves every other test
 already run.
 """
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -73,11 +75,19 @@ def test_noalloc_allocates_nothing():
     out = torch.empty(n * 16 * L[3] * 2, dtype=torch.float64, device="cuda")
     tl.loop_contract_local_noalloc(L, a, b, tl.F32, n, tl.LOOP_VV, out)   # first call: set-up
     torch.cuda.synchronize()
-    before = _alloc_state(tl)
-    for mode in (tl.LOOP_STD, tl.LOOP_VV, tl.LOOP_GEN):
-        tl.loop_contract_local_noalloc(L, a, b, tl.F32, n, mode, out)
-    torch.cuda.synchronize()
-    assert _alloc_state(tl) == before
+    # tensors of earlier tests that only the cycle collector frees would
+    # otherwise be released in the middle of the measurement
+    gc.collect()
+    gc.disable()
+    try:
+        before = _alloc_state(tl)
+        for mode in (tl.LOOP_STD, tl.LOOP_VV, tl.LOOP_GEN):
+            tl.loop_contract_local_noalloc(L, a, b, tl.F32, n, mode, out)
+        torch.cuda.synchronize()
+        after = _alloc_state(tl)
+    finally:
+        gc.enable()
+    assert after == before
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
