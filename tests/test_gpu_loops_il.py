@@ -191,3 +191,43 @@ def test_cg_solve_il_is_the_converted_solution(schur):
         tl.tm_cg_solve_il(op, x_il, eta, n, tl.cg_params(1e-6, 100, tl.CG_MIXED, inner_prec=tl.F32))
     assert e.value.status == 6
     op.close()
+
+
+def test_pipeline_bf16_lp_on_interleaved_layout():
+    """The TSM pipeline with BF16 LP solves on the interleaved layout (18-real
+    links; graph replay on at this size): every LP loop equals the oracle's
+    contraction of that LP solution (re-solved in one batch: the same bits) to
+    the BF16 rounding of D_W s and of the link products (8u), the local
+    one-end loops to FP32 rounding."""
+    tl = require_gpu()
+    from oracle.operator import apply_DW
+    from paper_1401_6749_gb300.tsm_pipeline import TsmPipeline
+    L = (6, 4, 4, 8)
+    T = L[3]
+    kappa, mu = 0.16, 0.01
+    U = synth.gauge_field(L, 2024)
+    op = tl.Operator(L, kappa, mu, to_dev(U), recon=18)
+    n_hp, n_lp = 2, 5
+    p = TsmPipeline(op, n_hp, n_lp, batch=4, lp_prec=tl.BF16, tol_lp=1e-2, tol_hp=1e-10, seed=5, delta=1e-3)
+    assert p.lp_il and p.lp_graph
+    p.run()
+    torch.cuda.synchronize()
+    assert all(s["status"] == 0 and s["rel_res"] <= 1e-2 for s in p.stats_lp)
+    n = n_hp + n_lp
+    eta = oz4(L, 5, 0, n)
+    x = tl.empty_field(L, tl.BF16, n)
+    tl.tm_cg_solve(op, x, pack(tl, L, eta, tl.BF16), n,
+                   tl.cg_params(1e-2, p.max_iter, tl.CG_PLAIN, prec=tl.BF16, check_every=2, schur=True))
+    xs = unpack(tl, L, x, tl.BF16, n)
+    g5dw = apply_DW(U, xs, kappa)
+    g5dw[..., 2:, :] *= -1
+    Ur = _round_links(U, 3)
+    ref = {"local_vv": oloops.local_loops(xs, xs, "vv"), "local_gen": oloops.local_loops(xs, g5dw, "gen"),
+           "oneD_vv": oloops.oneD_loops(Ur, xs, xs, "vv").reshape(n, 64, T),
+           "oneD_gen": oloops.oneD_loops(Ur, xs, g5dw, "gen").reshape(n, 64, T)}
+    tol = {"local_vv": 1e-5, "local_gen": 8 * UNIT_ROUNDOFF[3], "oneD_vv": 8 * UNIT_ROUNDOFF[3],
+           "oneD_gen": 8 * UNIT_ROUNDOFF[3]}
+    for k in p.kinds:
+        got = p.lp_loops[k].cpu().numpy().view(np.complex128).reshape(n, -1, T)
+        assert _max_rel(got, ref[k]) < tol[k], k
+    op.close()
