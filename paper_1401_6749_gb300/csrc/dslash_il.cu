@@ -1,14 +1,6 @@
-// FP16/BF16 Dslash on the tensor cores, on a system-interleaved field layout.
-//
-// Layout IL16 ("interleaved"): a set of nrhs 16-bit spinor fields stored as
-// ceil(nrhs / 16) blocks of 16 systems,
-//   [block][parity][cb][k = 3 spin + colour][slot 0..15] x 4 bytes,
-// one complex number (re in the low half) per slot, 64 bytes per (site, k)
-// and 768 contiguous bytes per site.  Systems j and j + 8 (j = 0..7), the two
-// a tensor-core lane needs, share one 8-byte pair of slots, at pair position
-// j in rows k = 0, 1 (mod 3) and j ^ 4 in rows k = 2 (mod 3): the XOR keeps
-// the three colour rows a warp reads at once in distinct shared-memory banks.
-// Slots of systems beyond nrhs are zero after tm_spinor_to_il.
+// FP16/BF16 Dslash on the tensor cores, on the system-interleaved field
+// layout IL16 (il_core.cuh: 16 systems per block, 768 contiguous bytes per
+// site, systems j and j + 8 in one 8-byte pair of slots).
 //
 // Every hop of a site is a small dense contraction over the 16 systems: with
 // the spin projection h_s = psi_s + SGN i^ak psi_{2+ac} (s = 0, 1; the upper
@@ -24,25 +16,23 @@
 // so the forward and backward hops of a direction are one product and the
 // accumulators stay in registers across the four directions: 16 MMAs per
 // site for 16 systems.  Lane (g, t) of a warp holds A rows g and g + 8 at
-// colour t (one 8-byte load per spin and hop straight from the layout), B
-// column g (output colour g/2, part g&1) at colour t (one link word per hop,
+// colour t (one 8-byte load per spin and hop from the staged site), B column
+// g (output colour g/2, part g&1) at colour t (one link word per hop,
 // rotated by a lane-dependent phase so that every B word is a fixed swap or
 // sign flip of it), and D rows g, g + 8 at output colour t: exactly the words
-// it loads and stores in the epilogue.  Nothing goes through shared memory.
+// it stores in the epilogue.
 //
-// A block of four warps takes 32 consecutive sites of one parity and one
-// block of systems, warp q the sites q, q + 4, ..., q + 28; blocks are
-// dispatched in site order with the systems' blocks fastest and live briefly,
-// so the sites in flight at one time are few and adjacent and their
-// neighbours meet in L2 (as in the CUDA-core kernel).  Lane i computes the
-// neighbour indices of the block's site i once; the loop broadcasts them.
-// Every load of a site (eight neighbours, eight links, the centre field) is
-// issued before any of its products, so that a warp has the whole site in
-// flight at once.  The block writes one partial sum per system and 32 sites
-// (FP32 per warp, then FP64 over the lanes and the warps in a fixed order),
-// in the per-warp layout of the CUDA-core kernel.  A system's result depends only on
-// its own MMA row: rows do not mix in the products, and the per-lane sums run
-// in a fixed order, whatever the other systems of the block are.
+// A block of four warps takes 64 consecutive sites of one parity and one
+// block of systems, warp q the sites q, q + 4, ..., q + 60; blocks are
+// dispatched in site order with the systems' blocks fastest, so the sites in
+// flight at one time are few and adjacent and their neighbours meet in L2.
+// Each warp stages every site's neighbours and links in shared memory with
+// bulk asynchronous copies (below), one site ahead of the one it computes.
+// The block writes one partial sum per system and 32 sites (FP32 per warp,
+// then FP64 over the lanes and the warps in a fixed order), in the per-warp
+// layout of the CUDA-core kernel.  A system's result depends only on its own
+// MMA row: rows do not mix in the products, and the per-lane sums run in a
+// fixed order, whatever the other systems of the block are.
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>

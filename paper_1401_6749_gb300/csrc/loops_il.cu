@@ -47,9 +47,15 @@
 
 namespace tml {
 
+// sites of one (slice, parity) per block (a tuning build may set TM_OD_CHUNK:
+// smaller blocks keep fewer sites in flight in L2, larger ones write fewer partial sums)
+#ifndef TM_OD_CHUNK
+#define TM_OD_CHUNK 512
+#endif
 constexpr int kOdWarps = 4;
-constexpr int kOdChunk = 512;                       // sites of one (slice, parity) per block
+constexpr int kOdChunk = TM_OD_CHUNK;
 constexpr int kOdWarpSites = kOdChunk / kOdWarps;   // sites per warp
+static_assert(kOdChunk % (32 * kOdWarps) == 0, "whole 32-site groups per warp");
 
 struct OdStage {
   static constexpr int kLinkOff = 10 * kIlSiteBytes;                 // ten sites, then U_mu(x)

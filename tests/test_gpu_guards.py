@@ -131,3 +131,30 @@ def test_solver_noise_and_contraction_guards():
     tl.loop_contract_oneD(op, x.view, x.view, tl.F16, n, tl.LOOP_VV, oned.as_f64())
     assert oned.intact()
     op.close()
+
+
+@pytest.mark.parametrize("n", [3, 17])
+def test_interleaved_solve_and_contraction_guards(n):
+    """tm_cg_solve_il's interleaved solution and the interleaved contractions'
+    loop arrays, on the ragged lattice (36 sites per slice and parity, not a
+    multiple of a warp's stride or a block's sites), with a partial second
+    block of 16 systems for n = 17."""
+    tl = require_gpu()
+    U = synth.gauge_field(LAT, seed=5)
+    op = tl.Operator(LAT, 0.16, 0.02, to_dev(U), recon=18)
+    T = LAT[3]
+    eta = tl.empty_field(LAT, tl.F16, n)
+    tl.z4_noise(LAT, eta, tl.F16, 11, 0, n)
+    x = Guarded(tl.tm_spinor_bytes_il(LAT, n))
+    for schur in (False, True):
+        tl.tm_cg_solve_il(op, x.view, eta, n, tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=tl.F16, schur=schur))
+        assert x.intact()
+    loc = Guarded(n * 16 * T * 2 * 8)
+    oned = Guarded(n * 64 * T * 2 * 8)
+    for g5 in (False, True):
+        tl.loop_contract_local_il(LAT, x.view, x.view, tl.F16, n, tl.LOOP_VV, loc.as_f64(), right_g5=g5)
+        assert loc.intact()
+        tl.loop_contract_oneD_il(op, x.view, x.view, tl.F16, n, tl.LOOP_VV, oned.as_f64(), right_g5=g5)
+        assert oned.intact()
+    tl.tm_op_check(op)
+    op.close()
