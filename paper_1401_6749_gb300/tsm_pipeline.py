@@ -32,12 +32,15 @@ class TsmPipeline:
     def __init__(self, op, n_hp, n_lp, batch=16, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2,
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
                  delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False,
-                 lp_layout=None, lp_graph=None, hp_ru_prec=None):
+                 lp_layout=None, lp_graph=None, hp_ru_prec=None, hp_first=False):
         """lp_layout: "il" keeps the LP solutions in the system-interleaved
         layout (tm_cg_solve_il), applies D_W there (tm_dslash_il) and contracts
         there (loop_contract_*_il, gamma_5 of the generalised estimator as
         right_g5); "std" uses the standard layout throughout.  Default: "il"
         for FP16/BF16 with 18-real 16-bit links (recon 18 or 0), else "std".
+        hp_first: without overlap, run the HP solves and loops before the LP
+        batches instead of after them (the sources are independent: every
+        per-source result is the same in either order).
         hp_ru_prec: arithmetic of the HP solves' true residuals (reliable
         updates), F64 (default) or FF.  FF is exact to about 2^-48 cond(M^dag M)
         relative to |b|: only for solves well enough conditioned that this
@@ -66,6 +69,7 @@ class TsmPipeline:
         self.seed, self.first = int(seed), int(first_src)
         self.max_iter, self.check_every, self.delta = max_iter, check_every, delta
         self.schur = bool(schur)
+        self.hp_first = bool(hp_first)
         if hp_loop_prec not in (tl.F64, tl.FF):
             raise ValueError("hp_loop_prec must be F64 or FF")
         self.hp_loop_prec = hp_loop_prec
@@ -235,6 +239,8 @@ class TsmPipeline:
         # that no masked-out iterations are launched past convergence
         lp_params = tl.cg_params(self.tol_lp, self.max_iter, tl.CG_PLAIN, prec=self.lp_prec,
                                  check_every=min(2, self.check_every), schur=self.schur, graph=self.lp_graph)
+        if self.n_hp and worker is None and self.hp_first:
+            self._run_hp(main)
         for b0 in range(0, n_all, self.batch):
             n = min(self.batch, n_all - b0)
             if self.lp_il:
@@ -246,7 +252,7 @@ class TsmPipeline:
         if worker is not None:
             worker.join()
             main.wait_stream(self.hp_stream)
-        elif self.n_hp:
+        elif self.n_hp and not self.hp_first:
             self._run_hp(main)
 
     def _combine_sets(self, k, hp, lphp, lp, n_hp, n_lp):

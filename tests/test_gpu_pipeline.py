@@ -3,7 +3,8 @@ and HP (mixed, 1e-10) even/odd solves, local and one-derivative loops in both
 one-end estimators, TSM combination.
 
 Checked: (1) running the HP solves on a second stream concurrently with the LP
-batches changes nothing (bit-identical per-source loops); (2) the HP loops
+batches, or before them instead of after, changes nothing (bit-identical
+per-source loops); (2) the HP loops
 agree with the oracle's (FP64 CG to 1e-12 and oracle contractions) within
 1e-8; (3) the combined estimate equals the oracle's TSM combination of the
 pipeline's own per-source loops; (4) every LP solve meets its truncation."""
@@ -37,16 +38,17 @@ def test_pipeline_overlap_and_parity():
     op = tl.Operator(L, kappa, mu, to_dev(U), recon=12)
     kw = dict(batch=4, lp_prec=tl.F16, hp_inner=tl.F32, tol_lp=1e-2, tol_hp=1e-10, seed=77, delta=1e-3)
     runs = []
-    for overlap in (False, True):
-        p = TsmPipeline(op, 3, 6, overlap=overlap, **kw)
+    for overlap, hp_first in ((False, False), (True, False), (False, True)):
+        p = TsmPipeline(op, 3, 6, overlap=overlap, hp_first=hp_first, **kw)
         res = p.run()
         torch.cuda.synchronize()
         runs.append((p, {k: (m.clone(), e.clone()) for k, (m, e) in res.items()}))
-    (p0, r0), (p1, r1) = runs
-    for k in p0.kinds:
-        np.testing.assert_array_equal(p0.lp_loops[k].cpu().numpy(), p1.lp_loops[k].cpu().numpy())
-        np.testing.assert_array_equal(p0.hp_loops[k].cpu().numpy(), p1.hp_loops[k].cpu().numpy())
-        np.testing.assert_array_equal(r0[k][0].cpu().numpy(), r1[k][0].cpu().numpy())
+    (p0, r0) = runs[0]
+    for p1, r1 in runs[1:]:
+        for k in p0.kinds:
+            np.testing.assert_array_equal(p0.lp_loops[k].cpu().numpy(), p1.lp_loops[k].cpu().numpy())
+            np.testing.assert_array_equal(p0.hp_loops[k].cpu().numpy(), p1.hp_loops[k].cpu().numpy())
+            np.testing.assert_array_equal(r0[k][0].cpu().numpy(), r1[k][0].cpu().numpy())
     assert all(s["status"] == 0 and s["rel_res"] <= 1e-2 for s in p0.stats_lp)
     assert all(s["status"] == 0 for s in p0.stats_hp)
     # HP loops vs the oracle
