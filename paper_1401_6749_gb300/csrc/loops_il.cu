@@ -60,12 +60,16 @@ static_assert(kOdChunk % (32 * kOdWarps) == 0, "whole 32-site groups per warp");
 struct OdStage {
   static constexpr int kLinkOff = 10 * kIlSiteBytes;                 // ten sites, then U_mu(x)
   static constexpr int kBwdOff = kLinkOff + kIlLinkSiteBytes;        // U_mu(x - mu), mu < 3
-  static constexpr int kBytes = kBwdOff + 3 * kIlLinkBytes;          // 8016
+  static constexpr int kCopyBytes = kBwdOff + 3 * kIlLinkBytes;      // 8016 bytes copied per site
+  // stages start on 128-byte lines, so that every stage has the bank
+  // alignment of the zero block's line
+  static constexpr int kBytes = (kCopyBytes + 127) / 128 * 128;       // 8064
   static constexpr int kStages = 2;
   static constexpr int kWarpBytes = kStages * kBytes;
-  // zero words for the lanes without a product word: 48 bytes into the
-  // block, so that system s's zero word sits in bank 12 s + 12, which no
-  // product word read by the same instruction occupies
+  // zero words for the lanes without a product word: 48 bytes into a line,
+  // so that system s's zero word sits in bank 12 s + 12 (mod 32) of the
+  // stage's alignment, which no product word read by the same instruction
+  // occupies
   static constexpr int kZeroOff = kOdWarps * kWarpBytes + 48;
   static constexpr int kSmem = kZeroOff + kIlSiteBytes;
   // stage slots: 2 mu / 2 mu + 1 = R(x + mu) / R(x - mu) (mu < 3), 6 R(x + t),
@@ -78,7 +82,7 @@ struct OdStage {
                                                                                                  : 7 * kIlSiteBytes;
   }
 };
-static_assert(OdStage::kBytes % 16 == 0, "bulk copies need 16-byte aligned stages");
+static_assert(OdStage::kBytes % 128 == 0 && OdStage::kWarpBytes % 128 == 0, "stages on 128-byte lines");
 static_assert(OdStage::w(1) + kIlSiteBytes <= 4 * kIlSiteBytes && OdStage::w(2) + kIlSiteBytes <= 6 * kIlSiteBytes,
               "product classes inside their slots");
 
@@ -163,7 +167,8 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
       rdoff = ST::kBwdOff + rmu * kIlLinkBytes;
       rbytes = kIlLinkBytes;
     }
-    constexpr unsigned total = 10 * kIlSiteBytes + kIlLinkSiteBytes + 3 * kIlLinkBytes;
+    constexpr unsigned total = ST::kCopyBytes;
+    static_assert(ST::kCopyBytes == 10 * kIlSiteBytes + kIlLinkSiteBytes + 3 * kIlLinkBytes, "copy roles");
     unsigned char* ring = od_smem + wq * ST::kWarpBytes;
     const unsigned ring_s = smem_u32(ring);
     const unsigned bar0 = smem_u32(&bars[wq][0]);
