@@ -95,8 +95,11 @@ typedef struct {
 typedef struct tm_op tm_op_t;
 
 /* Create an operator: validates p, copies the FP64 canonical gauge field
- * U_lex (device, [4][V][3][3][2] doubles, not retained) into internal
- * even/odd link arrays for every precision.  Blocks until done.            */
+ * U_lex ([4][V][3][3][2] doubles, not retained) into internal even/odd link
+ * arrays for every precision.  U_lex is device memory, or page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister, 16-byte aligned) that the GPU reads
+ * in one pass of its SMs over the host link into a staging buffer; other host
+ * memory is TM_ERR_ARG.  Blocks until done.                               */
 tm_status_t tm_op_create(tm_op_t **op, const tm_params_t *p, const double *U_lex, tm_stream_t s);
 tm_status_t tm_op_destroy(tm_op_t *op);
 /* A second handle on the same operator: shares the source's link arrays (no

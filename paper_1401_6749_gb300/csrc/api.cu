@@ -412,6 +412,55 @@ extern "C" tm_status_t tm_trace_read_flops(const char* name, double* total_flops
   return trace_sum(name, &n, &ms, &bytes, total_flops);
 }
 
+namespace tml {
+// One pass of the SMs over page-locked host memory into device memory (16-byte
+// words, grid-stride).  Right after sustained GPU load the copy engine's first
+// host-to-device transfer runs several times slower than these reads.
+__global__ void pull_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+}  // namespace tml
+
+// U_lex in page-locked host memory: pull it into a staging buffer of the pool
+// (*staged, freed by the caller in stream order) and point *U at it; device
+// memory passes through; other memory is an argument error.
+static tm_status_t stage_links(const double* U_lex, size_t bytes, const double** U, double** staged,
+                               cudaStream_t st) {
+  *U = U_lex;
+  *staged = nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, U_lex) != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return TM_OK;
+  if (at.type != cudaMemoryTypeHost) {
+    set_error("tm_op_create: U_lex must be device memory or page-locked host memory");
+    return TM_ERR_ARG;
+  }
+  const void* src = at.devicePointer ? at.devicePointer : U_lex;
+  if (reinterpret_cast<uintptr_t>(src) & 15u) {
+    set_error("tm_op_create: page-locked host U_lex must be 16-byte aligned");
+    return TM_ERR_ARG;
+  }
+  TM_TRY(dev_alloc((void**)staged, bytes, st, "tm_op_create"));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+  pull_kernel<<<(unsigned)nsm * 8u, 256, 0, st>>>(static_cast<const uint4*>(src), reinterpret_cast<uint4*>(*staged),
+                                                  bytes / 16);
+  count_launch();
+  const tm_status_t r = check_launch("tm_op_create: host links");
+  if (r != TM_OK) {
+    dev_free(*staged, st);
+    *staged = nullptr;
+    return r;
+  }
+  *U = *staged;
+  return TM_OK;
+}
+
 extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const double* U_lex,
                                     tm_stream_t s) {
   if (!out || !p || !U_lex) { set_error("tm_op_create: null argument"); return TM_ERR_ARG; }
@@ -443,28 +492,36 @@ extern "C" tm_status_t tm_op_create(tm_op_t** out, const tm_params_t* p, const d
   for (int i = 0; i < kNumPrec; ++i) op->links[i] = op->links_il[i] = nullptr;
   op->il_err = nullptr;
   const cudaStream_t st = (cudaStream_t)s;
+  const double* U = nullptr;
+  double* staged = nullptr;
+  {
+    const size_t ubytes = 4 * 2 * (size_t)op->g.Vh * 18 * sizeof(double);
+    const tm_status_t ss = stage_links(U_lex, ubytes, &U, &staged, st);
+    if (ss != TM_OK) { tm_op_destroy(op); return ss; }
+  }
   for (int i = 0; i < kNumPrec; ++i) {
     const tm_prec_t pr = (tm_prec_t)i;
     const size_t nb = link_bytes(op->g, pr, op->recon_p[i]);
     const tm_status_t sa = dev_alloc(&op->links[i], nb, st, "tm_op_create");
-    if (sa != TM_OK) { tm_op_destroy(op); return sa; }
-    const tm_status_t st2 = pack_links(op->g, pr, op->recon_p[i], op->links[i], U_lex, st);
-    if (st2 != TM_OK) { tm_op_destroy(op); return st2; }
+    if (sa != TM_OK) { dev_free(staged, st); tm_op_destroy(op); return sa; }
+    const tm_status_t st2 = pack_links(op->g, pr, op->recon_p[i], op->links[i], U, st);
+    if (st2 != TM_OK) { dev_free(staged, st); tm_op_destroy(op); return st2; }
     // the interleaved (tensor-core) Dslash reads the 16-bit links site-major
     if ((pr == TM_PREC_F16 || pr == TM_PREC_BF16) && op->recon_p[i] == 18) {
       tm_status_t s3 = dev_alloc(&op->links_il[i], il_link_bytes(op->g), st, "tm_op_create");
       if (s3 == TM_OK) s3 = il_pack_links(op->g, op->links_il[i], op->links[i], st);
-      if (s3 != TM_OK) { tm_op_destroy(op); return s3; }
+      if (s3 != TM_OK) { dev_free(staged, st); tm_op_destroy(op); return s3; }
       if (!op->il_err) {
         s3 = dev_alloc((void**)&op->il_err, sizeof(int), st, "tm_op_create");
         if (s3 == TM_OK && cudaMemsetAsync(op->il_err, 0, sizeof(int), st) != cudaSuccess) {
           set_error("tm_op_create: %s", cudaGetErrorString(cudaGetLastError()));
           s3 = TM_ERR_CUDA;
         }
-        if (s3 != TM_OK) { tm_op_destroy(op); return s3; }
+        if (s3 != TM_OK) { dev_free(staged, st); tm_op_destroy(op); return s3; }
       }
     }
   }
+  dev_free(staged, st);  // stream-ordered: after the packing that reads it
   if (op->il_err) {
     tm_status_t s4 = il_prepare();
     if (s4 == TM_OK) s4 = oned_il_prepare();

@@ -164,7 +164,9 @@ def link_reals(recon, prec):
 
 
 class Operator:
-    """Owner of a tm_op_t handle (gauge links in every precision)."""
+    """Owner of a tm_op_t handle (gauge links in every precision).  U: the FP64
+    lexicographic gauge field as a CUDA tensor or a pinned CPU tensor (read by
+    the GPU directly)."""
 
     def __init__(self, L, kappa, mu, U, antiperiodic=True, recon=12, stream=None):
         self.L = tuple(int(v) for v in L)

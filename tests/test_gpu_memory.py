@@ -41,3 +41,32 @@ def test_pool_reuses_memory_across_operators_and_trims():
     assert it1 == it2 and torch.equal(out1, out2)
     tl.tm_mem_trim(0)
     assert tl.tm_mem_reserved() == r0
+
+
+def test_operator_from_pinned_host_field():
+    """tm_op_create reads a page-locked host gauge field itself: the operator
+    is bit-identical to one made from the same field in device memory, and
+    pageable host memory is an argument error."""
+    import numpy as np
+    from paper_1401_6749_gb300 import synth
+    tl = require_gpu()
+    L = (8, 8, 4, 8)
+    U = synth.gauge_field(L, seed=17)
+    host = torch.from_numpy(U.view(np.float64).copy())
+    ops = [tl.Operator(L, 0.16, 0.01, host.cuda(), recon=0), tl.Operator(L, 0.16, 0.01, host.pin_memory(), recon=0)]
+    outs = []
+    for op in ops:
+        for prec in (tl.F64, tl.F32, tl.F16):
+            f = tl.empty_field(L, prec, 2)
+            tl.z4_noise(L, f, prec, 3, 0, 2)
+            o = tl.empty_field(L, prec, 2)
+            tl.tm_dslash(op, o, f, 2, prec=prec)
+            outs.append(o)
+    torch.cuda.synchronize()
+    for a, b in zip(outs[:3], outs[3:]):
+        assert torch.equal(a, b)
+    with pytest.raises(tl.TmError) as e:
+        tl.Operator(L, 0.16, 0.01, host, recon=0)     # pageable host memory
+    assert e.value.status == 1
+    for op in ops:
+        op.close()
