@@ -201,6 +201,14 @@ tm_status_t z4_noise(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t see
 tm_status_t z4_noise_diluted(const tm_geom_t *g, void *eta, tm_prec_t prec, uint64_t seed,
                              uint32_t first_src, int nsrc, int t0, int dt, tm_stream_t s);
 
+/* z4_noise written straight into the interleaved 16-bit layout (the same
+ * bits as z4_noise followed by tm_spinor_to_il): source r = first_src + j
+ * is system j of eta_il (tm_spinor_bytes_il(g, nsrc) bytes, 4-byte aligned);
+ * the slots of systems >= nsrc in the last block of 16 are written as zero.
+ * prec F16 or BF16, else TM_ERR_ARG.                                       */
+tm_status_t z4_noise_il(const tm_geom_t *g, void *eta_il, tm_prec_t prec, uint64_t seed,
+                        uint32_t first_src, int nsrc, tm_stream_t s);
+
 /* Hopping Parameter Expansion (Sec. 2.4, Eqs. 7-8).  With B = (1 + i nu g5)^-1
  * and H = M - B^-1 (-kappa times the hops of M),
  *   M^-1 = B - B H B + (BH)^2 B - (BH)^3 B + (BH)^4 M^-1.
@@ -278,12 +286,14 @@ typedef struct {
 tm_status_t tm_cg_solve(tm_op_t *op, void *x, const void *eta, int nrhs,
                         const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
 
-/* tm_cg_solve with the solution left in the interleaved layout: x_il (16-byte
- * aligned, tm_spinor_bytes_il(g, nrhs) bytes) receives the solution that
- * tm_cg_solve would convert into x (the same bits), eta as for tm_cg_solve.
- * Only for the solves that run on the interleaved layout (plain F16/BF16,
- * 18-real links, tm_cg_il_enable on): TM_ERR_UNSUPPORTED otherwise.        */
-tm_status_t tm_cg_solve_il(tm_op_t *op, void *x_il, const void *eta, int nrhs,
+/* tm_cg_solve on fields in the interleaved layout: eta_il and x_il (each
+ * 16-byte aligned, tm_spinor_bytes_il(g, nrhs) bytes, not overlapping) hold
+ * the sources and receive the solutions.  The solution bits equal those that
+ * tm_cg_solve, given the same sources in the standard layout, converts into
+ * x.  Only for the solves that run on the interleaved layout (plain
+ * F16/BF16, 18-real links, tm_cg_il_enable on): TM_ERR_UNSUPPORTED
+ * otherwise.                                                               */
+tm_status_t tm_cg_solve_il(tm_op_t *op, void *x_il, const void *eta_il, int nrhs,
                            const tm_cg_params_t *p, tm_cg_stats_t *stats, tm_stream_t s);
 
 /* Several independent batched solves advanced together (an uneven batch:

@@ -332,7 +332,7 @@ struct CgRun {
   // Dslash): eta is converted into eta_il at set-up, x_il back into x at the end
   bool il = false;
   void *eta_il = nullptr, *x_il = nullptr;
-  bool x_is_il = false;  // the caller's x is in the interleaved layout (tm_cg_solve_il)
+  bool x_is_il = false;  // the caller's x and eta are in the interleaved layout (tm_cg_solve_il)
   tm_prec_t lo = TM_PREC_F64, hi = TM_PREC_F64;
   int par0 = 0, npar = 2, nwarp = 0;
   void *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *y = nullptr;
@@ -412,7 +412,10 @@ tm_status_t CgRun::setup() {
       y = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
     } else {
       b = c.take(F); r = c.take(F); p = c.take(F); t = c.take(F);
-      if (il) { eta_il = c.take(F); x_il = x_is_il ? x : c.take(F); }
+      if (il) {
+        eta_il = x_is_il ? const_cast<void*>(eta) : c.take(F);
+        x_il = x_is_il ? x : c.take(F);
+      }
     }
     partial = (double*)c.take(P);
     st.bb = (double*)c.take(sizeof(double) * nrhs);
@@ -445,7 +448,7 @@ tm_status_t CgRun::setup() {
   scratch_hi = mixed ? tmp64 : t;
   const SolveOp Op = A();
 
-  if (il) TM_TRY(il_convert(g, eta_il, eta, nrhs, true, s));
+  if (il && !x_is_il) TM_TRY(il_convert(g, eta_il, eta, nrhs, true, s));
   const void* eta_in = il ? eta_il : eta;
   // b = Op^dag eta (Schur: Op^dag eta_hat), |b|^2
   {
@@ -846,11 +849,14 @@ extern "C" tm_status_t tm_cg_solve(tm_op_t* op, void* x, const void* eta, int nr
   return report(worst);
 }
 
-extern "C" tm_status_t tm_cg_solve_il(tm_op_t* op, void* x_il, const void* eta, int nrhs,
+extern "C" tm_status_t tm_cg_solve_il(tm_op_t* op, void* x_il, const void* eta_il, int nrhs,
                                       const tm_cg_params_t* prm, tm_cg_stats_t* stats, tm_stream_t strm) {
-  if (!op || !x_il || !eta || !prm || nrhs < 0) { set_error("tm_cg_solve_il: null argument"); return TM_ERR_ARG; }
-  if (x_il == eta) { set_error("tm_cg_solve_il: x and eta must not overlap"); return TM_ERR_ARG; }
-  if (reinterpret_cast<uintptr_t>(x_il) & 15u) { set_error("tm_cg_solve_il: x must be 16-byte aligned"); return TM_ERR_ARG; }
+  if (!op || !x_il || !eta_il || !prm || nrhs < 0) { set_error("tm_cg_solve_il: null argument"); return TM_ERR_ARG; }
+  if (x_il == eta_il) { set_error("tm_cg_solve_il: x and eta must not overlap"); return TM_ERR_ARG; }
+  if ((reinterpret_cast<uintptr_t>(x_il) | reinterpret_cast<uintptr_t>(eta_il)) & 15u) {
+    set_error("tm_cg_solve_il: x and eta must be 16-byte aligned");
+    return TM_ERR_ARG;
+  }
   TM_TRY(check_params(prm));
   const tm_prec_t lo = prm->prec;
   if (prm->mode != TM_CG_PLAIN || (lo != TM_PREC_F16 && lo != TM_PREC_BF16) || op->recon_p[lo] != 18 || !cg_il_on()) {
@@ -859,7 +865,7 @@ extern "C" tm_status_t tm_cg_solve_il(tm_op_t* op, void* x_il, const void* eta, 
   }
   if (nrhs == 0) return TM_OK;
   std::vector<CgRun> runs(1);
-  runs[0].op = op; runs[0].x = x_il; runs[0].eta = eta; runs[0].nrhs = nrhs;
+  runs[0].op = op; runs[0].x = x_il; runs[0].eta = eta_il; runs[0].nrhs = nrhs;
   runs[0].prm = *prm; runs[0].stats = stats; runs[0].x_is_il = true;
   tm_status_t worst = TM_OK;
   TM_TRY(solve_group(runs, prm, (cudaStream_t)strm, &worst));

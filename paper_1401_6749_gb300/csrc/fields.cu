@@ -186,6 +186,34 @@ __global__ void z4_kernel(Geom g, void* eta, uint2 key, uint32_t first, int t0, 
   store_spinor<S>(eta, SpinorRef<S>::base(g, j, par, cb), (size_t)g.Vh, v);
 }
 
+// The same noise written straight into the system-interleaved 16-bit layout
+// ([block][parity][cb][k][slot], systems j and j + 8 on pair position j of
+// rows k = 0, 1 (mod 3) and j ^ 4 of rows k = 2 (mod 3)).  One thread per
+// (site, system of the block): a warp covers two sites, and each of its 12
+// stores fills two 64-byte rows.  Systems >= nsrc are written as zero.  The
+// entries are bit patterns of the format's +-1 (one = 0x3C00 FP16, 0x3F80
+// BF16; sign bit 0x8000), re in the low half-word.
+__global__ void __launch_bounds__(256) z4_il_kernel(Geom g, unsigned* __restrict__ eta, uint2 key,
+                                                    uint32_t first, int nsrc, unsigned one) {
+  const int par = blockIdx.y, blk = blockIdx.z;
+  const int j = threadIdx.x & 15;
+  const int cb = blockIdx.x * 16 + (threadIdx.x >> 4);
+  if (cb >= g.Vh) return;
+  const int r = blk * 16 + j;
+  const Site st = site_of(g, par, cb);
+  const uint32_t w = r < nsrc ? philox4x32_10(make_uint4((uint32_t)st.lex, first + (uint32_t)r, 0u, 0u), key).x
+                              : 0u;
+  const unsigned neg = one | 0x8000u;
+  unsigned* o = eta + (((size_t)blk * 2 + par) * (size_t)g.Vh + (size_t)cb) * 192;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const unsigned q = (w >> (2 * k)) & 3u;
+    const unsigned v = r >= nsrc ? 0u : q == 0 ? one : q == 1 ? one << 16 : q == 2 ? neg : neg << 16;
+    const int slot = 2 * ((j & 7) ^ (k % 3 == 2 ? 4 : 0)) + (j >> 3);
+    o[16 * k + slot] = v;
+  }
+}
+
 // ------------------------------------------------------------ gauge packing
 template <class S>
 __device__ __forceinline__ S from_f64(double v) {
@@ -535,6 +563,28 @@ extern "C" tm_status_t z4_noise_diluted(const tm_geom_t* gg, void* eta, tm_prec_
     return TM_ERR_ARG;
   }
   return z4_launch(gg, eta, prec, seed, first_src, nsrc, t0, dt, s);
+}
+
+extern "C" tm_status_t z4_noise_il(const tm_geom_t* gg, void* eta_il, tm_prec_t prec, uint64_t seed,
+                                   uint32_t first_src, int nsrc, tm_stream_t s) {
+  if (!gg || !eta_il || nsrc < 0) { set_error("z4_noise_il: null argument"); return TM_ERR_ARG; }
+  if (prec != TM_PREC_F16 && prec != TM_PREC_BF16) {
+    set_error("z4_noise_il: the interleaved layout holds F16 or BF16 fields");
+    return TM_ERR_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(eta_il) & 3u) { set_error("z4_noise_il: eta_il must be 4-byte aligned"); return TM_ERR_ARG; }
+  if (check_geom(gg->L) != TM_OK) return TM_ERR_ARG;
+  if (nsrc == 0) return TM_OK;
+  const int nblk = (nsrc + 15) / 16;
+  if (nblk > 65535) { set_error("z4_noise_il: too many sources (%d)", nsrc); return TM_ERR_ARG; }
+  const Geom g = make_geom(gg->L, 1);
+  const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  TraceScope tr((cudaStream_t)s, "z4_noise", 16.0 * 48.0 * 2.0 * g.Vh, 0.0, nblk);
+  const dim3 grid((unsigned)((g.Vh + 15) / 16), 2, (unsigned)nblk);
+  z4_il_kernel<<<grid, 256, 0, (cudaStream_t)s>>>(g, static_cast<unsigned*>(eta_il), key, first_src, nsrc,
+                                                  prec == TM_PREC_F16 ? 0x3C00u : 0x3F80u);
+  count_launch();
+  return check_launch("z4_noise_il");
 }
 
 static tm_status_t z4_launch(const tm_geom_t* gg, void* eta, tm_prec_t prec, uint64_t seed,

@@ -82,6 +82,7 @@ _SIGS = {
     "loop_contract_local_noalloc": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _vp],
     "tsm_combine": [_vp, _vp, _i, _vp, _i, _sz, _d, _d, _vp, _vp, _vp],
     "z4_noise_diluted": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _i, _i, _vp],
+    "z4_noise_il": [_P(tm_geom_t), _vp, _i, _u64, _u32, _i, _vp],
     "tm_hpe_apply": [_vp, _vp, _vp, _i, _i, _i, _vp],
     "tm_hpe_exact": [_P(tm_params_t), _vp],
     "loop_contract_local_mom": [_P(tm_geom_t), _vp, _vp, _i, _i, _i, _vp, _i, _vp, _vp],
@@ -254,6 +255,12 @@ def empty_field_il(L, nrhs, device="cuda"):
     return torch.empty(tm_spinor_bytes_il(L, nrhs), dtype=torch.uint8, device=device)
 
 
+def z4_noise_il(L, eta_il, prec, seed, first_src, nsrc, stream=None):
+    """z4_noise written straight into the interleaved layout (F16 or BF16)."""
+    _check(_lib.z4_noise_il(ctypes.byref(geom(L)), _ptr(eta_il), int(prec), int(seed), int(first_src),
+                            int(nsrc), _stream(stream)))
+
+
 def tm_spinor_to_il(L, out_il, inp, prec, nrhs, stream=None):
     _check(_lib.tm_spinor_to_il(ctypes.byref(geom(L)), _ptr(out_il), _ptr(inp), int(prec), int(nrhs),
                                 _stream(stream)))
@@ -315,11 +322,11 @@ def tm_cg_solve(op, x, eta, nrhs, params, stream=None, raise_on_noconv=True):
     return st, out
 
 
-def tm_cg_solve_il(op, x_il, eta, nrhs, params, stream=None, raise_on_noconv=True):
-    """tm_cg_solve with the solution left in the interleaved layout (x_il from
-    empty_field_il); the same return values."""
+def tm_cg_solve_il(op, x_il, eta_il, nrhs, params, stream=None, raise_on_noconv=True):
+    """tm_cg_solve with sources and solutions in the interleaved layout (both
+    from empty_field_il); the same return values."""
     stats = (tm_cg_stats_t * max(int(nrhs), 1))()
-    st = _lib.tm_cg_solve_il(op.handle, _ptr(x_il), _ptr(eta), int(nrhs), ctypes.byref(params), stats,
+    st = _lib.tm_cg_solve_il(op.handle, _ptr(x_il), _ptr(eta_il), int(nrhs), ctypes.byref(params), stats,
                              _stream(stream))
     out = [dict(iters=s.iters, reliable_updates=s.reliable_updates, status=s.status,
                 rel_res=s.rel_res, true_res=s.true_res) for s in list(stats)[:int(nrhs)]]

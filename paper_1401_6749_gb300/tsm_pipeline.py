@@ -33,8 +33,9 @@ class TsmPipeline:
                  tol_hp=1e-9, seed=20140126, first_src=0, max_iter=20000, check_every=4,
                  delta=0.1, kinds=KINDS, schur=True, overlap=False, hp_loop_prec=tl.F64, timing=False,
                  lp_layout=None, lp_graph=None, hp_ru_prec=None, hp_first=False):
-        """lp_layout: "il" keeps the LP solutions in the system-interleaved
-        layout (tm_cg_solve_il), applies D_W there (tm_dslash_il) and contracts
+        """lp_layout: "il" draws the LP sources straight into the
+        system-interleaved layout (z4_noise_il), solves there (tm_cg_solve_il),
+        applies D_W there (tm_dslash_il) and contracts
         there (loop_contract_*_il, gamma_5 of the generalised estimator as
         right_g5); "std" uses the standard layout throughout.  Default: "il"
         for FP16/BF16 with 18-real 16-bit links (recon 18 or 0), else "std".
@@ -96,9 +97,7 @@ class TsmPipeline:
                                         dtype=torch.float64, device=dev) for k in self.kinds}
         b = min(self.batch, n_all)
         if self.lp_il:
-            # eta (standard layout, from the noise generator); x, D_W x and, for
-            # the standard estimator, eta in the interleaved layout
-            self._lp = [tl.empty_field(self.L, lp_prec, b)] + [tl.empty_field_il(self.L, b) for _ in range(3)]
+            self._lp = [tl.empty_field_il(self.L, b) for _ in range(3)]  # eta, x, D_W x (interleaved)
         else:
             self._lp = [tl.empty_field(self.L, lp_prec, b) for _ in range(3)]  # eta, x, g5 D_W x
         nh = max(min(self.batch, self.n_hp), 1)
@@ -150,12 +149,10 @@ class TsmPipeline:
 
     def _solve_and_contract_il(self, op, fields, prec, first, n, params, dst, row0, stream=None):
         """An LP batch on the interleaved layout: solve, D_W, contractions."""
-        eta, x, dw, eta_il = fields
+        eta_il, x, dw = fields
         ev = [self._event(stream)] if self.timing else None
-        tl.z4_noise(self.L, eta, prec, self.seed, first, n, stream)
-        st, stats = tl.tm_cg_solve_il(op, x, eta, n, params, stream, raise_on_noconv=False)
-        if any(k.endswith("std") for k in self.kinds):
-            tl.tm_spinor_to_il(self.L, eta_il, eta, prec, n, stream)
+        tl.z4_noise_il(self.L, eta_il, prec, self.seed, first, n, stream)
+        st, stats = tl.tm_cg_solve_il(op, x, eta_il, n, params, stream, raise_on_noconv=False)
         if ev:
             ev.append(self._event(stream))
         if any("gen" in k for k in self.kinds):

@@ -135,20 +135,21 @@ def test_solver_noise_and_contraction_guards():
 
 @pytest.mark.parametrize("n", [3, 17])
 def test_interleaved_solve_and_contraction_guards(n):
-    """tm_cg_solve_il's interleaved solution and the interleaved contractions'
-    loop arrays, on the ragged lattice (36 sites per slice and parity, not a
-    multiple of a warp's stride or a block's sites), with a partial second
-    block of 16 systems for n = 17."""
+    """z4_noise_il's sources, tm_cg_solve_il's interleaved solution and the
+    interleaved contractions' loop arrays, on the ragged lattice (36 sites per
+    slice and parity, not a multiple of a warp's stride or a block's sites),
+    with a partial second block of 16 systems for n = 17."""
     tl = require_gpu()
     U = synth.gauge_field(LAT, seed=5)
     op = tl.Operator(LAT, 0.16, 0.02, to_dev(U), recon=18)
     T = LAT[3]
-    eta = tl.empty_field(LAT, tl.F16, n)
-    tl.z4_noise(LAT, eta, tl.F16, 11, 0, n)
+    eta = Guarded(tl.tm_spinor_bytes_il(LAT, n))
+    tl.z4_noise_il(LAT, eta.view, tl.F16, 11, 0, n)
+    assert eta.intact()
     x = Guarded(tl.tm_spinor_bytes_il(LAT, n))
     for schur in (False, True):
-        tl.tm_cg_solve_il(op, x.view, eta, n, tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=tl.F16, schur=schur))
-        assert x.intact()
+        tl.tm_cg_solve_il(op, x.view, eta.view, n, tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=tl.F16, schur=schur))
+        assert x.intact() and eta.intact()
     loc = Guarded(n * 16 * T * 2 * 8)
     oned = Guarded(n * 64 * T * 2 * 8)
     for g5 in (False, True):

@@ -168,9 +168,54 @@ def test_il_contraction_arguments():
     op12.close()
 
 
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 6, 2, 6), (18, 12, 6, 4)])
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("n,first", [(1, 0), (16, 5), (17, 40), (35, 3)])
+def test_z4_noise_il_is_the_converted_noise(L, prec, n, first):
+    """z4_noise_il writes the oracle's Z4 noise (Sec. 2; +-1, +-i are exact
+    in every format) in the interleaved layout: read back, every entry equals
+    the oracle's; the bytes, including the zero slots of the systems past n
+    in the last block of 16, are those of z4_noise followed by
+    tm_spinor_to_il."""
+    tl = require_gpu()
+    seed = 0x1234_5678_9ABC                            # both key words non-zero
+    got = tl.empty_field_il(L, n)
+    got.fill_(0xA5)
+    tl.z4_noise_il(L, got, prec, seed, first, n)
+    std = tl.empty_field(L, prec, n)
+    tl.tm_spinor_from_il(L, std, got, prec, n)
+    assert np.array_equal(unpack(tl, L, std, prec, n), oz4(L, seed, first, n))
+    tl.z4_noise(L, std, prec, seed, first, n)
+    ref = tl.empty_field_il(L, n)
+    ref.fill_(0x5A)
+    tl.tm_spinor_to_il(L, ref, std, prec, n)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, got)
+
+
+def test_z4_noise_il_arguments():
+    tl = require_gpu()
+    L = (4, 4, 4, 4)
+    f = tl.empty_field_il(L, 2)
+    with pytest.raises(tl.TmError) as e:
+        tl.z4_noise_il(L, f, tl.F32, 1, 0, 2)          # FP32 is not an interleaved format
+    assert e.value.status == 1
+    with pytest.raises(tl.TmError) as e:
+        tl.z4_noise_il(L, f[2:], tl.F16, 1, 0, 2)      # misaligned field
+    assert e.value.status == 1
+    with pytest.raises(tl.TmError) as e:
+        tl.z4_noise_il((3, 4, 4, 4), f, tl.F16, 1, 0, 2)   # odd extent
+    assert e.value.status == 1
+    before = f.clone()
+    tl.z4_noise_il(L, f, tl.F16, 1, 0, 0)              # zero sources: no-op
+    torch.cuda.synchronize()
+    assert torch.equal(before, f)
+
+
 @pytest.mark.parametrize("schur", [True, False])
 def test_cg_solve_il_is_the_converted_solution(schur):
-    """tm_cg_solve_il leaves exactly the bits that tm_cg_solve converts back."""
+    """tm_cg_solve_il on the interleaved sources leaves exactly the bits that
+    tm_cg_solve, on the same sources in the standard layout, converts back."""
     tl = require_gpu()
     L = (6, 4, 4, 8)
     U = synth.gauge_field(L, seed=91)
@@ -180,16 +225,21 @@ def test_cg_solve_il_is_the_converted_solution(schur):
     prm = tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=tl.F16, check_every=2, schur=schur)
     x = tl.empty_field(L, tl.F16, n)
     _, s1 = tl.tm_cg_solve(op, x, eta, n, prm)
+    eta_il = tl.empty_field_il(L, n)
+    tl.z4_noise_il(L, eta_il, tl.F16, 7, 0, n)
     x_il = tl.empty_field_il(L, n)
-    _, s2 = tl.tm_cg_solve_il(op, x_il, eta, n, prm)
+    _, s2 = tl.tm_cg_solve_il(op, x_il, eta_il, n, prm)
     assert [a["iters"] for a in s1] == [b["iters"] for b in s2]
     ref = tl.empty_field_il(L, n)
     tl.tm_spinor_to_il(L, ref, x, tl.F16, n)
     torch.cuda.synchronize()
     assert torch.equal(ref, x_il)
     with pytest.raises(tl.TmError) as e:               # a mixed solve has no interleaved form
-        tl.tm_cg_solve_il(op, x_il, eta, n, tl.cg_params(1e-6, 100, tl.CG_MIXED, inner_prec=tl.F32))
+        tl.tm_cg_solve_il(op, x_il, eta_il, n, tl.cg_params(1e-6, 100, tl.CG_MIXED, inner_prec=tl.F32))
     assert e.value.status == 6
+    with pytest.raises(tl.TmError) as e:               # misaligned source
+        tl.tm_cg_solve_il(op, x_il, eta_il[4:], n, prm)
+    assert e.value.status == 1
     op.close()
 
 
