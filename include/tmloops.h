@@ -166,7 +166,7 @@ tm_status_t tm_dslash_g5(tm_op_t *op, void *out, const void *in, int nrhs, int d
  *   else TM_ERR_ARG).  Needs the 18-real 16-bit link copy (recon 18 or 0:
  *   TM_ERR_UNSUPPORTED for 12).  Results agree with tm_dslash to the 16-bit
  *   tolerance; the bits differ (summation order).  A staging wait that never
- *   completes gives up after a bounded number of rounds and sets a flag of
+ *   completes gives up after about one second and sets a flag of
  *   the operator: tm_op_check(op) waits for the device and returns
  *   TM_ERR_TIMEOUT (clearing the flag) if that happened, tm_cg_solve returns
  *   TM_ERR_TIMEOUT at its next poll.

@@ -139,6 +139,7 @@ constexpr int kIlSiteBytes = 768;
 constexpr int kIlLinkBytes = 48;                 // one direction of one site: 9 words + 3 pad
 constexpr int kIlLinkSiteBytes = 4 * kIlLinkBytes;
 constexpr unsigned kIlWaitLimit = 1u << 22;      // try_wait rounds before a wait gives up
+constexpr unsigned long long kIlWaitNs = 1000000000ull;  // global time before a wait gives up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -159,15 +160,25 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// bounded wait for a stage; false (and the launch's error flag set) if it gave up
+// bounded wait for a stage; false (and the launch's error flag set) if it
+// gave up, after kIlWaitNs of global time or kIlWaitLimit rounds
 __device__ __forceinline__ bool il_wait(unsigned bar, unsigned phase, int* err) {
-  for (unsigned it = 0; it < kIlWaitLimit; ++it)
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < kIlWaitLimit; ++it) {
     if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > kIlWaitNs) break;
+  }
   if (err) atomicExch(err, 1);
   return false;
 }
