@@ -94,8 +94,9 @@ struct IlArgs {
 struct IlLane {
   int gq, tq;
   bool ld;         // lane loads spinor words (colour t < 3)
-  bool lw;         // lane holds a link entry (t < 3, output colour g/2 < 3)
-  unsigned psel;   // lane phase of the link words: swap halves on odd columns
+  // lane phase of the link words: swap halves on odd columns; lanes t = 3
+  // (B rows of colour 3) select zero bytes
+  unsigned psel;
   unsigned pmf, pmb;
 };
 
@@ -282,9 +283,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       rbytes = kIlLinkBytes;
     }
     l.ld = l.tq < 3;
-    l.lw = l.tq < 3 && l.gq < 6;
     const bool odd = (l.gq & 1) != 0;
-    l.psel = odd ? 0x1032u : 0x3210u;
+    l.psel = l.tq == 3 ? 0x4444u : odd ? 0x1032u : 0x3210u;
     l.pmf = odd ? 0x80000000u : 0u;
     l.pmb = odd ? 0x00008000u : 0u;
     // lane offsets in a stage: spinor words (3 s + t) * 64 + pair * 8 (pair
@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     // of t = 0: finite values against the zero B rows of colour 3.
     const int teff = l.tq < 3 ? l.tq : 0;
     const int woff = teff * 64 + ((teff == 2 ? l.gq ^ 4 : l.gq) * 8);
-    const int lf_off = (3 * (l.gq >> 1) + l.tq) * 4, lb_off = (3 * l.tq + (l.gq >> 1)) * 4;
+    // link words: entry (g / 2, t) forward, (t, g / 2) backward.  Every lane
+    // loads a word of its direction's 48 bytes (lanes t = 3 that of t = 0,
+    // zeroed by psel); lanes g = 6, 7 read pad or colour words into B
+    // columns of output colour 3, which no lane stores.
+    const int lf_off = (3 * (l.gq >> 1) + teff) * 4, lb_off = (3 * teff + (l.gq >> 1)) * 4;
     const float nu = a.nu, shop = a.shop, inv = a.inv;
     float al0 = 0.0f, al1 = 0.0f;
     if constexpr (EPI == EPI_CGUPD) {
@@ -372,8 +376,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           pf[s] = *reinterpret_cast<const uint2*>(sd + (2 * mu) * kIlSiteBytes + woff + 192 * s);
           pb[s] = *reinterpret_cast<const uint2*>(sd + (2 * mu + 1) * kIlSiteBytes + woff + 192 * s);
         }
-        const unsigned uf = l.lw ? *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off) : 0u;
-        const unsigned ub = l.lw ? *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + kIlLinkSiteBytes + mu * kIlLinkBytes + lb_off) : 0u;
+        const unsigned uf = *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off);
+        const unsigned ub = *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + kIlLinkSiteBytes + mu * kIlLinkBytes + lb_off);
         const unsigned negf = (mu == 3 && (bf & 1u)) ? 0x80008000u : 0u;
         const unsigned negb = (mu == 3 && (bf & 2u)) ? 0x80008000u : 0u;
         if (mu == 0) il_dir<S, 0, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);

@@ -12,6 +12,11 @@ system where that takes seconds:
     formula on the same rounded inputs;
   * the LP solve of a source (interleaved layout, Schur) is bit-identical
     inside the batch and alone;
+  * the LP path of the bench on the interleaved layout, 16 systems: Z4
+    sources drawn there (the bytes of the standard noise converted), the
+    truncated solve (the bits of tm_cg_solve), D_W (2 x 512 sampled sites of
+    one system), and that system's generalised local loops (whole lattice)
+    and one-derivative loops (three slices) from the tensor-core kernels;
   * the HP solve (mixed precision, even/odd, 1e-9): the oracle's whole-lattice
     residual |eta - M x| / |eta|;
   * local loops of one system: the oracle's whole-lattice contraction;
@@ -168,3 +173,63 @@ def test_oneD_loops_sampled_slices(setup, prec, tol):
     for t in (0, 17, L[3] - 1):
         ref = _oneD_slice(U, la, lb, "gen", t)
         assert rel_l2(got[..., t], ref) < tol, t
+
+
+def test_interleaved_lp_path_full_size(setup):
+    """The LP batch as the bench runs it (16 FP16 systems, interleaved layout):
+    z4_noise_il, tm_cg_solve_il, D_W by tm_dslash_il, loop_contract_local_il
+    and loop_contract_oneD_il with gamma_5 on the right (generalised
+    estimator).  D_W against the oracle's formula at sampled sites (16u, as
+    for M); the contractions of system 5 against the oracle on the same FP16
+    values: local to FP32 rounding (1e-5), one-derivative with FP16-rounded
+    links to 4u (the link products rounded once)."""
+    tl, U, op = setup
+    n, T, r = 16, L[3], 5
+    u16 = UNIT_ROUNDOFF[tl.F16]
+    eta_il = tl.empty_field_il(L, n)
+    tl.z4_noise_il(L, eta_il, tl.F16, SEED, 0, n)
+    eta = tl.empty_field(L, tl.F16, n)
+    tl.z4_noise(L, eta, tl.F16, SEED, 0, n)
+    conv = tl.empty_field_il(L, n)
+    tl.tm_spinor_to_il(L, conv, eta, tl.F16, n)
+    torch.cuda.synchronize()
+    assert torch.equal(conv, eta_il)
+    del conv
+    prm = tl.cg_params(1e-2, 500, tl.CG_PLAIN, prec=tl.F16, check_every=2, schur=True)
+    x_il = tl.empty_field_il(L, n)
+    _, stats = tl.tm_cg_solve_il(op, x_il, eta_il, n, prm)
+    assert all(q["status"] == 0 and q["rel_res"] <= 1e-2 for q in stats)
+    x = tl.empty_field(L, tl.F16, n)
+    tl.tm_cg_solve(op, x, eta, n, prm)
+    conv = tl.empty_field_il(L, n)
+    tl.tm_spinor_to_il(L, conv, x, tl.F16, n)
+    torch.cuda.synchronize()
+    assert torch.equal(conv, x_il)
+    del conv, eta, eta_il
+    dw_il = tl.empty_field_il(L, n)
+    tl.tm_dslash_il(op, dw_il, x_il, n, mu_zero=True, prec=tl.F16)
+    dw = tl.empty_field(L, tl.F16, n)
+    tl.tm_spinor_from_il(L, dw, dw_il, tl.F16, n)
+    s = _unpack_one(tl, x, tl.F16, r, n)
+    w = _unpack_one(tl, dw, tl.F16, r, n)
+    del dw
+    sites = _sites(512, 4)
+    got = w[sites[:, 3], sites[:, 2], sites[:, 1], sites[:, 0]]
+    ref = apply_M_sites(U, s, KAPPA, 0.0, sites)
+    d = np.linalg.norm((got - ref).reshape(len(sites), -1), axis=1)
+    scale = np.maximum(np.linalg.norm(ref.reshape(len(sites), -1), axis=1),
+                       np.sqrt(np.mean(np.sum(np.abs(ref) ** 2, axis=(1, 2)))))
+    assert np.max(d / scale) < 16 * u16
+    g5w = w.copy()
+    g5w[..., 2:, :] *= -1
+    loc = torch.empty(n * 16 * T * 2, dtype=torch.float64, device="cuda")
+    tl.loop_contract_local_il(L, x_il, dw_il, tl.F16, n, tl.LOOP_GEN, loc, right_g5=True)
+    assert rel_l2(from_dev(loc, (n, 16, T))[r], oloops.local_loops(s, g5w, "gen")) < 1e-5
+    oned = torch.empty(n * 64 * T * 2, dtype=torch.float64, device="cuda")
+    tl.loop_contract_oneD_il(op, x_il, dw_il, tl.F16, n, tl.LOOP_GEN, oned, right_g5=True)
+    got = from_dev(oned, (n, 4, 16, T))[r]
+    tl.tm_op_check(op)                                 # no staging wait gave up
+    h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(torch.float16).to(torch.float64).numpy()
+    U16 = h(U.real) + 1j * h(U.imag)
+    for t in (0, 17, T - 1):
+        assert rel_l2(got[..., t], _oneD_slice(U16, s, g5w, "gen", t)) < 4 * u16, t
