@@ -87,7 +87,7 @@ struct IlArgs {
   int* trace_count;
   int nrhs, nblk, parity, nwarp;
   int centre, out_inv;
-  float nu, shop, inv;
+  float nu, shop, inv, sinv;  // sinv = shop * inv
 };
 
 // per-lane constants of a warp
@@ -195,12 +195,16 @@ struct IlStage {
 };
 
 
-// FORM = 2 * centre + out_inv: centre 0 (none), 1 (c), 2 (A c); out_inv: A^-1 on the result
+// FORM = 8 * norm + 2 * centre + out_inv: centre 0 (none), 1 (c), 2 (A c);
+// out_inv: A^-1 on the result; norm: the plain output also writes |out|^2
+// partial sums (the CG update and the residual always do)
+constexpr int kIlNorm = 8;
 template <class S, bool DAG, int EPI, int FORM>
 __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslash_il_kernel(const IlArgs a) {
   using H = H16<S>;
-  constexpr int CENTRE = FORM >> 1;
+  constexpr int CENTRE = (FORM & 7) >> 1;
   constexpr bool INV = (FORM & 1) != 0;
+  constexpr bool want_norm = EPI != EPI_OUT || (FORM & kIlNorm) != 0;
   using ST = IlStage<EPI>;
   extern __shared__ __align__(128) unsigned char il_smem[];
   __shared__ __align__(8) unsigned long long bars[kIlWarps][ST::kStages];
@@ -226,7 +230,6 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
   const int r0 = blk * kIlRows + l.gq, r1 = r0 + 8;
   const bool act0 = r0 < a.nrhs && (a.active == nullptr || a.active[r0] != 0);
   const bool act1 = r1 < a.nrhs && (a.active == nullptr || a.active[r1] != 0);
-  const bool want_norm = EPI != EPI_OUT || a.partial != nullptr;
   if (lane == 0) {
 #pragma unroll
     for (int st = 0; st < ST::kStages; ++st) mbar_init(smem_u32(&bars[wq][st]), 1);
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     // zeroed by psel); lanes g = 6, 7 read pad or colour words into B
     // columns of output colour 3, which no lane stores.
     const int lf_off = (3 * (l.gq >> 1) + teff) * 4, lb_off = (3 * teff + (l.gq >> 1)) * 4;
-    const float nu = a.nu, shop = a.shop, inv = a.inv;
+    const float nu = a.nu, shop = a.shop, inv = a.inv, sinv = a.sinv;
     float al0 = 0.0f, al1 = 0.0f;
     if constexpr (EPI == EPI_CGUPD) {
       al0 = act0 ? (float)a.alpha[r0] : 0.0f;
@@ -418,11 +421,15 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           }
           o0 = make_float2(__fmaf_rn(shop, h0r, c0.x), __fmaf_rn(shop, h0i, c0.y));
           o1 = make_float2(__fmaf_rn(shop, h1r, c1.x), __fmaf_rn(shop, h1i, c1.y));
+        } else if constexpr (INV) {
+          // A^-1 s_hop h = (s_hop / (1 + nu^2)) (h - i nu g5 h): one scale
+          o0 = make_float2(__fmul_rn(sinv, __fmaf_rn(tw, h0i, h0r)), __fmul_rn(sinv, __fmaf_rn(-tw, h0r, h0i)));
+          o1 = make_float2(__fmul_rn(sinv, __fmaf_rn(tw, h1i, h1r)), __fmul_rn(sinv, __fmaf_rn(-tw, h1r, h1i)));
         } else {
           o0 = make_float2(__fmul_rn(shop, h0r), __fmul_rn(shop, h0i));
           o1 = make_float2(__fmul_rn(shop, h1r), __fmul_rn(shop, h1i));
         }
-        if constexpr (INV) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
+        if constexpr (INV && CENTRE != 0) {  // A^-1 v = (v - i nu g5 v) / (1 + nu^2)
           o0 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o0.y, o0.x)), __fmul_rn(inv, __fmaf_rn(-tw, o0.x, o0.y)));
           o1 = make_float2(__fmul_rn(inv, __fmaf_rn(tw, o1.y, o1.x)), __fmul_rn(inv, __fmaf_rn(-tw, o1.x, o1.y)));
         }
@@ -430,8 +437,10 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           // every system's output (inactive and padding systems get the
           // operator applied to their own unchanged input)
           if (l.ld) ost[24 * s] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
-          n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
-          n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+          if constexpr (want_norm) {
+            n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
+            n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+          }
         } else if constexpr (EPI == EPI_CGUPD) {
           // r and x of inactive systems keep their bits
           float2 q0 = H::to_f2(rw[s].x), q1 = H::to_f2(rw[s].y);
@@ -456,8 +465,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
         }
       }
-      if (!l.ld) n0 = n1 = 0.0f;
-      if (want_norm) {
+      if constexpr (want_norm) {
+        if (!l.ld) n0 = n1 = 0.0f;
         if (act0) nacc0 = __fadd_rn(nacc0, n0);
         if (act1) nacc1 = __fadd_rn(nacc1, n1);
         // site base + wq + 4 m lies in 32-site group m / 8: flush at the group's end
@@ -478,7 +487,7 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       __syncwarp();  // every lane is done with the stage before it is refilled
     }
   }
-  if (want_norm) {
+  if constexpr (want_norm) {
     // the warps' sums of each 32-site group, fixed order
     __syncthreads();
     if (threadIdx.x < kIlGroups * kIlRows) {
@@ -505,7 +514,8 @@ static tm_status_t il_prepare_t() {
 }
 
 // the instantiated forms: every (centre, A^-1) combination for the plain
-// output, the twisted centre without A^-1 for the CG update and the residual
+// output, the twisted centre without A^-1 with norms (the solver's M) and
+// for the CG update and the residual
 template <class S, bool DAG>
 static tm_status_t il_prepare_sd() {
   TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 0>()));
@@ -514,6 +524,7 @@ static tm_status_t il_prepare_sd() {
   TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 3>()));
   TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 4>()));
   TM_TRY((il_prepare_t<S, DAG, EPI_OUT, 5>()));
+  TM_TRY((il_prepare_t<S, DAG, EPI_OUT, kIlNorm + 4>()));
   TM_TRY((il_prepare_t<S, DAG, EPI_CGUPD, 4>()));
   TM_TRY((il_prepare_t<S, DAG, EPI_RESID, 4>()));
   return TM_OK;
@@ -570,6 +581,7 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
   a.nu = (float)nu;
   a.shop = (float)hop;
   a.inv = (float)(1.0 / (1.0 + nu * nu));
+  a.sinv = (float)(hop / (1.0 + nu * nu));
   // every field the bulk copies read must sit on a 16-byte boundary
   const void* ptrs[6] = {a.in, a.cfield, a.p, a.x, a.r, a.b};
   for (const void* q : ptrs)
@@ -610,6 +622,10 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
     set_error("dslash_il: the CG update and residual forms need the twisted centre without A^-1");
     return TM_ERR_UNSUPPORTED;
   }
+  if (EPI == EPI_OUT && a.partial && form != 4) {
+    set_error("dslash_il: norms of the plain output only with the twisted centre without A^-1");
+    return TM_ERR_UNSUPPORTED;
+  }
   cudaEvent_t ev = nullptr;
   a.trace_count = trace_begin(st, &ev);
   const dim3 grid((unsigned)blocks);
@@ -620,7 +636,10 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
       case 1: dslash_il_kernel<S, DAG, EPI, 1><<<grid, kT, kM, st>>>(a); break;
       case 2: dslash_il_kernel<S, DAG, EPI, 2><<<grid, kT, kM, st>>>(a); break;
       case 3: dslash_il_kernel<S, DAG, EPI, 3><<<grid, kT, kM, st>>>(a); break;
-      case 4: dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a); break;
+      case 4:
+        if (a.partial) dslash_il_kernel<S, DAG, EPI, kIlNorm + 4><<<grid, kT, kM, st>>>(a);
+        else dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a);
+        break;
       default: dslash_il_kernel<S, DAG, EPI, 5><<<grid, kT, kM, st>>>(a); break;
     }
   } else {

@@ -199,13 +199,15 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
     };
     // stage 1 lane constants (as the interleaved Dslash): A words of rows
     // g, g + 8 at colour t (lanes t = 3 read colour 0 against zero B rows);
-    // link words, forward U[g/2][t], adjoint U[t][g/2]; B word transforms
+    // link words, forward U[g/2][t], adjoint U[t][g/2], loaded by every lane
+    // (lanes t = 3 those of t = 0, zeroed by the byte selector psel; lanes
+    // g = 6, 7 pad or colour words into the B columns of output colour 3,
+    // which no lane stores); B word transforms
     const int teff = tq < 3 ? tq : 0;
     const int woff = teff * 64 + (teff == 2 ? gq ^ 4 : gq) * 8;
-    const bool lw = tq < 3 && gq < 6;
-    const int lf_off = (3 * (gq >> 1) + tq) * 4, lb_off = (3 * tq + (gq >> 1)) * 4;
+    const int lf_off = (3 * (gq >> 1) + teff) * 4, lb_off = (3 * teff + (gq >> 1)) * 4;
     const bool odd = (gq & 1) != 0;
-    const unsigned psel = odd ? 0x1032u : 0x3210u;
+    const unsigned psel = tq == 3 ? 0x4444u : odd ? 0x1032u : 0x3210u;
     const unsigned pfw = odd ? 0u : 0x80000000u;   // forward:  conj(u) / (u_im, u_re)
     const unsigned pad = odd ? 0x00008000u : 0u;   // adjoint:  u / (-u_im, u_re)
     // stage 2 lane constants: A words (row g' = 4 mu + b of class g' >> 2 and
@@ -245,8 +247,8 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
           pf[s] = lds64(sd + (2 * mu) * kIlSiteBytes + woff + 192 * s);
           pb[s] = lds64(sd + (2 * mu + 1) * kIlSiteBytes + woff + 192 * s);
         }
-        const unsigned uf = lw ? lds32(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off) : 0u;
-        const unsigned ub = lw ? lds32(sd + ST::kBwdOff + mu * kIlLinkBytes + lb_off) : 0u;
+        const unsigned uf = lds32(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off);
+        const unsigned ub = lds32(sd + ST::kBwdOff + mu * kIlLinkBytes + lb_off);
         const unsigned b0 = __byte_perm(uf, 0u, psel) ^ pfw;
         const unsigned b1 = __byte_perm(ub, 0u, psel) ^ pad ^ 0x80008000u;
         float d[4][4];
@@ -262,8 +264,8 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
           pf[s] = lds64(sd + 6 * kIlSiteBytes + woff + 192 * s);
           pc[s] = lds64(sd + 7 * kIlSiteBytes + woff + 192 * s);
         }
-        const unsigned ut = lw ? lds32(sd + ST::kLinkOff + 3 * kIlLinkBytes + lf_off) : 0u;
-        const unsigned ua = lw ? lds32(sd + ST::kLinkOff + 3 * kIlLinkBytes + lb_off) : 0u;
+        const unsigned ut = lds32(sd + ST::kLinkOff + 3 * kIlLinkBytes + lf_off);
+        const unsigned ua = lds32(sd + ST::kLinkOff + 3 * kIlLinkBytes + lb_off);
         const unsigned neg = (g.antiperiodic && (msk_m & 0x40u)) ? 0x80008000u : 0u;
         const unsigned bt = __byte_perm(ut, 0u, psel) ^ pfw ^ neg;
         const unsigned ba = __byte_perm(ua, 0u, psel) ^ pad ^ 0x80008000u ^ neg;
