@@ -97,7 +97,11 @@ struct IlLane {
   // lane phase of the link words: swap halves on odd columns; lanes t = 3
   // (B rows of colour 3) select zero bytes
   unsigned psel;
-  unsigned pmf, pmb;
+  // lane phase (odd columns: forward words times -i, backward words times
+  // +i) combined with the fixed sign flips of the four B words: forward
+  // conj(u) for the upper spins, SF-signed for the lower ones; backward u,
+  // SB-signed
+  unsigned fup, fm, bup, bm;
 };
 
 
@@ -136,10 +140,10 @@ __device__ __forceinline__ void il_dir(float (&up)[2][4], float (&q)[6][4], cons
   using G = IlG<MU>;
   constexpr int SB = -SF;
   constexpr int pf2 = SF < 0 ? 2 : 0, pb2 = SB < 0 ? 2 : 0;
-  // lane phase (odd columns: forward words times -i, backward words times +i)
-  // and the time-boundary sign; every B word below is then a fixed sign flip
-  uf = __byte_perm(uf, 0u, l.psel) ^ l.pmf ^ negf;
-  ub = __byte_perm(ub, 0u, l.psel) ^ l.pmb ^ negb;
+  // lane swap of the link words (odd columns); the lane's sign patterns and
+  // the time-boundary sign follow in one logic operation per B word
+  uf = __byte_perm(uf, 0u, l.psel);
+  ub = __byte_perm(ub, 0u, l.psel);
   // projected words (rows g, g + 8) of the two upper spins for both hops
   const unsigned h0f0 = proj_w<G::ak0 + pf2, S>(pf[0].x, pf[2 + G::ac0].x);
   const unsigned h0f1 = proj_w<G::ak0 + pf2, S>(pf[0].y, pf[2 + G::ac0].y);
@@ -151,9 +155,9 @@ __device__ __forceinline__ void il_dir(float (&up)[2][4], float (&q)[6][4], cons
   const unsigned h1b1 = proj_w<G::ak1 + pb2, S>(pb[1].y, pb[2 + G::ac1].y);
   // B words: [U_f; U_b^dag] (forward conj(u), backward u) and the signed
   // [SF U_f; SB U_b^dag]
-  const unsigned bf_up = uf ^ 0x80000000u, bb_up = ub;
-  const unsigned bf_m = SF < 0 ? uf ^ 0x00008000u : bf_up;
-  const unsigned bb_m = SB < 0 ? ub ^ 0x80008000u : bb_up;
+  const unsigned bf_up = uf ^ l.fup ^ negf, bb_up = ub ^ l.bup ^ negb;
+  const unsigned bf_m = SF < 0 ? uf ^ l.fm ^ negf : bf_up;
+  const unsigned bb_m = SB < 0 ? ub ^ l.bm ^ negb : bb_up;
   // the first product into each accumulator of the site seeds it (direction 0
   // for the upper spins, il_quad_first for the quads)
   constexpr int q0 = il_quad(0, G::bk0), q1 = il_quad(1, G::bk1);
@@ -288,8 +292,14 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     l.ld = l.tq < 3;
     const bool odd = (l.gq & 1) != 0;
     l.psel = l.tq == 3 ? 0x4444u : odd ? 0x1032u : 0x3210u;
-    l.pmf = odd ? 0x80000000u : 0u;
-    l.pmb = odd ? 0x00008000u : 0u;
+    {
+      constexpr int SFl = DAG ? +1 : -1;
+      const unsigned pmf = odd ? 0x80000000u : 0u, pmb = odd ? 0x00008000u : 0u;
+      l.fup = pmf ^ 0x80000000u;
+      l.fm = SFl < 0 ? pmf ^ 0x00008000u : l.fup;
+      l.bup = pmb;
+      l.bm = SFl > 0 ? pmb ^ 0x80008000u : pmb;
+    }
     // lane offsets in a stage: spinor words (3 s + t) * 64 + pair * 8 (pair
     // position g, XOR 4 on colour 2).  Lanes t = 3 (no colour) read the words
     // of t = 0: finite values against the zero B rows of colour 3.
@@ -301,11 +311,14 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     // columns of output colour 3, which no lane stores.
     const int lf_off = (3 * (l.gq >> 1) + teff) * 4, lb_off = (3 * teff + (l.gq >> 1)) * 4;
     const float nu = a.nu, shop = a.shop, inv = a.inv, sinv = a.sinv;
+    const float2 shop2 = make_float2(shop, shop);
     float al0 = 0.0f, al1 = 0.0f;
     if constexpr (EPI == EPI_CGUPD) {
       al0 = act0 ? (float)a.alpha[r0] : 0.0f;
       al1 = act1 ? (float)a.alpha[r1] : 0.0f;
     }
+    const float2 pal0 = make_float2(al0, al0), pal1 = make_float2(al1, al1);
+    const float2 nal0 = make_float2(-al0, -al0), nal1 = make_float2(-al1, -al1);
     unsigned char* ring = il_smem + wq * ST::kWarpBytes;
     const unsigned ring_s = smem_u32(ring);
     const unsigned bar0 = smem_u32(&bars[wq][0]);
@@ -407,7 +420,9 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         hs[3][rr] = __fadd_rn(__fsub_rn(__fsub_rn(qq[2][rr + 1], qq[3][rr]), qq[4][rr + 1]), qq[5][rr]);
         hs[3][rr + 1] = __fadd_rn(__fsub_rn(qq[4][rr], __fadd_rn(qq[2][rr], qq[3][rr + 1])), qq[5][rr + 1]);
       }
-      float n0 = 0.0f, n1 = 0.0f;
+      // (re, im) pairs in packed FP32x2 operations where both parts take the
+      // same factor (each lane an ordinary round-to-nearest FMA)
+      float2 n0 = make_float2(0.0f, 0.0f), n1 = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const float tw = s < 2 ? nu : -nu;  // gamma_5 = diag(1, 1, -1, -1)
@@ -419,8 +434,8 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
             c0 = make_float2(__fmaf_rn(-tw, c0.y, c0.x), __fmaf_rn(tw, c0.x, c0.y));
             c1 = make_float2(__fmaf_rn(-tw, c1.y, c1.x), __fmaf_rn(tw, c1.x, c1.y));
           }
-          o0 = make_float2(__fmaf_rn(shop, h0r, c0.x), __fmaf_rn(shop, h0i, c0.y));
-          o1 = make_float2(__fmaf_rn(shop, h1r, c1.x), __fmaf_rn(shop, h1i, c1.y));
+          o0 = __ffma2_rn(shop2, make_float2(h0r, h0i), c0);
+          o1 = __ffma2_rn(shop2, make_float2(h1r, h1i), c1);
         } else if constexpr (INV) {
           // A^-1 s_hop h = (s_hop / (1 + nu^2)) (h - i nu g5 h): one scale
           o0 = make_float2(__fmul_rn(sinv, __fmaf_rn(tw, h0i, h0r)), __fmul_rn(sinv, __fmaf_rn(-tw, h0r, h0i)));
@@ -438,37 +453,36 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           // operator applied to their own unchanged input)
           if (l.ld) ost[24 * s] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
           if constexpr (want_norm) {
-            n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
-            n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+            n0 = __ffma2_rn(o0, o0, n0);
+            n1 = __ffma2_rn(o1, o1, n1);
           }
         } else if constexpr (EPI == EPI_CGUPD) {
           // r and x of inactive systems keep their bits
           float2 q0 = H::to_f2(rw[s].x), q1 = H::to_f2(rw[s].y);
-          q0 = make_float2(__fmaf_rn(-al0, o0.x, q0.x), __fmaf_rn(-al0, o0.y, q0.y));
-          q1 = make_float2(__fmaf_rn(-al1, o1.x, q1.x), __fmaf_rn(-al1, o1.y, q1.y));
+          q0 = __ffma2_rn(nal0, o0, q0);
+          q1 = __ffma2_rn(nal1, o1, q1);
           const uint2 rn = make_uint2(act0 ? H::pack(q0.x, q0.y) : rw[s].x, act1 ? H::pack(q1.x, q1.y) : rw[s].y);
-          n0 = __fmaf_rn(q0.x, q0.x, n0); n0 = __fmaf_rn(q0.y, q0.y, n0);
-          n1 = __fmaf_rn(q1.x, q1.x, n1); n1 = __fmaf_rn(q1.y, q1.y, n1);
-          const float2 x0 = H::to_f2(xw[s].x), x1 = H::to_f2(xw[s].y), p0 = H::to_f2(pw[s].x), p1 = H::to_f2(pw[s].y);
-          const uint2 xn = make_uint2(act0 ? H::pack(__fmaf_rn(al0, p0.x, x0.x), __fmaf_rn(al0, p0.y, x0.y)) : xw[s].x,
-                                      act1 ? H::pack(__fmaf_rn(al1, p1.x, x1.x), __fmaf_rn(al1, p1.y, x1.y)) : xw[s].y);
+          n0 = __ffma2_rn(q0, q0, n0);
+          n1 = __ffma2_rn(q1, q1, n1);
+          const float2 x0 = __ffma2_rn(pal0, H::to_f2(pw[s].x), H::to_f2(xw[s].x));
+          const float2 x1 = __ffma2_rn(pal1, H::to_f2(pw[s].y), H::to_f2(xw[s].y));
+          const uint2 xn = make_uint2(act0 ? H::pack(x0.x, x0.y) : xw[s].x, act1 ? H::pack(x1.x, x1.y) : xw[s].y);
           if (l.ld) {
             ost[24 * s] = rn;
             xst[24 * s] = xn;
           }
         } else {  // EPI_RESID: out = b - D in
-          const float2 b0 = H::to_f2(rw[s].x), b1 = H::to_f2(rw[s].y);
-          o0 = make_float2(__fsub_rn(b0.x, o0.x), __fsub_rn(b0.y, o0.y));
-          o1 = make_float2(__fsub_rn(b1.x, o1.x), __fsub_rn(b1.y, o1.y));
+          const float2 m1 = make_float2(-1.0f, -1.0f);  // b - o, rounded once as by a subtraction
+          o0 = __ffma2_rn(m1, o0, H::to_f2(rw[s].x));
+          o1 = __ffma2_rn(m1, o1, H::to_f2(rw[s].y));
           if (l.ld) ost[24 * s] = make_uint2(H::pack(o0.x, o0.y), H::pack(o1.x, o1.y));
-          n0 = __fmaf_rn(o0.x, o0.x, n0); n0 = __fmaf_rn(o0.y, o0.y, n0);
-          n1 = __fmaf_rn(o1.x, o1.x, n1); n1 = __fmaf_rn(o1.y, o1.y, n1);
+          n0 = __ffma2_rn(o0, o0, n0);
+          n1 = __ffma2_rn(o1, o1, n1);
         }
       }
       if constexpr (want_norm) {
-        if (!l.ld) n0 = n1 = 0.0f;
-        if (act0) nacc0 = __fadd_rn(nacc0, n0);
-        if (act1) nacc1 = __fadd_rn(nacc1, n1);
+        if (l.ld && act0) nacc0 = __fadd_rn(nacc0, __fadd_rn(n0.x, n0.y));
+        if (l.ld && act1) nacc1 = __fadd_rn(nacc1, __fadd_rn(n1.x, n1.y));
         // site base + wq + 4 m lies in 32-site group m / 8: flush at the group's end
         static_assert(kIlWarps == 4, "a warp takes 8 sites of each 32-site group");
         if ((m & 7) == 7 || m == nsite - 1) {
