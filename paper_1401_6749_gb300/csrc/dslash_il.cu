@@ -38,6 +38,8 @@
 #include <cstdlib>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "il_core.cuh"
 
 namespace tml {
@@ -180,10 +182,16 @@ __device__ __forceinline__ void il_store(uint2* p, unsigned w0, unsigned w1, boo
 // Each warp owns a ring of two stages in shared memory; a stage holds what
 // the hops of one output site need: its eight neighbour sites (768 bytes
 // each, copied whole), its forward links (4 directions x 48 bytes) and the
-// four backward links.  One bulk asynchronous copy (cp.async.bulk) per block,
-// each issued by its own lane in one instruction, completes on the stage's
-// mbarrier, whose expected byte count lane 0 posts; every lane waits on the
-// barrier's phase before reading its words.  The copies of site m + 1 are in
+// four backward links.  Four asynchronous copies fill a stage: two tensor
+// copies in gather4 mode (four neighbour sites each, rows of the field seen
+// as a 2-D tensor of 768-byte rows), one bulk copy of the forward links and
+// one gather4 copy of the backward links (rows of 48 bytes, one per site and
+// direction).  Every lane computes the row of one neighbour or backward link
+// and lane 0 issues the four copies, which complete on the stage's mbarrier;
+// every lane waits on the barrier's phase before reading its words.  (Copies
+// issued by several lanes at once execute one lane after another, each with
+// its own operand set-up: thirteen per-lane copies per site cost about a
+// quarter of the kernel's instructions.)  The copies of site m + 1 are in
 // flight while site m is computed.  The words of the output site itself
 // (centre, residual, solution, search direction) are read straight into
 // registers, issued right after the previous site's epilogue.
@@ -191,8 +199,9 @@ constexpr int kIlGroups = 2;                     // 32-site groups per block
 
 template <int EPI>
 struct IlStage {
-  static constexpr int kLinkOff = 8 * kIlSiteBytes;               // after the eight neighbours
-  static constexpr int kBytes = kLinkOff + 2 * kIlLinkSiteBytes;  // forward site links + 4 backward
+  static constexpr int kLinkOff = 8 * kIlSiteBytes;     // after the eight neighbours
+  static constexpr int kBwdOff = kLinkOff + 256;        // tensor copies land on 128-byte boundaries
+  static constexpr int kBytes = kBwdOff + 256;          // so do the stages
   static constexpr int kStages = 2;
   static constexpr int kWarpBytes = kStages * kBytes;
   static constexpr int kSmem = kIlWarps * kWarpBytes;
@@ -204,7 +213,8 @@ struct IlStage {
 // partial sums (the CG update and the residual always do)
 constexpr int kIlNorm = 8;
 template <class S, bool DAG, int EPI, int FORM>
-__global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslash_il_kernel(const IlArgs a) {
+__global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4)
+    dslash_il_kernel(const IlArgs a, const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tlk) {
   using H = H16<S>;
   constexpr int CENTRE = (FORM & 7) >> 1;
   constexpr bool INV = (FORM & 1) != 0;
@@ -213,11 +223,18 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
   extern __shared__ __align__(128) unsigned char il_smem[];
   __shared__ __align__(8) unsigned long long bars[kIlWarps][ST::kStages];
   __shared__ float red[kIlWarps][kIlGroups][kIlRows];
+  __shared__ __align__(16) int rowbuf[kIlWarps][12];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31;
   const int wq = threadIdx.x >> 5;
   const int blk = blockIdx.x % a.nblk;
   const int rest = blockIdx.x / a.nblk;
+  // the tensor copies need 128-byte aligned destinations: a block whose
+  // dynamic shared memory is not (never expected) flags the error and stops
+  if (smem_u32(il_smem) & 127u) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    return;
+  }
   if (a.trace_count && blockIdx.x == 0 && threadIdx.x == 0) {
     int n = 0;
     for (int r = 0; r < a.nrhs; ++r) n += (a.active == nullptr || a.active[r] != 0) ? 1 : 0;
@@ -260,35 +277,20 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
         bml |= (s.c[mu] == g.L[mu] - 1 ? 1u : 0u) << (2 * mu) | (s.c[mu] == 0 ? 2u : 0u) << (2 * mu);
     }
     const size_t obase = ((size_t)blk * 2 + par) * Vh * kIlSiteBytes;
-    // copy role of this lane (one bulk copy per lane and site): lanes 0..7 the
-    // neighbours (direction lane / 2, forward for even lanes), 9 the forward
-    // links, 10..13 the backward link of direction lane - 10; src = rbase +
-    // index * rmul, index the neighbour's or the site's checkerboard index
-    const int rmu = lane < 8 ? (lane >> 1) : (lane >= 10 && lane < 14 ? lane - 10 : 0);
+    // row role of this lane: lanes 0..7 the neighbour of direction lane / 2
+    // (forward for even lanes), a row (blk * 2 + opar) * Vh + cb' of the
+    // field; lanes 8..11 the backward link of direction lane - 8, row
+    // (opar * Vh + cb') * 4 + mu of the links; cb' the neighbour's
+    // checkerboard index
+    const int rmu = lane < 8 ? (lane >> 1) : (lane < 12 ? lane - 8 : 0);
     const bool rbwd = lane < 8 ? (lane & 1) != 0 : true;
-    const bool rnb = lane < 8 || (lane >= 10 && lane < 14);
     // the role's hop: lex step, and the step when it wraps around
     const int rbit = 2 * rmu + (rbwd ? 1 : 0);
     const int rstep = rbwd ? -g.stride[rmu] : g.stride[rmu];
     const int rwrap = rbwd ? (g.L[rmu] - 1) * g.stride[rmu] : -(g.L[rmu] - 1) * g.stride[rmu];
-    const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il);
-    const unsigned char* rbase = nullptr;
-    unsigned rmul = kIlSiteBytes, rdoff = 0, rbytes = 0;
-    if (lane < 8) {
-      rbase = reinterpret_cast<const unsigned char*>(a.in) + ((size_t)blk * 2 + opar) * Vh * kIlSiteBytes;
-      rdoff = lane * kIlSiteBytes;
-      rbytes = kIlSiteBytes;
-    } else if (lane == 9) {
-      rbase = lk + (size_t)par * Vh * kIlLinkSiteBytes;
-      rmul = kIlLinkSiteBytes;
-      rdoff = ST::kLinkOff;
-      rbytes = kIlLinkSiteBytes;
-    } else if (lane >= 10 && lane < 14) {
-      rbase = lk + (size_t)opar * Vh * kIlLinkSiteBytes + rmu * kIlLinkBytes;
-      rmul = kIlLinkSiteBytes;
-      rdoff = ST::kLinkOff + kIlLinkSiteBytes + rmu * kIlLinkBytes;
-      rbytes = kIlLinkBytes;
-    }
+    const int rrow0 = lane < 8 ? (blk * 2 + opar) * g.Vh : opar * g.Vh * 4 + rmu;
+    const int rrmul = lane < 8 ? 1 : 4;
+    const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il) + (size_t)par * Vh * kIlLinkSiteBytes;
     l.ld = l.tq < 3;
     const bool odd = (l.gq & 1) != 0;
     l.psel = l.tq == 3 ? 0x4444u : odd ? 0x1032u : 0x3210u;
@@ -324,6 +326,9 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
     const unsigned bar0 = smem_u32(&bars[wq][0]);
     constexpr int SF = DAG ? +1 : -1;
     constexpr unsigned total = 8 * kIlSiteBytes + kIlLinkSiteBytes + 4 * kIlLinkBytes;
+    static_assert(ST::kBwdOff % 128 == 0 && ST::kBytes % 128 == 0 && ST::kBwdOff >= ST::kLinkOff + kIlLinkSiteBytes &&
+                      ST::kBytes >= ST::kBwdOff + 4 * kIlLinkBytes,
+                  "stage layout");
     // the output site's own words (centre, r, x, p or b), straight into
     // registers; per-lane base pointers of the output parity, so that a site
     // adds one offset and the spins are immediate offsets
@@ -354,13 +359,24 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
       const int lex = __shfl_sync(0xffffffffu, lexl, m);
       const unsigned msk = __shfl_sync(0xffffffffu, bml, m);
       const int nlex = lex + (((msk >> rbit) & 1u) ? rwrap : rstep);
-      const int idx = rnb ? (nlex >> 1) : base + wq + kIlWarps * m;
+      if (lane < 12) rowbuf[wq][lane] = rrow0 + (nlex >> 1) * rrmul;
       const unsigned bar = bar0 + st * 8;
       // the stage was last read by this warp (generic proxy): order those reads
-      // before the copies' writes (async proxy)
+      // before the copies' writes (async proxy), every lane before lane 0 issues
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (lane == 0) mbar_expect_tx(bar, total);
-      if (rbytes) bulk_g2s(ring_s + st * ST::kBytes + rdoff, rbase + (size_t)idx * rmul, rbytes, bar);
+      __syncwarp();
+      if (lane == 0) {
+        const int4 q0 = *reinterpret_cast<const int4*>(&rowbuf[wq][0]);
+        const int4 q1 = *reinterpret_cast<const int4*>(&rowbuf[wq][4]);
+        const int4 q2 = *reinterpret_cast<const int4*>(&rowbuf[wq][8]);
+        const unsigned sb = ring_s + st * ST::kBytes;
+        mbar_expect_tx(bar, total);
+        gather4_g2s(sb, &tin, q0.x, q0.y, q0.z, q0.w, bar);
+        gather4_g2s(sb + 4 * kIlSiteBytes, &tin, q1.x, q1.y, q1.z, q1.w, bar);
+        bulk_g2s(sb + ST::kLinkOff, lk + (size_t)(base + wq + kIlWarps * m) * kIlLinkSiteBytes, kIlLinkSiteBytes,
+                 bar);
+        gather4_g2s(sb + ST::kBwdOff, &tlk, q2.x, q2.y, q2.z, q2.w, bar);
+      }
       return msk;
     };
     static_assert(ST::kStages == 2, "one site in flight while one is computed");
@@ -393,7 +409,7 @@ __global__ void __launch_bounds__(kIlWarps * 32, EPI == EPI_CGUPD ? 3 : 4) dslas
           pb[s] = *reinterpret_cast<const uint2*>(sd + (2 * mu + 1) * kIlSiteBytes + woff + 192 * s);
         }
         const unsigned uf = *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + mu * kIlLinkBytes + lf_off);
-        const unsigned ub = *reinterpret_cast<const unsigned*>(sd + ST::kLinkOff + kIlLinkSiteBytes + mu * kIlLinkBytes + lb_off);
+        const unsigned ub = *reinterpret_cast<const unsigned*>(sd + ST::kBwdOff + mu * kIlLinkBytes + lb_off);
         const unsigned negf = (mu == 3 && (bf & 1u)) ? 0x80008000u : 0u;
         const unsigned negb = (mu == 3 && (bf & 2u)) ? 0x80008000u : 0u;
         if (mu == 0) il_dir<S, 0, SF>(ua, qq, l, pf, pb, uf, ub, negf, negb);
@@ -558,6 +574,44 @@ tm_status_t il_prepare() {
   return TM_OK;
 }
 
+// ------------------------------------------------ tensor maps (host)
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 il_encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// rows of row_words 4-byte words at base as a 2-D tensor whose box is one
+// whole row (the gather4 copies take four rows at a time)
+tm_status_t il_row_map(CUtensorMap* m, const void* base, unsigned row_words, size_t rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = il_encode_fn();
+  if (!enc) {
+    set_error("dslash_il: cuTensorMapEncodeTiled is not available");
+    return TM_ERR_CUDA;
+  }
+  const cuuint64_t dim[2] = {row_words, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)row_words * 4};
+  const cuuint32_t box[2] = {row_words, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dim, stride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("dslash_il: tensor map encoding failed (%d)", (int)r);
+    return TM_ERR_CUDA;
+  }
+  return TM_OK;
+}
+
 template <class S, bool DAG, int EPI>
 static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_t st, tm_prec_t prec) {
   IlArgs a{};
@@ -603,10 +657,16 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
       set_error("dslash_il: fields must be 16-byte aligned");
       return TM_ERR_ARG;
     }
-  if ((size_t)g.Vh * kIlSiteBytes / 8 >= (size_t)0xffffffffu) {
-    set_error("dslash_il: lattice too large for the interleaved kernel (V/2 * 96 >= 2^32)");
+  if ((size_t)g.Vh * kIlSiteBytes / 8 >= (size_t)0xffffffffu || (size_t)a.nblk * 2 * g.Vh >= ((size_t)1 << 31) ||
+      (size_t)g.Vh * 8 >= ((size_t)1 << 31)) {
+    set_error("dslash_il: lattice too large for the interleaved kernel (V/2 * 96 >= 2^32 or rows >= 2^31)");
     return TM_ERR_UNSUPPORTED;
   }
+  // the neighbours' rows (768 bytes per site) and the backward links' rows
+  // (48 bytes per site and direction) as tensors of the gather4 copies
+  CUtensorMap tin, tlk;
+  TM_TRY(il_row_map(&tin, a.in, kIlSiteBytes / 4, (size_t)a.nblk * 2 * g.Vh));
+  TM_TRY(il_row_map(&tlk, a.links_il, kIlLinkBytes / 4, (size_t)g.Vh * 8));
   const int npar = c.parity < 0 ? 2 : 1;
   const long chunks = ((long)g.Vh + kIlGroups * 32 - 1) / (kIlGroups * 32);
   const long blocks = (long)a.nblk * npar * chunks;  // one block per 128 sites and 16 systems
@@ -646,18 +706,18 @@ static tm_status_t il_launch_t(const tm_op* op, const DslashCall& c, cudaStream_
   constexpr int kT = kIlWarps * 32, kM = IlStage<EPI>::kSmem;
   if constexpr (EPI == EPI_OUT) {
     switch (form) {
-      case 0: dslash_il_kernel<S, DAG, EPI, 0><<<grid, kT, kM, st>>>(a); break;
-      case 1: dslash_il_kernel<S, DAG, EPI, 1><<<grid, kT, kM, st>>>(a); break;
-      case 2: dslash_il_kernel<S, DAG, EPI, 2><<<grid, kT, kM, st>>>(a); break;
-      case 3: dslash_il_kernel<S, DAG, EPI, 3><<<grid, kT, kM, st>>>(a); break;
+      case 0: dslash_il_kernel<S, DAG, EPI, 0><<<grid, kT, kM, st>>>(a, tin, tlk); break;
+      case 1: dslash_il_kernel<S, DAG, EPI, 1><<<grid, kT, kM, st>>>(a, tin, tlk); break;
+      case 2: dslash_il_kernel<S, DAG, EPI, 2><<<grid, kT, kM, st>>>(a, tin, tlk); break;
+      case 3: dslash_il_kernel<S, DAG, EPI, 3><<<grid, kT, kM, st>>>(a, tin, tlk); break;
       case 4:
-        if (a.partial) dslash_il_kernel<S, DAG, EPI, kIlNorm + 4><<<grid, kT, kM, st>>>(a);
-        else dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a);
+        if (a.partial) dslash_il_kernel<S, DAG, EPI, kIlNorm + 4><<<grid, kT, kM, st>>>(a, tin, tlk);
+        else dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a, tin, tlk);
         break;
-      default: dslash_il_kernel<S, DAG, EPI, 5><<<grid, kT, kM, st>>>(a); break;
+      default: dslash_il_kernel<S, DAG, EPI, 5><<<grid, kT, kM, st>>>(a, tin, tlk); break;
     }
   } else {
-    dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a);
+    dslash_il_kernel<S, DAG, EPI, 4><<<grid, kT, kM, st>>>(a, tin, tlk);
   }
   count_launch();
   trace_end(st, name, ev, a.trace_count, per_rhs, fixed, 0, out_sites * site_flops);

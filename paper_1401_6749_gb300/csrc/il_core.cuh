@@ -10,6 +10,8 @@
 // k = 0, 1 (mod 3) and j ^ 4 in rows k = 2 (mod 3).
 #pragma once
 
+#include <cuda.h>
+
 #include "tm_host.h"
 
 namespace tml {
@@ -170,6 +172,17 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// four rows of a 2-D tensor (rows r0..r3, the whole box of columns from
+// column 0) into consecutive rows at dst: one tensor copy in gather4 mode
+__device__ __forceinline__ void gather4_g2s(unsigned dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+      : "memory");
+}
+
 // bounded wait for a stage; false (and the launch's error flag set) if it
 // gave up, after kIlWaitNs of global time or kIlWaitLimit rounds
 __device__ __forceinline__ bool il_wait(unsigned bar, unsigned phase, int* err) {
