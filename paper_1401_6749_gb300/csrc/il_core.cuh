@@ -172,6 +172,10 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// rows of row_words 4-byte words at base as a 2-D tensor whose box is one
+// whole row, for the gather4 copies (host; dslash_il.cu)
+tm_status_t il_row_map(CUtensorMap* m, const void* base, unsigned row_words, size_t rows);
+
 // four rows of a 2-D tensor (rows r0..r3, the whole box of columns from
 // column 0) into consecutive rows at dst: one tensor copy in gather4 mode
 __device__ __forceinline__ void gather4_g2s(unsigned dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,

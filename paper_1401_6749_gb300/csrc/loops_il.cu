@@ -59,11 +59,13 @@ static_assert(kOdChunk % (32 * kOdWarps) == 0, "whole 32-site groups per warp");
 
 struct OdStage {
   static constexpr int kLinkOff = 10 * kIlSiteBytes;                 // ten sites, then U_mu(x)
-  static constexpr int kBwdOff = kLinkOff + kIlLinkSiteBytes;        // U_mu(x - mu), mu < 3
-  static constexpr int kCopyBytes = kBwdOff + 3 * kIlLinkBytes;      // 8016 bytes copied per site
+  // U_mu(x - mu), mu < 3, and a fourth row (a copy of mu = 2) that fills the
+  // gather4 copy; on a 128-byte line, as tensor copies need
+  static constexpr int kBwdOff = kLinkOff + 256;
+  static constexpr int kCopyBytes = 10 * kIlSiteBytes + kIlLinkSiteBytes + 4 * kIlLinkBytes;  // 8064 per site
   // stages start on 128-byte lines, so that every stage has the bank
   // alignment of the zero block's line
-  static constexpr int kBytes = (kCopyBytes + 127) / 128 * 128;       // 8064
+  static constexpr int kBytes = kBwdOff + 256;                        // 8192
   static constexpr int kStages = 2;
   static constexpr int kWarpBytes = kStages * kBytes;
   // zero words for the lanes without a product word: 48 bytes into a line,
@@ -111,12 +113,20 @@ __device__ __forceinline__ void od_store(unsigned char* w, const float (&d)[4][4
 }
 
 template <class S>
-__global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs a) {
+__global__ void __launch_bounds__(kOdWarps * 32, 3)
+    oneD_il_kernel(const OdArgs a, const __grid_constant__ CUtensorMap tr, const __grid_constant__ CUtensorMap tlk) {
   using ST = OdStage;
   extern __shared__ __align__(128) unsigned char od_smem[];
   __shared__ __align__(8) unsigned long long bars[kOdWarps][ST::kStages];
+  __shared__ __align__(16) int rowbuf[kOdWarps][12];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  // the tensor copies need 128-byte aligned destinations: a block whose
+  // dynamic shared memory is not (never expected) flags the error and stops
+  if (smem_u32(od_smem) & 127u) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    return;
+  }
   const int blk = blockIdx.x % a.nblk, chunk = blockIdx.x / a.nblk;
   const int t = blockIdx.y >> 1, par = blockIdx.y & 1, opar = par ^ 1;
   const size_t Vh = (size_t)g.Vh;
@@ -137,38 +147,24 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
   for (int s = 0; s < kIlRows; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.0f;
   const int gq = lane >> 2, tq = lane & 3;
   if (nsite > 0) {
-    // copy role of this lane: 0..5 R(x +- mu), 6 R(x + t), 7 R(x), 8 L(x),
-    // 9 L(x + t), 10 U(x), 11..13 U_mu(x - mu); hop roles add the
-    // neighbour's lex step (or its wrap), the others take the site itself
-    const bool hop = lane < 7 || lane == 9 || (lane >= 11 && lane < 14);
-    const int rmu = lane < 6 ? (lane >> 1) : (lane == 6 || lane == 9) ? 3 : (lane >= 11 && lane < 14 ? lane - 11 : 0);
-    const bool rbwd = lane < 6 ? (lane & 1) != 0 : lane >= 11;
+    // row role of this lane: 0..5 R(x +- mu), 6 R(x + t), 7 R(x), rows
+    // (blk * 2 + parity) * Vh + cb of the field; 8..11 U_mu(x - mu) (lane 11
+    // repeats mu = 2), rows (opar * Vh + cb') * 4 + mu of the links.  Hop roles
+    // add the neighbour's lex step (or its wrap), R(x) takes the site itself.
+    // L(x) and L(x + t) are the rows of R(x) and R(x + t) in the left field.
+    const bool hop = lane != 7;
+    const int rmu = lane < 6 ? (lane >> 1) : lane == 6 ? 3 : (lane >= 8 && lane < 12 ? min(lane - 8, 2) : 0);
+    const bool rbwd = lane < 6 ? (lane & 1) != 0 : lane >= 8;
     const int rbit = 2 * rmu + (rbwd ? 1 : 0);
     const int rstep = rbwd ? -g.stride[rmu] : g.stride[rmu];
     const int rwrap = rbwd ? (g.L[rmu] - 1) * g.stride[rmu] : -(g.L[rmu] - 1) * g.stride[rmu];
-    const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il);
-    const unsigned char* rbase = nullptr;
-    unsigned rmul = kIlSiteBytes, rdoff = 0, rbytes = 0;
-    const size_t fpar = ((size_t)blk * 2 + par) * Vh * kIlSiteBytes;
-    const size_t fopar = ((size_t)blk * 2 + opar) * Vh * kIlSiteBytes;
-    if (lane < 10) {
-      const unsigned char* f = (lane == 8 || lane == 9) ? a.L : a.R;
-      rbase = f + ((lane == 7 || lane == 8) ? fpar : fopar);
-      rdoff = lane * kIlSiteBytes;
-      rbytes = kIlSiteBytes;
-    } else if (lane == 10) {
-      rbase = lk + (size_t)par * Vh * kIlLinkSiteBytes;
-      rmul = kIlLinkSiteBytes;
-      rdoff = ST::kLinkOff;
-      rbytes = kIlLinkSiteBytes;
-    } else if (lane < 14) {
-      rbase = lk + (size_t)opar * Vh * kIlLinkSiteBytes + rmu * kIlLinkBytes;
-      rmul = kIlLinkSiteBytes;
-      rdoff = ST::kBwdOff + rmu * kIlLinkBytes;
-      rbytes = kIlLinkBytes;
-    }
+    const int rrow0 = lane < 8 ? (blk * 2 + (lane == 7 ? par : opar)) * g.Vh : opar * g.Vh * 4 + rmu;
+    const int rrmul = lane < 8 ? 1 : 4;
+    const unsigned char* lk = reinterpret_cast<const unsigned char*>(a.links_il) + (size_t)par * Vh * kIlLinkSiteBytes;
     constexpr unsigned total = ST::kCopyBytes;
-    static_assert(ST::kCopyBytes == 10 * kIlSiteBytes + kIlLinkSiteBytes + 3 * kIlLinkBytes, "copy roles");
+    static_assert(ST::kLinkOff % 128 == 0 && ST::kBwdOff % 128 == 0 && ST::kBytes % 128 == 0 &&
+                      ST::kBwdOff >= ST::kLinkOff + kIlLinkSiteBytes && ST::kBytes >= ST::kBwdOff + 4 * kIlLinkBytes,
+                  "stage layout");
     unsigned char* ring = od_smem + wq * ST::kWarpBytes;
     const unsigned ring_s = smem_u32(ring);
     const unsigned bar0 = smem_u32(&bars[wq][0]);
@@ -192,10 +188,25 @@ __global__ void __launch_bounds__(kOdWarps * 32, 3) oneD_il_kernel(const OdArgs 
       const int lex = __shfl_sync(0xffffffffu, lexl, m & 31);
       const unsigned msk = __shfl_sync(0xffffffffu, bml, m & 31);
       const int nlex = lex + (((msk >> rbit) & 1u) ? rwrap : rstep);
-      const int idx = hop ? (nlex >> 1) : cb0 + kOdWarps * m;
+      const int cb = cb0 + kOdWarps * m;
+      if (lane < 12) rowbuf[wq][lane] = rrow0 + (hop ? (nlex >> 1) : cb) * rrmul;
       const unsigned bar = bar0 + st * 8;
-      if (lane == 0) mbar_expect_tx(bar, total);
-      if (rbytes) bulk_g2s(ring_s + st * ST::kBytes + rdoff, rbase + (size_t)idx * rmul, rbytes, bar);
+      __syncwarp();
+      if (lane == 0) {
+        // every copy of the stage from one lane: gather4 of R's eight rows,
+        // the two rows of L, the site's links, gather4 of the backward links
+        const int4 q0 = *reinterpret_cast<const int4*>(&rowbuf[wq][0]);
+        const int4 q1 = *reinterpret_cast<const int4*>(&rowbuf[wq][4]);
+        const int4 q2 = *reinterpret_cast<const int4*>(&rowbuf[wq][8]);
+        const unsigned sb = ring_s + st * ST::kBytes;
+        mbar_expect_tx(bar, total);
+        gather4_g2s(sb, &tr, q0.x, q0.y, q0.z, q0.w, bar);
+        gather4_g2s(sb + 4 * kIlSiteBytes, &tr, q1.x, q1.y, q1.z, q1.w, bar);
+        bulk_g2s(sb + 8 * kIlSiteBytes, a.L + (size_t)q1.w * kIlSiteBytes, kIlSiteBytes, bar);
+        bulk_g2s(sb + 9 * kIlSiteBytes, a.L + (size_t)q1.z * kIlSiteBytes, kIlSiteBytes, bar);
+        bulk_g2s(sb + ST::kLinkOff, lk + (size_t)cb * kIlLinkSiteBytes, kIlLinkSiteBytes, bar);
+        gather4_g2s(sb + ST::kBwdOff, &tlk, q2.x, q2.y, q2.z, q2.w, bar);
+      }
     };
     // stage 1 lane constants (as the interleaved Dslash): A words of rows
     // g, g + 8 at colour t (lanes t = 3 read colour 0 against zero B rows);
@@ -544,6 +555,20 @@ extern "C" tm_status_t loop_contract_oneD_il(tm_op_t* op, const void* left, cons
   a.nchunk = nchunk;
   a.right_g5 = right_g5 != 0;
   const dim3 grid((unsigned)(nblk * nchunk), (unsigned)(2 * g.L[3]));
+  if ((size_t)nblk * 2 * g.Vh >= ((size_t)1 << 31) || (size_t)g.Vh * 8 >= ((size_t)1 << 31)) {
+    set_error("%s: lattice too large for the interleaved kernel (rows >= 2^31)", what);
+    dev_free(scratch, s);
+    return TM_ERR_UNSUPPORTED;
+  }
+  // R's rows (768 bytes per site) and the backward links' rows (48 bytes
+  // per site and direction) as tensors of the gather4 copies
+  CUtensorMap tmr, tlk;
+  tm_status_t mst = il_row_map(&tmr, right, kIlSiteBytes / 4, (size_t)nblk * 2 * g.Vh);
+  if (mst == TM_OK) mst = il_row_map(&tlk, a.links_il, kIlLinkBytes / 4, (size_t)g.Vh * 8);
+  if (mst != TM_OK) {
+    dev_free(scratch, s);
+    return mst;
+  }
   tm_status_t st;
   {
     // algorithmic bytes: both fields once (16 systems per 768-byte site) and
@@ -551,9 +576,9 @@ extern "C" tm_status_t loop_contract_oneD_il(tm_op_t* op, const void* left, cons
     TraceScope tr(s, prec == TM_PREC_F16 ? "oneD.f16il" : "oneD.bf16il", 2.0 * 24.0 * 2.0 * 2.0 * g.Vh,
                   4.0 * 18.0 * 2.0 * 2.0 * g.Vh, nrhs);
     if (prec == TM_PREC_F16)
-      oneD_il_kernel<__half><<<grid, kOdWarps * 32, OdStage::kSmem, s>>>(a);
+      oneD_il_kernel<__half><<<grid, kOdWarps * 32, OdStage::kSmem, s>>>(a, tmr, tlk);
     else
-      oneD_il_kernel<__nv_bfloat16><<<grid, kOdWarps * 32, OdStage::kSmem, s>>>(a);
+      oneD_il_kernel<__nv_bfloat16><<<grid, kOdWarps * 32, OdStage::kSmem, s>>>(a, tmr, tlk);
     count_launch();
     st = check_launch(what);
   }
