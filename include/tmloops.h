@@ -162,8 +162,9 @@ tm_status_t tm_dslash_g5(tm_op_t *op, void *out, const void *in, int nrhs, int d
  * tm_dslash_il: out = M in, M^dag in or D_W in (as tm_dslash) on fields in
  *   this layout, each hop a warp-level MMA over 16 systems (FP16/BF16
  *   products, FP32 accumulation), every site's neighbours staged in shared
- *   memory by bulk asynchronous copies (the fields must be 16-byte aligned,
- *   else TM_ERR_ARG).  Needs the 18-real 16-bit link copy (recon 18 or 0:
+ *   memory by asynchronous tensor (gather4) and bulk copies (the fields must
+ *   be 16-byte aligned, else TM_ERR_ARG; TM_ERR_CUDA if the driver cannot
+ *   encode a tensor map).  Needs the 18-real 16-bit link copy (recon 18 or 0:
  *   TM_ERR_UNSUPPORTED for 12).  Results agree with tm_dslash to the 16-bit
  *   tolerance; the bits differ (summation order).  A staging wait that never
  *   completes gives up after about one second and sets a flag of
@@ -350,7 +351,7 @@ tm_status_t loop_contract_oneD(tm_op_t *op, const void *left, const void *right,
  *   directions as warp-level MMAs over the systems (FP32 accumulation, rounded
  *   once to the storage format), then the 4 x 4 spin products per system as
  *   MMAs over (colour, re/im) with FP32 sums over the sites; every site's
- *   neighbours staged by bounded bulk copies as in tm_dslash_il (its
+ *   neighbours staged by bounded tensor and bulk copies as in tm_dslash_il (its
  *   time-outs set the operator's flag: tm_op_check).  Needs the 18-real
  *   16-bit links (recon 18 or 0, else TM_ERR_UNSUPPORTED).
  * Results agree with the standard contractions of the same fields to the
