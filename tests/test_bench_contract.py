@@ -8,6 +8,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -29,18 +31,21 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
-def test_traffic_ratio_applies_only_to_the_captured_sources():
+@pytest.mark.parametrize("summary,sources,kernel", [
+    ("dslash_traffic.txt", ("dslash.cuh", "tm_core.cuh"), "dslash.f16.out"),
+    ("dslash_il_traffic.txt", ("dslash_il.cu", "il_core.cuh", "tm_core.cuh"), "dslash.f16il.out")])
+def test_traffic_ratio_applies_only_to_the_captured_sources(summary, sources, kernel):
     sys.path.insert(0, ROOT)
     import bench
     kv = {}
-    with open(os.path.join(ROOT, "profiles", "dslash_traffic.txt")) as f:
+    with open(os.path.join(ROOT, "profiles", summary)) as f:
         for line in f:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
     csrc = os.path.join(ROOT, "paper_1401_6749_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in ("dslash.cuh", "tm_core.cuh"))
-    got = bench._traffic_per_launch(1_000_000, "dslash.f16.out")
+    src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in sources)
+    got = bench._traffic_per_launch(1_000_000, kernel)
     if hashlib.sha256(src).hexdigest() == kv["kernel_sources_sha256"]:
         assert got == round(float(kv["traffic_per_algorithmic_byte"]) * 1_000_000)
     else:
